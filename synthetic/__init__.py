@@ -1,0 +1,205 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module only *places* problem data: mesh edge coordinates, physical
+coordinates of sample points, the isentropic-vortex initial state of Sec. 5.1
+(Eq. VP_Solution), smooth random states and random vectors.  It holds none of
+the flux-reconstruction, Krylov or time-integration arithmetic, and it imports
+neither the oracle nor the CUDA package.
+
+Point layout used everywhere: state arrays have shape ``(Ne, 4, Np)`` with
+``Np = (p+1)**2``; point ``i + (p+1)*j`` is the i-th node along x and the j-th
+node along y; element ``ix + Nx*iy``.  Variables are the conserved
+``(rho, rho*u, rho*v, E)`` of Sec. 2 in two dimensions.
+
+The node positions used to *place* a field come from NumPy's Gauss-Legendre
+routine; they only decide where the smooth input field is sampled.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def uniform_edges(n: int, lo: float, hi: float) -> np.ndarray:
+    """``n+1`` equally spaced element edges on ``[lo, hi]``."""
+    return np.linspace(lo, hi, n + 1, dtype=np.float64)
+
+
+def channel_y_edges(ny: int, first: float = 1e-3, ratio: float = 1.15,
+                    height: float = 1.0) -> np.ndarray:
+    """Wall-clustered edges on ``[0, height]``.
+
+    Cells grow geometrically by ``ratio`` from ``first`` at each wall until
+    they reach the uniform size that fills the rest of each half, which is
+    kept from then on (the capped reading of the stretched channel mesh).
+    """
+    if ny % 2:
+        raise ValueError("ny must be even")
+    half = ny // 2
+    half_h = 0.5 * height
+    # find the number of geometric cells g such that the remaining uniform
+    # cells are at least as large as the last geometric cell
+    best = None
+    for g in range(0, half + 1):
+        geo = [first * ratio ** k for k in range(g)]
+        rest = half - g
+        if rest == 0:
+            if abs(sum(geo) - half_h) / half_h < 1e-9:
+                best = (g, geo, 0.0)
+            continue
+        u = (half_h - sum(geo)) / rest
+        if u <= 0:
+            break
+        if not geo or u >= geo[-1] * ratio * 0.999999:
+            best = (g, geo, u)
+        else:
+            break
+    if best is None:
+        raise ValueError("cannot build the stretched half-channel")
+    g, geo, u = best
+    sizes = geo + [u] * (half - g)
+    lower = np.concatenate([[0.0], np.cumsum(sizes)])
+    lower[-1] = half_h
+    upper = height - lower[::-1]
+    return np.concatenate([lower, upper[1:]])
+
+
+def sample_nodes(p: int) -> np.ndarray:
+    """Gauss-Legendre nodes on [-1, 1] used to place sample points."""
+    x, _ = np.polynomial.legendre.leggauss(p + 1)
+    return x
+
+
+def point_coords(x_edges: np.ndarray, y_edges: np.ndarray, p: int):
+    """Physical coordinates ``X, Y`` of shape ``(Ne, Np)`` in the point layout."""
+    s = sample_nodes(p)
+    nx, ny = len(x_edges) - 1, len(y_edges) - 1
+    xa, hx = x_edges[:-1], np.diff(x_edges)
+    ya, hy = y_edges[:-1], np.diff(y_edges)
+    # (ny, nx, p+1 [j], p+1 [i])
+    X = xa[None, :, None, None] + 0.5 * (s[None, None, None, :] + 1.0) * hx[None, :, None, None]
+    Y = ya[:, None, None, None] + 0.5 * (s[None, None, :, None] + 1.0) * hy[:, None, None, None]
+    X = np.broadcast_to(X, (ny, nx, p + 1, p + 1)).reshape(nx * ny, (p + 1) ** 2)
+    Y = np.broadcast_to(Y, (ny, nx, p + 1, p + 1)).reshape(nx * ny, (p + 1) ** 2)
+    return np.ascontiguousarray(X), np.ascontiguousarray(Y)
+
+
+def conserved(rho, u, v, pr, gamma: float = GAMMA) -> np.ndarray:
+    """Stack primitive fields into conserved ``(Ne, 4, Np)``."""
+    E = pr / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.ascontiguousarray(np.stack([rho, rho * u, rho * v, E], axis=1))
+
+
+@dataclass(frozen=True)
+class Vortex:
+    """Isentropic vortex of Sec. 5.1 (Eq. VP_Solution).
+
+    Free stream density 1, speed ``sqrt(2)`` along angle ``theta`` (45 degrees
+    gives u = v = 1), Mach number ``mach`` on that speed, gas constant R = 1,
+    strength ``alpha`` and ``phi``.  ``r`` is read as the Euclidean distance to
+    the centre, so the exponent is ``phi * (1 - r**2)``.
+    """
+    alpha: float = 5.0
+    phi: float = 0.5
+    mach: float = 0.5
+    theta: float = math.pi / 4
+    x0: float = 0.0
+    y0: float = 0.0
+    gamma: float = GAMMA
+
+    @property
+    def speed(self) -> float:
+        return math.sqrt(2.0)
+
+    @property
+    def uinf(self) -> float:
+        return self.speed * math.cos(self.theta)
+
+    @property
+    def vinf(self) -> float:
+        return self.speed * math.sin(self.theta)
+
+    @property
+    def pinf(self) -> float:
+        return self.speed ** 2 / (self.gamma * self.mach ** 2)
+
+    def state(self, X, Y, t: float = 0.0, box=(-5.0, 5.0, -5.0, 5.0)) -> np.ndarray:
+        """Conserved state at time ``t``: the vortex advected with the free
+        stream, centre taken at its nearest periodic image."""
+        g = self.gamma
+        lx, ly = box[1] - box[0], box[3] - box[2]
+        xc = self.x0 + self.uinf * t
+        yc = self.y0 + self.vinf * t
+        dx = X - xc
+        dy = Y - yc
+        dx = dx - lx * np.round(dx / lx)
+        dy = dy - ly * np.round(dy / ly)
+        r2 = dx * dx + dy * dy
+        ex = np.exp(self.phi * (1.0 - r2))
+        du = -self.alpha / (2 * math.pi) * dy * ex
+        dv = self.alpha / (2 * math.pi) * dx * ex
+        dT = -self.alpha ** 2 * (g - 1.0) / (16 * self.phi * g * math.pi ** 2) * ex * ex
+        Tinf = self.pinf  # rho_inf = 1, R = 1
+        T = Tinf + dT
+        rho = (T / Tinf) ** (1.0 / (g - 1.0))
+        pr = rho * T
+        return conserved(rho, self.uinf + du, self.vinf + dv, pr, g)
+
+
+def density_wave_state(X, Y, t: float = 0.0, amp: float = 0.2, u: float = 1.0, v: float = 1.0,
+                       pr: float = 1.0, box=(-5.0, 5.0, -5.0, 5.0), gamma: float = GAMMA):
+    """Smooth density wave advected at constant (u, v, p): exact solution of
+    the Euler equations is pure translation."""
+    lx = box[1] - box[0]
+    ly = box[3] - box[2]
+    kx, ky = 2 * math.pi / lx, 2 * math.pi / ly
+    rho = 1.0 + amp * np.sin(kx * (X - u * t) + ky * (Y - v * t))
+    return conserved(rho, np.full_like(X, u), np.full_like(X, v), np.full_like(X, pr), gamma)
+
+
+def smooth_random_state(X, Y, seed: int, amp: float = 0.05, modes: int = 3,
+                        box=(-5.0, 5.0, -5.0, 5.0), base=(1.0, 0.7, -0.4, 2.0),
+                        gamma: float = GAMMA) -> np.ndarray:
+    """Free stream ``base = (rho, u, v, p)`` plus random periodic Fourier
+    modes of relative amplitude ``amp`` in every primitive field."""
+    rng = np.random.default_rng(seed)
+    lx = box[1] - box[0]
+    ly = box[3] - box[2]
+    fields = []
+    for b in base:
+        f = np.full_like(X, b)
+        for _ in range(modes):
+            kx, ky = rng.integers(-3, 4, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.uniform(-1, 1) * amp * max(abs(b), 1.0)
+            f = f + a * np.sin(2 * math.pi * (kx * X / lx + ky * Y / ly) + ph)
+        fields.append(f)
+    rho, u, v, pr = fields
+    return conserved(rho, u, v, pr, gamma)
+
+
+def random_vector(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Standard-normal array of the given shape (fp64)."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal(shape)
+
+
+def uniform_mesh(n: int, box=(-5.0, 5.0, -5.0, 5.0), ny: int | None = None):
+    ny = n if ny is None else ny
+    return uniform_edges(n, box[0], box[1]), uniform_edges(ny, box[2], box[3])
+
+
+def stretched_mesh(nx: int, ny: int, seed: int = 0, amp: float = 0.3,
+                   box=(-5.0, 5.0, -5.0, 5.0)):
+    """Tensor-product mesh with randomly jittered (non-uniform) edges."""
+    rng = np.random.default_rng(seed)
+    def jitter(n, lo, hi):
+        e = np.linspace(lo, hi, n + 1)
+        h = (hi - lo) / n
+        e[1:-1] += rng.uniform(-amp, amp, n - 1) * h
+        return e
+    return jitter(nx, box[0], box[1]), jitter(ny, box[2], box[3])
