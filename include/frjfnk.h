@@ -1,0 +1,182 @@
+/*
+ * frjfnk.h - C ABI of the GB300 Jacobian-free Newton-Krylov library for
+ * high-order flux reconstruction (FR/CPR) on 2D quadrilaterals.
+ *
+ * Method: Wang & Yu, "A comparative study of implicit Jacobian-free
+ * Rosenbrock-Wanner, ESDIRK and BDF methods for unsteady flow simulation with
+ * high-order flux reconstruction formulations" (arXiv 1904.04825).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status (FR_OK = 0 or an FR_ERR_* code); the
+ *    message of the last failure is returned by fr_last_error(ctx).
+ *  - State-shaped vectors (U, R, z, y, b, x, ...) are caller-owned DEVICE
+ *    pointers to double[Ne][4][Np] with Np = (p+1)^2: element ix + Nx*iy,
+ *    variable (rho, rho*u, rho*v, E) of Sec. 2, point i + (p+1)*j where i
+ *    runs along x and j along y over the Gauss-Legendre solution points.
+ *    The total length is ndof = Ne * 4 * Np doubles.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered; calls that return a convergence
+ *    result (gmres_solve, step_*) synchronise the stream before returning.
+ *  - A context owns all workspace (Krylov basis, element blocks, stage
+ *    buffers), allocated once by fr_ctx_create on the device that is current
+ *    at that time; that device must be current for every later call on the
+ *    context.  Calls on one context must not overlap (one stream at a time).
+ *    Nothing is allocated after fr_ctx_create.
+ *  - The mesh is a periodic tensor-product mesh of axis-aligned quads; the
+ *    edge arrays are HOST pointers copied at creation.
+ */
+#ifndef FRJFNK_H
+#define FRJFNK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FR_OK = 0,
+  FR_ERR_INVALID_ARG = 1,   /* bad pointer, size, degree or option */
+  FR_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  FR_ERR_NONFINITE = 3,     /* a NaN/Inf norm was met; the stepper's U is unchanged */
+  FR_ERR_NOT_CONVERGED = 4, /* GMRES hit its restart limit / PTC hit max iterations */
+  FR_ERR_PTC_STALLED = 5,   /* too many rejected pseudo-time steps */
+  FR_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
+  FR_ERR_UNSUPPORTED = 7    /* degree or configuration not compiled in */
+};
+
+typedef struct fr_ctx fr_ctx;
+
+/* Periodic mesh: nx*ny quads, element ix+nx*iy spans
+ * [x_edges[ix], x_edges[ix+1]] x [y_edges[iy], y_edges[iy+1]] (Sec. 3:
+ * affine elements, |J| = hx*hy/4).  nx, ny >= 2.  Host arrays of length
+ * nx+1 and ny+1, strictly increasing. */
+typedef struct fr_mesh_desc {
+  int nx, ny;
+  const double* x_edges;
+  const double* y_edges;
+} fr_mesh_desc;
+
+/* Options (fill with fr_default_opts first). */
+typedef struct fr_opts {
+  double gamma;          /* ratio of specific heats, 1.4 (Sec. 2) */
+  int m_max;             /* largest GMRES restart length the workspace holds (30) */
+  double eps_rel;        /* FD Jv step eps = eps_rel (1 + ||U||_2) / ||z||_2 (1e-7) */
+  double eps_fixed;      /* > 0: fixed eps instead (the paper's 1e-8, Sec. 4.5) */
+  double block_eps_rel;  /* element-block FD step eps_j = block_eps_rel (1 + |U_j|) (1e-7) */
+  int precond;           /* 1: element-Jacobi right preconditioner (Sec. 4.5), 0: none */
+  int gmres_m;           /* restart length used by the steppers (30) */
+  int gmres_max_restarts;/* restart limit used by the steppers (20) */
+  double tol_lin;        /* ROW: GMRES relative tolerance tol_rel,linear (1e-8) */
+} fr_opts;
+
+/* Pseudo-transient continuation options (Sec. 4.4; fill with
+ * fr_default_ptc_opts first). */
+typedef struct fr_ptc_opts {
+  double tol_nl;         /* ||F^k|| / ||F^0|| stopping tolerance (1e-6) */
+  double tol_lin;        /* GMRES relative tolerance inside PTC (1e-1) */
+  double dtau_init;      /* <= 0: dtau_init = dt (the paper's default) */
+  double dtau_max;       /* 1e20 (the paper's default) */
+  int max_iters;         /* accepted pseudo steps per solve (200) */
+  int max_rejections;    /* rejected pseudo steps before FR_ERR_PTC_STALLED (30) */
+  double reject_above;   /* reject when the GMRES relative residual exceeds this (0.1) */
+} fr_ptc_opts;
+
+typedef struct fr_gmres_info {
+  int iters;             /* Arnoldi iterations over all cycles */
+  int restarts;          /* cycles after the first that iterated */
+  int converged;         /* 1 if relres <= rtol */
+  double relres;         /* Givens estimate of ||b - A x|| / ||b|| */
+} fr_gmres_info;
+
+typedef struct fr_step_stats {
+  int gmres_iters;       /* sum over all linear solves of the step */
+  int gmres_calls;       /* number of linear solves */
+  int ptc_iters;         /* accepted pseudo steps (ESDIRK / BDF2) */
+  int rejections;        /* rejected pseudo steps (ESDIRK / BDF2) */
+  int residual_evals;    /* R(q) evaluations outside the Jv products */
+  int converged;         /* 1 if every solve met its tolerance */
+} fr_step_stats;
+
+void fr_default_opts(fr_opts* opts);
+void fr_default_ptc_opts(fr_ptc_opts* opts);
+
+/* Create a context for degree p (2 <= p <= 4) on the current device.
+ * Copies the mesh, builds the 1D tables (Gauss-Legendre points, Lagrange
+ * basis, Radau g_DG correction derivatives, Sec. 3) and allocates every
+ * workspace buffer.  *out receives the handle (NULL on failure). */
+int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opts, fr_ctx** out);
+/* Free the context and its device memory. NULL is accepted. */
+int fr_ctx_destroy(fr_ctx* ctx);
+/* Message of the last failing call on ctx ("" if none); static string for ctx == NULL. */
+const char* fr_last_error(const fr_ctx* ctx);
+/* Number of doubles in one state vector (Ne * 4 * (p+1)^2). */
+long long fr_ndof(const fr_ctx* ctx);
+
+/* R = R(U), the FR/CPR semi-discrete right-hand side dq/dt = R(q)
+ * (Sec. 3 Eqs. discrete_ns and simplified_ode): Lagrange extrapolation of
+ * the solution to the flux points, Rusanov common flux F^num scaled as in
+ * Eq. norm_num_f, divergence of the local flux plus the Radau correction.
+ * U, R: device, ndof doubles, must not alias. */
+int fr_residual(fr_ctx* ctx, const double* U, double* R, void* stream);
+
+/* y = shift*z - (R(U + eps z) - R0) / eps, the finite-difference
+ * Jacobian-vector product of Sec. 4.5 applied as A z with
+ * A = D - dR/dq, D = shift*I (Eq. linear).  eps follows fr_opts; a zero z
+ * gives y = 0.  R0 must equal R(U).  All device, ndof doubles; y must not
+ * alias the inputs. */
+int fr_jv(fr_ctx* ctx, const double* U, const double* R0, const double* z, double shift,
+          double* y, void* stream);
+
+/* Form and invert the element-Jacobi preconditioner blocks
+ * M_e = shift*I - dR_e/dq_e (the diagonal blocks of A, Sec. 4.5) at the
+ * state U, stored inside ctx.  The paper does not say how the blocks are
+ * formed: here by element-local forward differences with every neighbour
+ * trace frozen, step block_eps_rel (1 + |U_j|).  Block rows/columns follow
+ * the element's slice of the state.  R0 is accepted for interface symmetry
+ * and may be NULL (the local differences need only U). */
+int ejacobi_factor(fr_ctx* ctx, const double* U, const double* R0, double shift, void* stream);
+
+/* z_e = M_e^{-1} r_e for every element with the blocks of the last
+ * ejacobi_factor call (FR_ERR_INVALID_ARG if there was none).  r, z: device,
+ * ndof doubles, must not alias. */
+int ejacobi_apply(fr_ctx* ctx, const double* r, double* z, void* stream);
+
+/* Solve A x = b, A z = shift*z - (R(U+eps z) - R0)/eps, with restarted
+ * GMRES(m) (Sec. 4.5), right-preconditioned by the current element-Jacobi
+ * blocks when fr_opts.precond = 1 (call ejacobi_factor with the same U and
+ * shift first).  x is the initial guess on entry and the solution on exit.
+ * Stops when the Givens estimate of ||b - A x|| <= rtol*||b|| or after
+ * max_restarts+1 cycles (then FR_ERR_NOT_CONVERGED, x holds the last
+ * iterate).  m <= fr_opts.m_max.  info may be NULL. */
+int gmres_solve(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                double* x, int m, double rtol, int max_restarts, fr_gmres_info* info,
+                void* stream);
+
+/* One linearly implicit Rosenbrock-Wanner step of Eq. Rosenbrock_General,
+ * q^{n+1} = q^n + sum_j m_j Y_j, with (I/(omega dt) - dR/dq)^n frozen at
+ * q^n.  scheme = 2 (ROW2, 3 stages), 3 (ROS34PW2, 4 stages), 4 (RODASP,
+ * 6 stages).  Linear solves use fr_opts.gmres_m / gmres_max_restarts /
+ * tol_lin from a zero guess.  U (device) is advanced in place.  stats may be
+ * NULL. */
+int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_stats* stats, void* stream);
+
+/* One ESDIRK step (Eq. ESDIRK2); every implicit stage (Eq. SDIRK_newton) is
+ * solved by pseudo-transient continuation with SER time-step control and
+ * rejection (Eq. linearized_pseudo_transient_final, Sec. 4.4), the
+ * element-Jacobi blocks re-formed at every pseudo step.  scheme = 2, 3, 4
+ * (3, 4, 6 stages).  ptc may be NULL (defaults).  U advanced in place. */
+int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts* ptc,
+                fr_step_stats* stats, void* stream);
+
+/* One BDF2 step (Eq. BDF with omega = 2/3, a = (4/3, -1/3); Eq. BDF_newton
+ * solved by pseudo-transient continuation).  U holds q^n on entry and
+ * q^{n+1} on exit; U_prev holds q^{n-1} on entry and q^n on exit.
+ * first_step != 0 takes one backward-Euler step instead (the paper does not
+ * say how BDF2 starts) and ignores U_prev's input. */
+int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
+              const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRJFNK_H */

@@ -1,0 +1,261 @@
+"""Python binding of libfrjfnk (GB300 Jacobian-free Newton-Krylov for 2D FR/CPR).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library built from ``csrc/`` (see ``include/frjfnk.h`` for the C ABI).  The
+functions keep the C names and take PyTorch CUDA float64 tensors laid out as
+``(Ne, 4, Np)`` (any contiguous shape with ``ndof`` elements); PyTorch only
+provides device memory and the current stream.
+
+Importing this package loads ``lib/libfrjfnk.so`` and fails loudly when it
+has not been built (``python -c "import __graft_entry__ as g; g.build()"``):
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libfrjfnk.so")
+
+FR_OK = 0
+FR_ERR_INVALID_ARG = 1
+FR_ERR_CUDA = 2
+FR_ERR_NONFINITE = 3
+FR_ERR_NOT_CONVERGED = 4
+FR_ERR_PTC_STALLED = 5
+FR_ERR_TIMEOUT = 6
+FR_ERR_UNSUPPORTED = 7
+ERROR_NAMES = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_CUDA", 3: "FR_ERR_NONFINITE",
+               4: "FR_ERR_NOT_CONVERGED", 5: "FR_ERR_PTC_STALLED", 6: "FR_ERR_TIMEOUT",
+               7: "FR_ERR_UNSUPPORTED"}
+
+
+class FrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fr_mesh_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x_edges", ctypes.POINTER(ctypes.c_double)),
+                ("y_edges", ctypes.POINTER(ctypes.c_double))]
+
+
+class fr_opts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("m_max", ctypes.c_int),
+                ("eps_rel", ctypes.c_double), ("eps_fixed", ctypes.c_double),
+                ("block_eps_rel", ctypes.c_double), ("precond", ctypes.c_int),
+                ("gmres_m", ctypes.c_int), ("gmres_max_restarts", ctypes.c_int),
+                ("tol_lin", ctypes.c_double)]
+
+
+class fr_ptc_opts(ctypes.Structure):
+    _fields_ = [("tol_nl", ctypes.c_double), ("tol_lin", ctypes.c_double),
+                ("dtau_init", ctypes.c_double), ("dtau_max", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("max_rejections", ctypes.c_int),
+                ("reject_above", ctypes.c_double)]
+
+
+class fr_gmres_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+class fr_step_stats(ctypes.Structure):
+    _fields_ = [("gmres_iters", ctypes.c_int), ("gmres_calls", ctypes.c_int),
+                ("ptc_iters", ctypes.c_int), ("rejections", ctypes.c_int),
+                ("residual_evals", ctypes.c_int), ("converged", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "fr_default_opts": (None, [ctypes.POINTER(fr_opts)]),
+        "fr_default_ptc_opts": (None, [ctypes.POINTER(fr_ptc_opts)]),
+        "fr_ctx_create": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts),
+                              ctypes.POINTER(ctypes.c_void_p)]),
+        "fr_ctx_destroy": (I, [P]),
+        "fr_last_error": (ctypes.c_char_p, [P]),
+        "fr_ndof": (ctypes.c_longlong, [P]),
+        "fr_residual": (I, [P, P, P, V]),
+        "fr_jv": (I, [P, P, P, P, D, P, V]),
+        "ejacobi_factor": (I, [P, P, P, D, V]),
+        "ejacobi_apply": (I, [P, P, P, V]),
+        "gmres_solve": (I, [P, P, P, D, P, P, I, D, I, ctypes.POINTER(fr_gmres_info), V]),
+        "step_row": (I, [P, I, D, P, ctypes.POINTER(fr_step_stats), V]),
+        "step_esdirk": (I, [P, I, D, P, ctypes.POINTER(fr_ptc_opts),
+                            ctypes.POINTER(fr_step_stats), V]),
+        "step_bdf2": (I, [P, D, P, P, I, ctypes.POINTER(fr_ptc_opts),
+                          ctypes.POINTER(fr_step_stats), V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def default_opts(**kw) -> fr_opts:
+    o = fr_opts()
+    lib.fr_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_ptc_opts(**kw) -> fr_ptc_opts:
+    o = fr_ptc_opts()
+    lib.fr_default_ptc_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns an ``fr_ctx`` (mesh, degree, options, device workspace)."""
+
+    def __init__(self, x_edges, y_edges, p: int, opts: fr_opts | None = None):
+        xe = np.ascontiguousarray(x_edges, dtype=np.float64)
+        ye = np.ascontiguousarray(y_edges, dtype=np.float64)
+        desc = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
+                            xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.opts = opts if opts is not None else default_opts()
+        h = ctypes.c_void_p()
+        rc = lib.fr_ctx_create(ctypes.byref(desc), p, ctypes.byref(self.opts), ctypes.byref(h))
+        if rc != FR_OK:
+            raise FrError(rc, "fr_ctx_create failed")
+        self.handle = h
+        self.p = p
+        self.nx, self.ny = len(xe) - 1, len(ye) - 1
+        self.ne = self.nx * self.ny
+        self.np = (p + 1) ** 2
+        self.ndof = int(lib.fr_ndof(h))
+        self.shape = (self.ne, 4, self.np)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fr_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc, allow=()):
+        if rc != FR_OK and rc not in allow:
+            raise FrError(rc, lib.fr_last_error(self.handle).decode())
+        return rc
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+
+def fr_residual(ctx: Context, U, R, stream=None):
+    return ctx.check(lib.fr_residual(ctx.handle, _ptr(U), _ptr(R), _stream(stream)))
+
+
+def fr_jv(ctx: Context, U, R0, z, shift, y, stream=None):
+    return ctx.check(lib.fr_jv(ctx.handle, _ptr(U), _ptr(R0), _ptr(z), float(shift), _ptr(y),
+                               _stream(stream)))
+
+
+def ejacobi_factor(ctx: Context, U, R0, shift, stream=None):
+    return ctx.check(lib.ejacobi_factor(ctx.handle, _ptr(U), _ptr(R0), float(shift), _stream(stream)))
+
+
+def ejacobi_apply(ctx: Context, r, z, stream=None):
+    return ctx.check(lib.ejacobi_apply(ctx.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+
+@dataclass
+class GmresInfo:
+    iters: int
+    restarts: int
+    converged: bool
+    relres: float
+    code: int
+
+
+def gmres_solve(ctx: Context, U, R0, shift, b, x, m=30, rtol=1e-8, max_restarts=20, stream=None,
+                allow_not_converged=True) -> GmresInfo:
+    info = fr_gmres_info()
+    rc = lib.gmres_solve(ctx.handle, _ptr(U), _ptr(R0), float(shift), _ptr(b), _ptr(x), int(m),
+                         float(rtol), int(max_restarts), ctypes.byref(info), _stream(stream))
+    ctx.check(rc, allow=(FR_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return GmresInfo(info.iters, info.restarts, bool(info.converged), info.relres, rc)
+
+
+@dataclass
+class StepStats:
+    gmres_iters: int
+    gmres_calls: int
+    ptc_iters: int
+    rejections: int
+    residual_evals: int
+    converged: bool
+    code: int
+
+
+def _stats(st, rc):
+    return StepStats(st.gmres_iters, st.gmres_calls, st.ptc_iters, st.rejections,
+                     st.residual_evals, bool(st.converged), rc)
+
+
+def step_row(ctx: Context, scheme: int, dt: float, U, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+    st = fr_step_stats()
+    rc = lib.step_row(ctx.handle, int(scheme), float(dt), _ptr(U), ctypes.byref(st), _stream(stream))
+    ctx.check(rc, allow=allow)
+    return _stats(st, rc)
+
+
+def step_esdirk(ctx: Context, scheme: int, dt: float, U, ptc: fr_ptc_opts | None = None, stream=None,
+                allow=(FR_ERR_NOT_CONVERGED,)):
+    st = fr_step_stats()
+    rc = lib.step_esdirk(ctx.handle, int(scheme), float(dt), _ptr(U),
+                         ctypes.byref(ptc) if ptc is not None else None, ctypes.byref(st),
+                         _stream(stream))
+    ctx.check(rc, allow=allow)
+    return _stats(st, rc)
+
+
+def step_bdf2(ctx: Context, dt: float, U, U_prev, first_step: bool, ptc: fr_ptc_opts | None = None,
+              stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+    st = fr_step_stats()
+    rc = lib.step_bdf2(ctx.handle, float(dt), _ptr(U), _ptr(U_prev), int(bool(first_step)),
+                       ctypes.byref(ptc) if ptc is not None else None, ctypes.byref(st),
+                       _stream(stream))
+    ctx.check(rc, allow=allow)
+    return _stats(st, rc)

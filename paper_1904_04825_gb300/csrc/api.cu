@@ -1,0 +1,250 @@
+// C ABI entry points: context lifetime, argument checks, and the thin
+// wrappers around the kernels of residual.cu, blocks.cu and krylov.cu.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace frk {
+
+int set_error(fr_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+namespace {
+
+void free_ctx(fr_ctx* c) {
+  if (!c) return;
+  cudaFree(c->hx);
+  cudaFree(c->hy);
+  cudaFree(c->blocks);
+  cudaFree(c->V);
+  cudaFree(c->z);
+  for (double* b : c->buf) cudaFree(b);
+  cudaFree(c->scal);
+  cudaFree(c->red.partials);
+  cudaFree(c->red.counter);
+  cudaFree(c->gd.H);
+  cudaFree(c->gd.cs);
+  cudaFree(c->gd.sn);
+  cudaFree(c->gd.g);
+  cudaFree(c->gd.y);
+  cudaFree(c->gd.h1);
+  cudaFree(c->gd.h2);
+  cudaFree(c->gd.invh);
+  cudaFree(c->gd.done);
+  cudaFree(c->gd.k);
+  cudaFree(c->gd.res);
+  cudaFree(c->gd.target);
+  cudaFreeHost(c->h_stat);
+  cudaFreeHost(c->h_scal);
+  delete c;
+}
+
+template <typename T>
+int dalloc(fr_ctx* c, T** p, size_t count) {
+  FRK_CUDA(c, cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+  FRK_CUDA(c, cudaMemset(*p, 0, count * sizeof(T)));
+  return FR_OK;
+}
+
+int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
+  c->opts = *o;
+  c->p = p;
+  c->n1 = p + 1;
+  c->np = c->n1 * c->n1;
+  c->nb = 4 * c->np;
+  c->nx = mesh->nx;
+  c->ny = mesh->ny;
+  c->ne = (long long)mesh->nx * mesh->ny;
+  c->ndof = c->ne * c->nb;
+  FRK_CUDA(c, cudaGetDevice(&c->device));
+  build_tables(p, &c->tab);
+  double* hx = new double[mesh->nx];
+  double* hy = new double[mesh->ny];
+  for (int i = 0; i < mesh->nx; ++i) hx[i] = mesh->x_edges[i + 1] - mesh->x_edges[i];
+  for (int i = 0; i < mesh->ny; ++i) hy[i] = mesh->y_edges[i + 1] - mesh->y_edges[i];
+  int rc = dalloc(c, &c->hx, mesh->nx);
+  if (rc == FR_OK) rc = dalloc(c, &c->hy, mesh->ny);
+  if (rc == FR_OK && cudaMemcpy(c->hx, hx, mesh->nx * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = set_error(c, FR_ERR_CUDA, "copying the mesh failed");
+  if (rc == FR_OK && cudaMemcpy(c->hy, hy, mesh->ny * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = set_error(c, FR_ERR_CUDA, "copying the mesh failed");
+  delete[] hx;
+  delete[] hy;
+  FRK_TRY(rc);
+  const size_t n = (size_t)c->ndof;
+  const int m = o->m_max;
+  FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * c->nb * c->nb));
+  FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
+  FRK_TRY(dalloc(c, &c->z, n));
+  for (double*& b : c->buf) FRK_TRY(dalloc(c, &b, n));
+  FRK_TRY(dalloc(c, &c->scal, S_COUNT));
+  FRK_TRY(dalloc(c, &c->red.partials, (size_t)kRedBlocks * kMaxVec));
+  FRK_TRY(dalloc(c, &c->red.counter, 1));
+  c->gd.ldh = m + 1;
+  FRK_TRY(dalloc(c, &c->gd.H, (size_t)(m + 1) * m));
+  FRK_TRY(dalloc(c, &c->gd.cs, m));
+  FRK_TRY(dalloc(c, &c->gd.sn, m));
+  FRK_TRY(dalloc(c, &c->gd.g, m + 1));
+  FRK_TRY(dalloc(c, &c->gd.y, m));
+  FRK_TRY(dalloc(c, &c->gd.h1, kMaxVec));
+  FRK_TRY(dalloc(c, &c->gd.h2, kMaxVec));
+  FRK_TRY(dalloc(c, &c->gd.invh, m + 1));
+  FRK_TRY(dalloc(c, &c->gd.done, 1));
+  FRK_TRY(dalloc(c, &c->gd.k, 1));
+  FRK_TRY(dalloc(c, &c->gd.res, 1));
+  FRK_TRY(dalloc(c, &c->gd.target, 1));
+  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), 4 * sizeof(int)));
+  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 8 * sizeof(double)));
+  FRK_CUDA(c, cudaDeviceSynchronize());
+  return FR_OK;
+}
+
+int check_vec(fr_ctx* ctx, const void* p, const char* name) {
+  if (!p) return set_error(ctx, FR_ERR_INVALID_ARG, "%s is NULL", name);
+  return FR_OK;
+}
+
+char g_static_err[256] = "invalid context";
+
+}  // namespace
+}  // namespace frk
+
+using namespace frk;
+
+extern "C" void fr_default_opts(fr_opts* o) {
+  if (!o) return;
+  o->gamma = 1.4;
+  o->m_max = 30;
+  o->eps_rel = 1e-7;
+  o->eps_fixed = 0.0;
+  o->block_eps_rel = 1e-7;
+  o->precond = 1;
+  o->gmres_m = 30;
+  o->gmres_max_restarts = 20;
+  o->tol_lin = 1e-8;
+}
+
+extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
+  if (!o) return;
+  o->tol_nl = 1e-6;
+  o->tol_lin = 1e-1;
+  o->dtau_init = 0.0;
+  o->dtau_max = 1e20;
+  o->max_iters = 200;
+  o->max_rejections = 30;
+  o->reject_above = 0.1;
+}
+
+extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opts, fr_ctx** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !mesh->x_edges || !mesh->y_edges || mesh->nx < 2 || mesh->ny < 2)
+    return FR_ERR_INVALID_ARG;
+  if (p < 2 || p > 4) return FR_ERR_UNSUPPORTED;
+  fr_opts o;
+  fr_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.m_max < 1 || o.m_max > kMaxVec - 1 || o.gmres_m < 1 || o.gmres_m > o.m_max ||
+      o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0))
+    return FR_ERR_INVALID_ARG;
+  for (int i = 0; i < mesh->nx; ++i)
+    if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;
+  for (int i = 0; i < mesh->ny; ++i)
+    if (!(mesh->y_edges[i + 1] > mesh->y_edges[i])) return FR_ERR_INVALID_ARG;
+  fr_ctx* c = new (std::nothrow) fr_ctx();
+  if (!c) return FR_ERR_CUDA;
+  const int rc = create(mesh, p, &o, c);
+  if (rc != FR_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return FR_OK;
+}
+
+extern "C" int fr_ctx_destroy(fr_ctx* ctx) {
+  free_ctx(ctx);
+  return FR_OK;
+}
+
+extern "C" const char* fr_last_error(const fr_ctx* ctx) { return ctx ? ctx->err : g_static_err; }
+
+extern "C" long long fr_ndof(const fr_ctx* ctx) { return ctx ? ctx->ndof : 0; }
+
+extern "C" int fr_residual(fr_ctx* ctx, const double* U, double* R, void* stream) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  FRK_TRY(check_vec(ctx, R, "R"));
+  if (U == R) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_residual: U and R alias");
+  return launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R, 0.0, nullptr, nullptr, nullptr,
+                         as_stream(stream));
+}
+
+extern "C" int fr_jv(fr_ctx* ctx, const double* U, const double* R0, const double* z, double shift,
+                     double* y, void* stream) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  FRK_TRY(check_vec(ctx, R0, "R0"));
+  FRK_TRY(check_vec(ctx, z, "z"));
+  FRK_TRY(check_vec(ctx, y, "y"));
+  if (y == U || y == R0 || y == z) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_jv: y aliases an input");
+  cudaStream_t s = as_stream(stream);
+  FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_NU2, s));
+  FRK_TRY(launch_sumsq(ctx, z, ctx->scal + S_NZ2, s));
+  return launch_residual(ctx, 1, U, z, R0, nullptr, y, shift, ctx->scal + S_NU2, ctx->scal + S_NZ2,
+                         nullptr, s);
+}
+
+extern "C" int ejacobi_factor(fr_ctx* ctx, const double* U, const double* R0, double shift,
+                              void* stream) {
+  (void)R0;
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  if (!std::isfinite(shift)) return set_error(ctx, FR_ERR_INVALID_ARG, "shift is not finite");
+  FRK_TRY(launch_block_factor(ctx, U, shift, as_stream(stream)));
+  ctx->blocks_valid = 1;
+  return FR_OK;
+}
+
+extern "C" int ejacobi_apply(fr_ctx* ctx, const double* r, double* z, void* stream) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, r, "r"));
+  FRK_TRY(check_vec(ctx, z, "z"));
+  if (r == z) return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply: r and z alias");
+  if (!ctx->blocks_valid) return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply before ejacobi_factor");
+  const int saved = ctx->opts.precond;
+  ctx->opts.precond = 1;
+  const int rc = launch_block_apply(ctx, const_cast<double*>(r), nullptr, z, nullptr, nullptr,
+                                    as_stream(stream));
+  ctx->opts.precond = saved;
+  return rc;
+}
+
+extern "C" int gmres_solve(fr_ctx* ctx, const double* U, const double* R0, double shift,
+                           const double* b, double* x, int m, double rtol, int max_restarts,
+                           fr_gmres_info* info, void* stream) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  FRK_TRY(check_vec(ctx, R0, "R0"));
+  FRK_TRY(check_vec(ctx, b, "b"));
+  FRK_TRY(check_vec(ctx, x, "x"));
+  if (m < 1 || m > ctx->opts.m_max) return set_error(ctx, FR_ERR_INVALID_ARG, "m = %d outside [1, %d]", m, ctx->opts.m_max);
+  if (max_restarts < 0 || !(rtol >= 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "bad rtol / max_restarts");
+  if (x == b || x == U || x == R0) return set_error(ctx, FR_ERR_INVALID_ARG, "gmres_solve: x aliases an input");
+  if (ctx->opts.precond && !ctx->blocks_valid)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "gmres_solve: call ejacobi_factor first (precond = 1)");
+  fr_gmres_info loc{};
+  const int rc = gmres_impl(ctx, U, R0, shift, b, x, m, rtol, max_restarts, false, &loc, as_stream(stream));
+  if (info) *info = loc;
+  return rc;
+}

@@ -1,0 +1,98 @@
+// Device helpers: Euler fluxes, Rusanov flux, deterministic reductions.
+#pragma once
+
+#include "internal.cuh"
+
+namespace frk {
+
+// Inviscid fluxes f (x) and g (y) of the 2D Euler equations (Sec. 2).
+__device__ __forceinline__ void euler_fluxes(const double q[4], double gam, double f[4],
+                                             double g[4]) {
+  const double rinv = 1.0 / q[0];
+  const double u = q[1] * rinv, v = q[2] * rinv;
+  const double p = (gam - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  f[0] = q[1];
+  f[1] = fma(q[1], u, p);
+  f[2] = q[2] * u;
+  f[3] = u * (q[3] + p);
+  g[0] = q[2];
+  g[1] = q[1] * v;
+  g[2] = fma(q[2], v, p);
+  g[3] = v * (q[3] + p);
+}
+
+// Normal flux along +x (dir 0) or +y (dir 1), plus |u_n| + c.
+__device__ __forceinline__ double normal_flux(const double q[4], int dir, double gam, double f[4]) {
+  const double rinv = 1.0 / q[0];
+  const double u = q[1] * rinv, v = q[2] * rinv;
+  const double p = (gam - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  const double un = dir == 0 ? u : v;
+  f[0] = q[1 + dir];
+  f[1] = q[1] * un + (dir == 0 ? p : 0.0);
+  f[2] = q[2] * un + (dir == 1 ? p : 0.0);
+  f[3] = un * (q[3] + p);
+  return fabs(un) + sqrt(gam * p * rinv);
+}
+
+// Rusanov common flux f_n = (f(qm)+f(qp))/2 - lam/2 (qp - qm),
+// lam = max(|u_n|+c) over both sides; qm is the side the +x/+y normal leaves.
+__device__ __forceinline__ void rusanov(const double qm[4], const double qp[4], int dir, double gam,
+                                        double out[4]) {
+  double fm[4], fp[4];
+  const double am = normal_flux(qm, dir, gam, fm);
+  const double ap = normal_flux(qp, dir, gam, fp);
+  const double lam = fmax(am, ap);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * lam * (qp[v] - qm[v]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order; result valid in thread 0. `sh` holds 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += sh[i];
+  }
+  return s;
+}
+
+// Called by every thread of every block after thread 0 wrote its partials.
+// Returns true in the last block to arrive.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return am_last;
+}
+
+// In the last block: out[i] = sum over blocks b (ascending) of partials[b][i], i < nvec.
+// Resets the counter.  Needs blockDim.x >= 32.
+__device__ __forceinline__ void finish_sums(const Reduce& red, int nvec, double* out) {
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < nvec; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + (size_t)b * kMaxVec + i);
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+  if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+}  // namespace frk

@@ -1,0 +1,136 @@
+// Internal declarations shared by the translation units of libfrjfnk.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "frjfnk.h"
+
+namespace frk {
+
+constexpr int kMaxN = 5;          // p <= 4
+constexpr int kThreads = 256;     // default block size of the vector kernels
+constexpr int kMaxVec = 32;       // largest Krylov basis slice handled per call (m_max + 1)
+constexpr int kVecBlocks = 1216;  // 8 x 152 SMs: grid of the streaming vector kernels
+constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
+
+// 1D tables of Sec. 3 on Gauss-Legendre points, passed to kernels by value.
+//   Dt[i][k] = D_ik - g_L'(xi_i) l_k(-1) - g_R'(xi_i) l_k(+1)
+// folds the local-flux traces F^l(+-1) into the derivative matrix, so the
+// corrected divergence is  sum_k Dt_ik F_k + g_L'_i F^num_L + g_R'_i F^num_R.
+struct Tables {
+  double Dt[kMaxN][kMaxN];
+  double lm[kMaxN];   // l_k(-1)
+  double lp[kMaxN];   // l_k(+1)
+  double dgL[kMaxN];  // g_L'(xi_i)
+  double dgR[kMaxN];  // g_R'(xi_i)
+  double xi[kMaxN];   // solution points
+  double w[kMaxN];    // quadrature weights
+};
+
+// Deterministic two-stage reduction scratch: per-block partial sums and a
+// completion counter (the last block to finish sums the partials in a fixed
+// order and resets the counter).
+struct Reduce {
+  double* partials;   // [kRedBlocks][kMaxVec]
+  unsigned* counter;
+};
+
+// GMRES cycle state kept on the device so a whole cycle is launched without
+// host round trips.
+struct GmresDev {
+  double* H;        // (m_max+1) x m_max, column-major: H[j*(m_max+1) + i]
+  double* cs;       // Givens cosines [m_max]
+  double* sn;       // Givens sines [m_max]
+  double* g;        // rotated rhs [m_max+1]
+  double* y;        // least-squares solution [m_max]
+  double* h1;       // first Gram-Schmidt coefficients [kMaxVec]
+  double* h2;       // second (re-orthogonalisation) coefficients [kMaxVec]
+  double* invh;     // 1/||v_j|| of the not-yet-normalised basis vector j [m_max+1]
+  int* done;        // cycle finished (converged or breakdown)
+  int* k;           // iterations done in this cycle
+  double* res;      // |g_k|
+  double* target;   // rtol * ||b||
+  int ldh;          // m_max + 1
+};
+
+// Device scalars (sums of squares) used by the FD step and GMRES.
+enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_COUNT };
+
+}  // namespace frk
+
+struct fr_ctx {
+  int device = 0;
+  int nx = 0, ny = 0, p = 0, n1 = 0, np = 0, nb = 0;
+  long long ne = 0, ndof = 0;
+  fr_opts opts{};
+  frk::Tables tab{};
+  double* hx = nullptr;      // [nx] element widths (device)
+  double* hy = nullptr;      // [ny] element heights (device)
+  double* blocks = nullptr;  // [ne][nb][nb] inverse blocks, column-major per element
+  int blocks_valid = 0;
+  double* V = nullptr;       // (m_max+1) x ndof Krylov basis
+  double* z = nullptr;       // preconditioned basis vector
+  double* buf[16] = {};      // stepper buffers, ndof each
+  double* scal = nullptr;    // frk::S_COUNT device scalars
+  frk::Reduce red{};
+  frk::GmresDev gd{};
+  int* h_stat = nullptr;     // pinned host mirror: done, k
+  double* h_scal = nullptr;  // pinned host mirror of a few doubles
+  char err[512] = {0};
+};
+
+namespace frk {
+
+int set_error(fr_ctx* ctx, int code, const char* fmt, ...);
+
+#define FRK_CUDA(ctx, call)                                                           \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return ::frk::set_error((ctx), FR_ERR_CUDA, "%s failed: %s (%s:%d)", #call,     \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);           \
+  } while (0)
+
+#define FRK_LAUNCHED(ctx)                                                             \
+  do {                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                             \
+    if (e_ != cudaSuccess)                                                           \
+      return ::frk::set_error((ctx), FR_ERR_CUDA, "kernel launch failed: %s (%s:%d)", \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);           \
+  } while (0)
+
+#define FRK_TRY(expr)         \
+  do {                        \
+    int r_ = (expr);          \
+    if (r_ != FR_OK) return r_; \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- launchers implemented in the .cu files --------------------------------
+// residual.cu: mode 0: out = R(U); mode 1: out = A z; mode 2: out = b - A z
+int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
+                    const double* b, double* out, double shift, const double* nU2,
+                    const double* nz2, const int* done, cudaStream_t s);
+// blocks.cu
+int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
+int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
+                       const int* done, cudaStream_t s);
+int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s);
+// krylov.cu
+int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s);
+int launch_lincomb(fr_ctx* ctx, double* out, int nterms, const double* const* xs,
+                   const double* coefs, double* sumsq, cudaStream_t s);
+int launch_copy(fr_ctx* ctx, double* dst, const double* src, cudaStream_t s);
+int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s);
+int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+               double* x, int m, double rtol, int max_restarts, bool x_is_zero,
+               fr_gmres_info* info, cudaStream_t s);
+// tables.cu
+void build_tables(int p, Tables* t);
+
+}  // namespace frk

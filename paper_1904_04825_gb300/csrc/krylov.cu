@@ -1,0 +1,300 @@
+// Restarted GMRES(m) of Sec. 4.5 on the device.
+//
+// Arnoldi uses classical Gram-Schmidt with one re-orthogonalisation pass
+// (CGS2): every pass is one multi-dot kernel and one multi-AXPY kernel over
+// the whole basis slice, with deterministic two-stage reductions.  The
+// Hessenberg column, the Givens rotation and the convergence test run in a
+// one-warp kernel, so a cycle of m iterations is launched without any host
+// round trip: once the device sets `done`, the remaining kernels of the
+// cycle return at once.  The host reads the cycle status once per restart.
+#include <cmath>
+
+#include "device.cuh"
+
+namespace frk {
+namespace {
+
+unsigned vgrid(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > kVecBlocks) g = kVecBlocks;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+__global__ void k_sumsq(const double* __restrict__ x, long long n, double* out, Reduce red) {
+  __shared__ double sh[32];
+  double ss = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    ss = fma(x[i], x[i], ss);
+  const double bs = block_sum(ss, sh);
+  if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+  if (last_block(red.counter)) finish_sums(red, 1, out);
+}
+
+struct Lincomb {
+  const double* x[8];
+  double c[8];
+  int n;
+};
+
+// out = sum_t c_t x_t (out may alias any x_t), optional sum of squares of out
+__global__ void k_lincomb(double* out, long long len, const Lincomb lc, double* sumsq, Reduce red) {
+  __shared__ double sh[32];
+  double ss = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = lc.c[0] * lc.x[0][i];
+    for (int t = 1; t < lc.n; ++t) v = fma(lc.c[t], lc.x[t][i], v);
+    out[i] = v;
+    ss = fma(v, v, ss);
+  }
+  if (sumsq) {
+    const double bs = block_sum(ss, sh);
+    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+    if (last_block(red.counter)) finish_sums(red, 1, sumsq);
+  }
+}
+
+// out[i] = <V_i, w>, i < nvec (nvec <= kMaxVec); chunks of 8 vectors per sweep
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long long ldv, int nvec,
+                                              const double* __restrict__ w, long long n, double* out,
+                                              Reduce red, const int* done) {
+  __shared__ double sh[32];
+  if (done && *done) return;
+  for (int c0 = 0; c0 < nvec; c0 += 8) {
+    const int nc = min(8, nvec - c0);
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (long long)gridDim.x * blockDim.x) {
+      const double wr = w[r];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < nc) acc[i] = fma(V[(c0 + i) * ldv + r], wr, acc[i]);
+    }
+    for (int i = 0; i < nc; ++i) {
+      const double bs = block_sum(acc[i], sh);
+      if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec + c0 + i] = bs;
+    }
+  }
+  if (last_block(red.counter)) finish_sums(red, nvec, out);
+}
+
+// w -= sum_i h_i V_i, optional sum of squares of the new w
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const double* __restrict__ V,
+                                                long long ldv, int nvec, const double* h,
+                                                long long n, double* sumsq, Reduce red,
+                                                const int* done) {
+  __shared__ double sh[32];
+  __shared__ double hs[kMaxVec];
+  if (done && *done) return;
+  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double ss = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    double v = w[r];
+    for (int i = 0; i < nvec; ++i) v = fma(-hs[i], V[i * ldv + r], v);
+    w[r] = v;
+    ss = fma(v, v, ss);
+  }
+  if (sumsq) {
+    const double bs = block_sum(ss, sh);
+    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+    if (last_block(red.counter)) finish_sums(red, 1, sumsq);
+  }
+}
+
+// start of a cycle: beta = ||r||, g = beta e_1, done if beta <= rtol ||b||
+__global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, double rtol, int m) {
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(*nr2);
+  const double target = rtol * sqrt(*nb2);
+  for (int i = 0; i <= m; ++i) gd.g[i] = 0.0;
+  gd.g[0] = beta;
+  *gd.target = target;
+  *gd.res = beta;
+  *gd.k = 0;
+  *gd.done = (beta <= target) ? 1 : 0;
+  gd.invh[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// Hessenberg column j, Givens rotations, residual estimate, convergence
+__global__ void k_givens(GmresDev gd, int j, const double* nw2) {
+  if (threadIdx.x != 0) return;
+  if (*gd.done) return;
+  double* Hj = gd.H + (size_t)j * gd.ldh;
+  for (int i = 0; i <= j; ++i) Hj[i] = gd.h1[i] + gd.h2[i];
+  const double hn = sqrt(*nw2);
+  Hj[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = gd.cs[i] * Hj[i] + gd.sn[i] * Hj[i + 1];
+    Hj[i + 1] = -gd.sn[i] * Hj[i] + gd.cs[i] * Hj[i + 1];
+    Hj[i] = t;
+  }
+  const double den = hypot(Hj[j], Hj[j + 1]);
+  const double c = den > 0.0 ? Hj[j] / den : 1.0;
+  const double s = den > 0.0 ? Hj[j + 1] / den : 0.0;
+  gd.cs[j] = c;
+  gd.sn[j] = s;
+  Hj[j] = den;
+  Hj[j + 1] = 0.0;
+  gd.g[j + 1] = -s * gd.g[j];
+  gd.g[j] = c * gd.g[j];
+  *gd.k = j + 1;
+  const double res = fabs(gd.g[j + 1]);
+  *gd.res = res;
+  gd.invh[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (res <= *gd.target || hn == 0.0 || !(res == res)) *gd.done = 1;
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k)
+__global__ void k_backsub(GmresDev gd) {
+  if (threadIdx.x != 0) return;
+  const int k = *gd.k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gd.g[i];
+    for (int l = i + 1; l < k; ++l) s -= gd.H[(size_t)l * gd.ldh + i] * gd.y[l];
+    gd.y[i] = s / gd.H[(size_t)i * gd.ldh + i];
+  }
+}
+
+__global__ void k_copy(double* dst, const double* src, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void k_fill(double* dst, double v, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+
+}  // namespace
+
+int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s) {
+  k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red);
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int launch_lincomb(fr_ctx* ctx, double* out, int nterms, const double* const* xs,
+                   const double* coefs, double* sumsq, cudaStream_t s) {
+  if (nterms < 1 || nterms > 8) return set_error(ctx, FR_ERR_INVALID_ARG, "lincomb of %d terms", nterms);
+  Lincomb lc{};
+  lc.n = nterms;
+  for (int t = 0; t < nterms; ++t) {
+    lc.x[t] = xs[t];
+    lc.c[t] = coefs[t];
+  }
+  k_lincomb<<<vgrid(ctx->ndof), kThreads, 0, s>>>(out, ctx->ndof, lc, sumsq, ctx->red);
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int launch_copy(fr_ctx* ctx, double* dst, const double* src, cudaStream_t s) {
+  k_copy<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, src, ctx->ndof);
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s) {
+  k_fill<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, v, ctx->ndof);
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+               double* x, int m, double rtol, int max_restarts, bool x_is_zero,
+               fr_gmres_info* info, cudaStream_t s) {
+  const long long n = ctx->ndof;
+  double* sc = ctx->scal;
+  GmresDev& gd = ctx->gd;
+  double* V = ctx->V;
+  fr_gmres_info loc{};
+  // ||U|| for the FD step, ||b|| for the stopping test
+  FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
+  FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
+  if (!x_is_zero) {
+    FRK_TRY(launch_sumsq(ctx, x, sc + S_NX2, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, sc + S_NB2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 1, sc + S_NX2, sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_scal[0] == 0.0) {  // b = 0: the solution is x = 0
+      FRK_TRY(launch_fill(ctx, x, 0.0, s));
+      loc.converged = 1;
+      if (info) *info = loc;
+      return FR_OK;
+    }
+    x_is_zero = ctx->h_scal[1] == 0.0;
+  }
+  int cycles_iterated = 0;
+  int status = FR_ERR_NOT_CONVERGED;
+  for (int cycle = 0; cycle <= max_restarts; ++cycle) {
+    // r = b - A x into V[0]
+    if (cycle == 0 && x_is_zero) {
+      FRK_TRY(launch_copy(ctx, V, b, s));
+    } else {
+      FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s));
+      FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_NU2, sc + S_NZ2, nullptr, s));
+    }
+    FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
+    k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m);
+    FRK_LAUNCHED(ctx);
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      // v_j = r_j / ||r_j|| (written back), z = M^{-1} v_j, ||z||^2
+      FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s));
+      // w = A z
+      FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_NU2, sc + S_NZ2,
+                              gd.done, s));
+      // CGS2
+      k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, ctx->red, gd.done);
+      k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, nullptr, ctx->red, gd.done);
+      k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, ctx->red, gd.done);
+      k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done);
+      k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2);
+      FRK_LAUNCHED(ctx);
+    }
+    k_backsub<<<1, 32, 0, s>>>(gd);
+    FRK_LAUNCHED(ctx);
+    FRK_TRY(launch_solution_update(ctx, x, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat, gd.k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, gd.res, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 1, gd.target, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 2, sc + S_NB2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaStreamSynchronize(s));
+    const int k = ctx->h_stat[0];
+    const double res = ctx->h_scal[0], target = ctx->h_scal[1], bn = std::sqrt(ctx->h_scal[2]);
+    if (!std::isfinite(res) || !std::isfinite(bn)) {
+      if (info) *info = loc;
+      return set_error(ctx, FR_ERR_NONFINITE, "GMRES residual is not finite");
+    }
+    if (bn == 0.0) {  // b = 0 and x = 0 on entry
+      loc.converged = 1;
+      loc.relres = 0.0;
+      status = FR_OK;
+      break;
+    }
+    loc.iters += k;
+    if (k > 0) ++cycles_iterated;
+    loc.relres = res / bn;
+    if (res <= target) {
+      loc.converged = 1;
+      status = FR_OK;
+      break;
+    }
+  }
+  loc.restarts = cycles_iterated > 0 ? cycles_iterated - 1 : 0;
+  if (info) *info = loc;
+  if (status != FR_OK)
+    set_error(ctx, FR_ERR_NOT_CONVERGED, "GMRES stopped after %d iterations at relres %.3e",
+              loc.iters, loc.relres);
+  return status;
+}
+
+}  // namespace frk

@@ -1,0 +1,379 @@
+// Host control of the time integrators of Sec. 4 (ROW, ESDIRK with
+// pseudo-transient continuation, BDF2).  Every vector operation is a kernel
+// on the caller's stream; the host reads back only the scalars the method
+// branches on (GMRES cycle status, ||F|| of each pseudo step).
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace frk {
+namespace {
+
+// ---- coefficient sets (the paper names them but prints none) --------------
+// Rosenbrock sets in the form of Eq. Rosenbrock_General: omega (= gamma),
+// a (stage arguments), c (stage right-hand sides), m (solution weights).
+struct RowTab {
+  int s = 0;
+  double gamma = 0.0;
+  double a[6][6] = {};
+  double c[6][6] = {};
+  double m[6] = {};
+};
+
+// Convert the Hairer-Wanner form (alpha, Gamma, b) to (a, c, m):
+// a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b Gamma^-1.
+void from_alpha(int s, const double al[6][6], const double G[6][6], const double* b, RowTab* t) {
+  double Gi[6][6] = {};
+  // inverse of the lower-triangular Gamma by forward substitution
+  for (int j = 0; j < s; ++j) {
+    for (int i = 0; i < s; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= G[i][k] * Gi[k][j];
+      Gi[i][j] = v / G[i][i];
+    }
+  }
+  t->s = s;
+  t->gamma = G[0][0];
+  for (int i = 0; i < s; ++i) {
+    for (int j = 0; j < s; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < s; ++k) v += al[i][k] * Gi[k][j];
+      t->a[i][j] = j < i ? v : 0.0;
+      t->c[i][j] = j < i ? -Gi[i][j] : 0.0;
+    }
+  }
+  for (int j = 0; j < s; ++j) {
+    double v = 0.0;
+    for (int i = 0; i < s; ++i) v += b[i] * Gi[i][j];
+    t->m[j] = v;
+  }
+}
+
+RowTab row_tableau(int order) {
+  RowTab t;
+  double al[6][6] = {}, G[6][6] = {}, b[6] = {};
+  if (order == 2) {
+    // 3 stages, order 2, stiffly accurate: W-order 2, stability function
+    // matching exp(z) to third order (gamma: root of g^3 - 3g^2 + 3g/2 - 1/6).
+    double g = 0.4;
+    for (int it = 0; it < 60; ++it) g -= (g * g * g - 3 * g * g + 1.5 * g - 1.0 / 6.0) / (3 * g * g - 6 * g + 1.5);
+    const double a21 = 2 * g, b2 = (0.5 - g) / a21, g21 = (g * g - g) / b2, b3 = g, b1 = 1.0 - b2 - b3;
+    const double a31 = b1 / (1.0 - g), a32 = b2 / (1.0 - g);
+    al[1][0] = a21; al[2][0] = a31; al[2][1] = a32;
+    G[0][0] = G[1][1] = G[2][2] = g;
+    G[1][0] = g21; G[2][0] = b1 - a31; G[2][1] = b2 - a32;
+    b[0] = b1; b[1] = b2; b[2] = b3;
+    from_alpha(3, al, G, b, &t);
+  } else if (order == 3) {
+    // ROS34PW2 (Rang & Angermann 2005)
+    const double g = 4.3586652150845900e-01;
+    al[1][0] = 8.7173304301691801e-01;
+    al[2][0] = 8.4457060015369423e-01; al[2][1] = -1.1299064236484185e-01;
+    al[3][0] = 0.0; al[3][1] = 0.0; al[3][2] = 1.0;
+    for (int i = 0; i < 4; ++i) G[i][i] = g;
+    G[1][0] = -8.7173304301691801e-01;
+    G[2][0] = -9.0338057013044082e-01; G[2][1] = 5.4180672388095326e-02;
+    G[3][0] = 2.4212380706095346e-01; G[3][1] = -1.2232505839045147e+00; G[3][2] = 5.4526025533510214e-01;
+    b[0] = 2.4212380706095346e-01; b[1] = -1.2232505839045147e+00;
+    b[2] = 1.5452602553351020e+00; b[3] = g;
+    from_alpha(4, al, G, b, &t);
+  } else {
+    // RODASP (Steinebach 1995), entered in the transformed form
+    t.s = 6;
+    t.gamma = 0.25;
+    const double r5[4] = {-7.170454962423024, -4.741636671481785, -16.31002631330971, -1.062004044111401};
+    t.a[1][0] = 3.0;
+    t.a[2][0] = 1.831036793486759; t.a[2][1] = 0.4955183967433795;
+    t.a[3][0] = 2.304376582692669; t.a[3][1] = -0.05249275245743001; t.a[3][2] = -1.176798761832782;
+    for (int j = 0; j < 4; ++j) { t.a[4][j] = r5[j]; t.a[5][j] = r5[j]; t.m[j] = r5[j]; }
+    t.a[5][4] = 1.0;
+    t.m[4] = 1.0; t.m[5] = 1.0;
+    t.c[1][0] = -12.0;
+    t.c[2][0] = -8.791795173947035; t.c[2][1] = -2.207865586973518;
+    t.c[3][0] = 10.81793056857153; t.c[3][1] = 6.780270611428266; t.c[3][2] = 19.53485944642410;
+    t.c[4][0] = 34.19095006749676; t.c[4][1] = 15.49671153725963; t.c[4][2] = 54.74760875964130;
+    t.c[4][3] = 14.16005392148534;
+    t.c[5][0] = 34.62605830930532; t.c[5][1] = 15.30084976114473; t.c[5][2] = 56.99955578662667;
+    t.c[5][3] = 18.40807009793095; t.c[5][4] = -5.714285714285717;
+  }
+  return t;
+}
+
+struct EsdirkTab {
+  int s = 0;
+  double A[6][6] = {};
+  double b[6] = {};
+};
+
+EsdirkTab esdirk_tableau(int order) {
+  EsdirkTab t;
+  if (order == 2) {
+    const double g = 1.0 - std::sqrt(2.0) / 2.0, r = std::sqrt(2.0) / 4.0;
+    t.s = 3;
+    t.A[1][0] = g; t.A[1][1] = g;
+    t.A[2][0] = r; t.A[2][1] = r; t.A[2][2] = g;
+  } else if (order == 3) {
+    const double g = 1767732205903.0 / 4055673282236.0;
+    t.s = 4;
+    t.A[1][0] = g; t.A[1][1] = g;
+    t.A[2][0] = 2746238789719.0 / 10658868560708.0; t.A[2][1] = -640167445237.0 / 6845629431997.0;
+    t.A[2][2] = g;
+    t.A[3][0] = 1471266399579.0 / 7840856788654.0; t.A[3][1] = -4482444167858.0 / 7529755066697.0;
+    t.A[3][2] = 11266239266428.0 / 11593286722821.0; t.A[3][3] = g;
+  } else {
+    const double q = 0.25;
+    t.s = 6;
+    t.A[1][0] = q; t.A[1][1] = q;
+    t.A[2][0] = 8611.0 / 62500.0; t.A[2][1] = -1743.0 / 31250.0; t.A[2][2] = q;
+    t.A[3][0] = 5012029.0 / 34652500.0; t.A[3][1] = -654441.0 / 2922500.0;
+    t.A[3][2] = 174375.0 / 388108.0; t.A[3][3] = q;
+    t.A[4][0] = 15267082809.0 / 155376265600.0; t.A[4][1] = -71443401.0 / 120774400.0;
+    t.A[4][2] = 730878875.0 / 902184768.0; t.A[4][3] = 2285395.0 / 8070912.0; t.A[4][4] = q;
+    t.A[5][0] = 82889.0 / 524892.0; t.A[5][1] = 0.0; t.A[5][2] = 15625.0 / 83664.0;
+    t.A[5][3] = 69875.0 / 102672.0; t.A[5][4] = -2260.0 / 8211.0; t.A[5][5] = q;
+  }
+  for (int j = 0; j < t.s; ++j) t.b[j] = t.A[t.s - 1][j];
+  return t;
+}
+
+// buffer roles
+enum {
+  B_R0 = 0, B_RHS, B_STAGE, B_RSTAGE, B_CONST, B_F, B_DQ, B_Q, B_RQ, B_NEW,
+  B_Y0 = 10  // 6 stage vectors B_Y0 .. B_Y0+5
+};
+
+int read_scalar(fr_ctx* ctx, const double* dev, double* host, cudaStream_t s) {
+  FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 3, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  *host = ctx->h_scal[3];
+  return FR_OK;
+}
+
+// Linear solve with zero initial guess: x = A^{-1} b at tolerance tol.
+int solve(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b, double* x,
+          double tol, fr_step_stats* st, fr_gmres_info* info, cudaStream_t s) {
+  FRK_TRY(launch_fill(ctx, x, 0.0, s));
+  const int rc = gmres_impl(ctx, U, R0, shift, b, x, ctx->opts.gmres_m, tol,
+                            ctx->opts.gmres_max_restarts, true, info, s);
+  st->gmres_iters += info->iters;
+  st->gmres_calls += 1;
+  if (rc == FR_ERR_NOT_CONVERGED) {
+    st->converged = 0;
+    return FR_OK;  // the caller decides (ROW keeps going, PTC may reject)
+  }
+  return rc;
+}
+
+// Pseudo-transient continuation for F(q) = (q - cst)/(omega dt) - R(q) = 0
+// (Sec. 4.4); q (in/out) starts from the given iterate; Rq receives R(q).
+int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, double* Rq,
+        const fr_ptc_opts& po, fr_step_stats* st, cudaStream_t s) {
+  double* F = ctx->buf[B_F];
+  double* dq = ctx->buf[B_DQ];
+  double* nF2 = ctx->scal + S_NF2;
+  auto eval_F = [&](double* Fn) -> int {
+    FRK_TRY(launch_residual(ctx, 0, q, nullptr, nullptr, nullptr, Rq, 0.0, nullptr, nullptr, nullptr, s));
+    st->residual_evals += 1;
+    const double* xs[3] = {q, cst, Rq};
+    const double cs[3] = {1.0 / omega_dt, -1.0 / omega_dt, -1.0};
+    FRK_TRY(launch_lincomb(ctx, F, 3, xs, cs, nF2, s));
+    double v;
+    FRK_TRY(read_scalar(ctx, nF2, &v, s));
+    *Fn = std::sqrt(v);
+    return FR_OK;
+  };
+  double Fn;
+  FRK_TRY(eval_F(&Fn));
+  if (!std::isfinite(Fn)) return set_error(ctx, FR_ERR_NONFINITE, "||F|| is not finite");
+  const double F0 = Fn;
+  double dtau = po.dtau_init > 0.0 ? po.dtau_init : dt;
+  double dtau_max = po.dtau_max;
+  int k = 0, rejections = 0;
+  while (F0 > 0.0 && Fn / F0 >= po.tol_nl) {
+    if (k >= po.max_iters) {
+      st->converged = 0;
+      return set_error(ctx, FR_ERR_NOT_CONVERGED, "PTC reached %d pseudo steps (||F||/||F0|| = %.3e)",
+                       k, Fn / F0);
+    }
+    const double shift = 1.0 / dtau + 1.0 / omega_dt;
+    if (ctx->opts.precond) FRK_TRY(launch_block_factor(ctx, q, shift, s));
+    ctx->blocks_valid = ctx->opts.precond;
+    // b = -F into B_RHS
+    const double* xs[1] = {F};
+    const double cs[1] = {-1.0};
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_RHS], 1, xs, cs, nullptr, s));
+    fr_gmres_info info{};
+    const int conv_before = st->converged;
+    FRK_TRY(solve(ctx, q, Rq, shift, ctx->buf[B_RHS], dq, po.tol_lin, st, &info, s));
+    st->converged = conv_before;  // an inexact inner solve is not a failure of the step
+    if (info.relres > po.reject_above) {
+      ++rejections;
+      ++st->rejections;
+      if (rejections > po.max_rejections) {
+        st->converged = 0;
+        return set_error(ctx, FR_ERR_PTC_STALLED, "PTC: %d rejected pseudo steps", rejections);
+      }
+      dtau_max *= 0.5;
+      dtau = std::fmin(dtau, dtau_max);
+      continue;
+    }
+    const double* xq[2] = {q, dq};
+    const double cq[2] = {1.0, 1.0};
+    FRK_TRY(launch_lincomb(ctx, q, 2, xq, cq, nullptr, s));
+    double Fnew;
+    FRK_TRY(eval_F(&Fnew));
+    if (!std::isfinite(Fnew)) return set_error(ctx, FR_ERR_NONFINITE, "||F|| is not finite");
+    dtau = Fnew > 0.0 ? std::fmin(dtau * Fn / Fnew, dtau_max) : dtau_max;
+    Fn = Fnew;
+    ++k;
+    ++st->ptc_iters;
+  }
+  return FR_OK;
+}
+
+}  // namespace
+}  // namespace frk
+
+using namespace frk;
+
+extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_stats* stats,
+                        void* stream) {
+  if (!ctx || !U) return set_error(ctx, FR_ERR_INVALID_ARG, "step_row: null argument");
+  if (scheme < 2 || scheme > 4) return set_error(ctx, FR_ERR_INVALID_ARG, "step_row: scheme %d", scheme);
+  if (!(dt > 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "step_row: dt must be > 0");
+  cudaStream_t s = as_stream(stream);
+  const RowTab t = row_tableau(scheme);
+  fr_step_stats st{};
+  st.converged = 1;
+  const double shift = 1.0 / (t.gamma * dt);
+  double* R0 = ctx->buf[B_R0];
+  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R0, 0.0, nullptr, nullptr, nullptr, s));
+  st.residual_evals += 1;
+  if (ctx->opts.precond) {
+    FRK_TRY(launch_block_factor(ctx, U, shift, s));
+    ctx->blocks_valid = 1;
+  }
+  for (int i = 0; i < t.s; ++i) {
+    double* Yi = ctx->buf[B_Y0 + i];
+    const double* Ri = R0;
+    bool any_a = false;
+    for (int j = 0; j < i; ++j) any_a |= t.a[i][j] != 0.0;
+    if (i > 0 && any_a) {
+      const double* xs[7];
+      double cs[7];
+      xs[0] = U; cs[0] = 1.0;
+      for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.a[i][j]; }
+      FRK_TRY(launch_lincomb(ctx, ctx->buf[B_STAGE], i + 1, xs, cs, nullptr, s));
+      FRK_TRY(launch_residual(ctx, 0, ctx->buf[B_STAGE], nullptr, nullptr, nullptr, ctx->buf[B_RSTAGE],
+                              0.0, nullptr, nullptr, nullptr, s));
+      st.residual_evals += 1;
+      Ri = ctx->buf[B_RSTAGE];
+    }
+    const double* b = Ri;
+    if (i > 0) {
+      const double* xs[7];
+      double cs[7];
+      xs[0] = Ri; cs[0] = 1.0;
+      for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.c[i][j] / dt; }
+      FRK_TRY(launch_lincomb(ctx, ctx->buf[B_RHS], i + 1, xs, cs, nullptr, s));
+      b = ctx->buf[B_RHS];
+    }
+    fr_gmres_info info{};
+    FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
+  }
+  // q^{n+1} = q^n + sum m_j Y_j, checked before it overwrites U
+  const double* xs[7];
+  double cs[7];
+  xs[0] = U; cs[0] = 1.0;
+  for (int j = 0; j < t.s; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.m[j]; }
+  FRK_TRY(launch_lincomb(ctx, ctx->buf[B_NEW], t.s + 1, xs, cs, ctx->scal + S_NX2, s));
+  double nn;
+  FRK_TRY(read_scalar(ctx, ctx->scal + S_NX2, &nn, s));
+  if (stats) *stats = st;
+  if (!std::isfinite(nn)) return set_error(ctx, FR_ERR_NONFINITE, "step_row: new state not finite");
+  FRK_TRY(launch_copy(ctx, U, ctx->buf[B_NEW], s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  if (!st.converged) return set_error(ctx, FR_ERR_NOT_CONVERGED, "step_row: a stage solve did not converge");
+  return FR_OK;
+}
+
+extern "C" int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts* ptc_opts,
+                           fr_step_stats* stats, void* stream) {
+  if (!ctx || !U) return set_error(ctx, FR_ERR_INVALID_ARG, "step_esdirk: null argument");
+  if (scheme < 2 || scheme > 4) return set_error(ctx, FR_ERR_INVALID_ARG, "step_esdirk: scheme %d", scheme);
+  if (!(dt > 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "step_esdirk: dt must be > 0");
+  fr_ptc_opts po;
+  fr_default_ptc_opts(&po);
+  if (ptc_opts) po = *ptc_opts;
+  cudaStream_t s = as_stream(stream);
+  const EsdirkTab t = esdirk_tableau(scheme);
+  const double omega = t.A[1][1];
+  fr_step_stats st{};
+  st.converged = 1;
+  // stage residuals R(q_j) in B_Y0 + j
+  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, ctx->buf[B_Y0], 0.0, nullptr, nullptr,
+                          nullptr, s));
+  st.residual_evals += 1;
+  double* q = ctx->buf[B_Q];
+  FRK_TRY(launch_copy(ctx, q, U, s));
+  int rc = FR_OK;
+  for (int i = 1; i < t.s; ++i) {
+    const double* xs[7];
+    double cs[7];
+    xs[0] = U; cs[0] = 1.0;
+    for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = dt * t.A[i][j]; }
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_CONST], i + 1, xs, cs, nullptr, s));
+    rc = ptc(ctx, ctx->buf[B_CONST], omega * dt, dt, q, ctx->buf[B_Y0 + i], po, &st, s);
+    if (rc != FR_OK && rc != FR_ERR_NOT_CONVERGED) {
+      if (stats) *stats = st;
+      return rc;
+    }
+  }
+  const double* xs[7];
+  double cs[7];
+  xs[0] = U; cs[0] = 1.0;
+  for (int j = 0; j < t.s; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = dt * t.b[j]; }
+  FRK_TRY(launch_lincomb(ctx, ctx->buf[B_NEW], t.s + 1, xs, cs, ctx->scal + S_NX2, s));
+  double nn;
+  FRK_TRY(read_scalar(ctx, ctx->scal + S_NX2, &nn, s));
+  if (stats) *stats = st;
+  if (!std::isfinite(nn)) return set_error(ctx, FR_ERR_NONFINITE, "step_esdirk: new state not finite");
+  FRK_TRY(launch_copy(ctx, U, ctx->buf[B_NEW], s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  if (!st.converged) return set_error(ctx, FR_ERR_NOT_CONVERGED, "step_esdirk: a stage did not converge");
+  return FR_OK;
+}
+
+extern "C" int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
+                         const fr_ptc_opts* ptc_opts, fr_step_stats* stats, void* stream) {
+  if (!ctx || !U || !U_prev) return set_error(ctx, FR_ERR_INVALID_ARG, "step_bdf2: null argument");
+  if (!(dt > 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "step_bdf2: dt must be > 0");
+  fr_ptc_opts po;
+  fr_default_ptc_opts(&po);
+  if (ptc_opts) po = *ptc_opts;
+  cudaStream_t s = as_stream(stream);
+  fr_step_stats st{};
+  st.converged = 1;
+  double omega, a1, a2;
+  if (first_step) { omega = 1.0; a1 = 1.0; a2 = 0.0; }
+  else { omega = 2.0 / 3.0; a1 = 4.0 / 3.0; a2 = -1.0 / 3.0; }
+  {
+    const double* xs[2] = {U, U_prev};
+    const double cs[2] = {a1, a2};
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_CONST], first_step ? 1 : 2, xs, cs, nullptr, s));
+  }
+  double* q = ctx->buf[B_Q];
+  FRK_TRY(launch_copy(ctx, q, U, s));
+  const int rc = ptc(ctx, ctx->buf[B_CONST], omega * dt, dt, q, ctx->buf[B_RQ], po, &st, s);
+  if (stats) *stats = st;
+  if (rc != FR_OK && rc != FR_ERR_NOT_CONVERGED) return rc;
+  FRK_TRY(launch_sumsq(ctx, q, ctx->scal + S_NX2, s));
+  double nn;
+  FRK_TRY(read_scalar(ctx, ctx->scal + S_NX2, &nn, s));
+  if (!std::isfinite(nn)) return set_error(ctx, FR_ERR_NONFINITE, "step_bdf2: new state not finite");
+  FRK_TRY(launch_copy(ctx, U_prev, U, s));
+  FRK_TRY(launch_copy(ctx, U, q, s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  if (rc != FR_OK || !st.converged) return set_error(ctx, FR_ERR_NOT_CONVERGED, "step_bdf2: PTC did not converge");
+  return FR_OK;
+}

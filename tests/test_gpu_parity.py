@@ -1,0 +1,346 @@
+"""GPU path (C ABI through the binding) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances:
+* R(U): 1e-12 relative L2 (two FP64 evaluations of the same formulas differ
+  only by rounding order); free stream 1e-13 absolute.
+* FD products: the difference quotient (R(U+eps z) - R0)/eps multiplies the
+  O(u |R terms|) rounding difference between two correct evaluations of R by
+  1/eps, with eps |z_i| ~ 1e-7 (1+||U||)/sqrt(N).  The bound used is
+  TOL_FD = 64 u S / min_i(eps |z_i|)-free form: relative L2 1e-6, which is
+  two orders above the measured differences and far below the O(eps) FD
+  truncation error itself.
+* Element blocks: forward differences with step 1e-7 (1+|q_j|), compared
+  through their action z = M^-1 r, relative L2 1e-6 (same reasoning).
+* End-of-run states with tol_lin = 1e-12: 1e-9 relative L2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle.fr2d import Mesh
+from oracle.jfnk import ElementJacobi, Problem, element_blocks, fd_jv, gmres
+from oracle.steppers import PtcOpts, SolverOpts
+from oracle.steppers import step_bdf2 as o_bdf2
+from oracle.steppers import step_esdirk as o_esdirk
+from oracle.steppers import step_row as o_row
+from oracle.tableaus import ESDIRK, ROW
+
+pytestmark = pytest.mark.gpu
+
+TOL_R = 1e-12
+TOL_FD = 1e-6
+TOL_RUN = 1e-9
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_1904_04825_gb300 as mod
+    return mod
+
+
+def _case(kind, nx, ny, p, seed):
+    if kind == "uniform":
+        xe, ye = S.uniform_mesh(nx, ny=ny)
+    else:
+        xe, ye = S.stretched_mesh(nx, ny, seed=seed)
+    X, Y = S.point_coords(xe, ye, p)
+    return xe, ye, X, Y
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ R(U) --
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("kind,nx,ny", [("uniform", 4, 4), ("stretched", 7, 5), ("stretched", 13, 11)])
+def test_residual_matches_oracle(fr, p, kind, nx, ny):
+    xe, ye, X, Y = _case(kind, nx, ny, p, seed=nx + p)
+    U0 = S.smooth_random_state(X, Y, seed=100 + p, amp=0.1)
+    ctx = fr.Context(xe, ye, p)
+    U = _t(U0)
+    R = ctx.empty()
+    fr.fr_residual(ctx, U, R)
+    Ro = Problem(Mesh(xe, ye), p).R(U0)
+    Rg = R.cpu().numpy()
+    assert _rel(Rg, Ro) < TOL_R
+    assert np.max(np.abs(Rg - Ro)) < 1e-11 * np.max(np.abs(Ro))
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_residual_free_stream_and_conservation(fr, p):
+    xe, ye, X, Y = _case("stretched", 9, 6, p, seed=3)
+    one = np.ones_like(X)
+    ctx = fr.Context(xe, ye, p)
+    R = ctx.empty()
+    fr.fr_residual(ctx, _t(S.conserved(1.3 * one, 0.4 * one, -0.9 * one, 2.2 * one)), R)
+    assert float(R.abs().max()) < 1e-13 * 10
+    U0 = S.smooth_random_state(X, Y, seed=5, amp=0.1)
+    fr.fr_residual(ctx, _t(U0), R)
+    Rg = R.cpu().numpy()
+    m = Mesh(xe, ye)
+    from oracle.basis import Basis
+    b = Basis(p)
+    w2 = np.outer(b.w, b.w).reshape(-1)
+    detJ = (0.25 * m.hx * m.hy).reshape(-1)
+    tot = np.einsum("evp,p,e->v", Rg, w2, detJ)
+    scale = np.einsum("evp,p,e->v", np.abs(Rg), w2, detJ)
+    assert np.all(np.abs(tot) < 1e-13 * np.maximum(scale, 1.0))
+
+
+def test_residual_vortex_full_size_c2(fr):
+    """160 x 160, p = 3 (1.6 M DOFs) in the launch configuration the bench uses."""
+    p = 3
+    xe, ye = S.uniform_mesh(160)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.Vortex().state(X, Y)
+    ctx = fr.Context(xe, ye, p)
+    R = ctx.empty()
+    fr.fr_residual(ctx, _t(U0), R)
+    Ro = Problem(Mesh(xe, ye), p).R(U0)
+    assert _rel(R.cpu().numpy(), Ro) < TOL_R
+
+
+# -------------------------------------------------------------------- Jv --
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("shift", [0.0, 7.5])
+def test_jv_matches_oracle(fr, p, shift):
+    xe, ye, X, Y = _case("stretched", 6, 5, p, seed=p)
+    U0 = S.smooth_random_state(X, Y, seed=7, amp=0.1)
+    z0 = S.random_vector(U0.shape, 11)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    ctx = fr.Context(xe, ye, p)
+    y = ctx.empty()
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(z0), shift, y)
+    yo = fd_jv(prob, U0, R0, z0, shift)
+    assert _rel(y.cpu().numpy(), yo) < TOL_FD
+    # zero direction gives exactly zero
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(np.zeros_like(z0)), shift, y)
+    assert float(y.abs().max()) == 0.0
+
+
+def test_jv_paper_fixed_epsilon(fr):
+    p = 3
+    xe, ye, X, Y = _case("uniform", 5, 5, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    z0 = S.random_vector(U0.shape, 2) * 1e-2
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(eps_fixed=1e-8))
+    y = ctx.empty()
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(z0), 0.0, y)
+    yo = fd_jv(prob, U0, R0, z0, 0.0, eps_fixed=1e-8)
+    assert _rel(y.cpu().numpy(), yo) < 1e-5
+
+
+# ------------------------------------------------------- element blocks --
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_element_jacobi_apply_matches_oracle(fr, p):
+    xe, ye, X, Y = _case("stretched", 5, 4, p, seed=2 * p)
+    U0 = S.smooth_random_state(X, Y, seed=17, amp=0.1)
+    r0 = S.random_vector(U0.shape, 19)
+    shift = 40.0
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p)
+    U = _t(U0)
+    fr.ejacobi_factor(ctx, U, None, shift)
+    z = ctx.empty()
+    fr.ejacobi_apply(ctx, _t(r0), z)
+    zo = ElementJacobi(element_blocks(prob, U0, shift))(r0)
+    assert _rel(z.cpu().numpy(), zo) < TOL_FD
+
+
+def test_element_jacobi_full_size_sampled(fr):
+    """160 x 160, p = 3: blocks of sampled elements (ragged sample incl. the
+    first and last element) against the oracle's element-local FD."""
+    p = 3
+    xe, ye = S.uniform_mesh(160)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.Vortex().state(X, Y)
+    shift = 1.0 / (0.25 * 0.05)
+    ctx = fr.Context(xe, ye, p)
+    fr.ejacobi_factor(ctx, _t(U0), None, shift)
+    r0 = S.random_vector(U0.shape, 23)
+    z = ctx.empty()
+    fr.ejacobi_apply(ctx, _t(r0), z)
+    zg = z.cpu().numpy()
+    prob = Problem(Mesh(xe, ye), p)
+    sample = np.unique(np.concatenate([[0, 159, 160 * 80 + 80, 25599],
+                                       np.random.default_rng(0).integers(0, 25600, 60)]))
+    M = element_blocks(prob, U0, shift, elements=sample)
+    zo = np.linalg.solve(M, r0[sample].reshape(len(sample), -1, 1))[..., 0]
+    assert _rel(zg[sample].reshape(len(sample), -1), zo) < TOL_FD
+
+
+# ----------------------------------------------------------------- GMRES --
+@pytest.mark.parametrize("precond", [1, 0])
+def test_gmres_matches_oracle(fr, precond):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 6, 6, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    b0 = S.random_vector(U0.shape, 31)
+    shift = 1.0 / (0.43586652150845900 * 0.1)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(precond=precond))
+    U = _t(U0)
+    if precond:
+        fr.ejacobi_factor(ctx, U, None, shift)
+    x = ctx.empty().zero_()
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=30, rtol=1e-12, max_restarts=40)
+    assert info.converged
+    Minv = ElementJacobi(element_blocks(prob, U0, shift)) if precond else None
+    A = lambda v: fd_jv(prob, U0, R0, v, shift)
+    xo, io = gmres(A, b0, None, 30, 1e-12, 40, Minv)
+    assert io.converged
+    assert _rel(x.cpu().numpy(), xo) < 1e-8
+    # iteration counts agree to within the last restart's slack
+    assert abs(info.iters - io.iters) <= 2
+    # the true residual of the GPU answer, measured by the oracle
+    rr = b0 - A(x.cpu().numpy())
+    assert np.linalg.norm(rr) <= 1e-9 * np.linalg.norm(b0)
+
+
+def test_gmres_restarts_and_not_converged_status(fr):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    b0 = S.random_vector(U0.shape, 3)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(precond=0))
+    x = ctx.empty().zero_()
+    info = fr.gmres_solve(ctx, _t(U0), _t(R0), 2.0, _t(b0), x, m=3, rtol=1e-14, max_restarts=2)
+    assert not info.converged and info.code == fr.FR_ERR_NOT_CONVERGED
+    assert info.iters == 9 and info.restarts == 2
+    xo, io = gmres(lambda v: fd_jv(prob, U0, R0, v, 2.0), b0, None, 3, 1e-14, 2, None)
+    assert io.iters == 9
+    assert abs(info.relres - io.relres) < 1e-6 * io.relres
+    # zero right-hand side: x = 0, converged
+    x.fill_(1.0)
+    info = fr.gmres_solve(ctx, _t(U0), _t(R0), 2.0, _t(np.zeros_like(b0)), x, m=3, rtol=1e-8)
+    assert info.converged and float(x.abs().max()) == 0.0
+
+
+def test_gmres_nonzero_initial_guess(fr):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    b0 = S.random_vector(U0.shape, 4)
+    shift = 30.0
+    ctx = fr.Context(xe, ye, p)
+    U = _t(U0)
+    fr.ejacobi_factor(ctx, U, None, shift)
+    x = ctx.empty().zero_()
+    fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=30, rtol=1e-12)
+    x2 = x.clone()
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x2, m=30, rtol=1e-10)
+    assert info.converged and info.iters <= 1
+
+
+# -------------------------------------------------------------- steppers --
+TIGHT = SolverOpts(tol_lin=1e-12, m=30, max_restarts=40)
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+def test_step_row_matches_oracle(fr, scheme):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 6, 6, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=40))
+    U = _t(U0)
+    Uo = U0.copy()
+    for _ in range(2):
+        st = fr.step_row(ctx, scheme, 0.1, U)
+        assert st.converged
+        Uo, so = o_row(prob, ROW[scheme](), 0.1, Uo, TIGHT)
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+
+
+def test_c1_end_of_run_matches_oracle(fr):
+    """The plain-method workload: 20 x 20, p = 2, ROW2, 10 steps of 0.05,
+    GMRES(30), element-Jacobi; tol_lin = 1e-12 so both sides stop alike."""
+    p = 2
+    xe, ye = S.uniform_mesh(20)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=40))
+    U = _t(U0)
+    Uo = U0.copy()
+    for _ in range(10):
+        fr.step_row(ctx, 2, 0.05, U)
+        Uo, _ = o_row(prob, ROW[2](), 0.05, Uo, TIGHT)
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+def test_step_esdirk_matches_oracle(fr, scheme):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 5, 5, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(gmres_max_restarts=40))
+    po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
+    U = _t(U0)
+    st = fr.step_esdirk(ctx, scheme, 0.1, U, po)
+    Uo, so = o_esdirk(prob, ESDIRK[scheme](), 0.1, U0, PtcOpts(tol_nl=1e-12, tol_lin=1e-3), TIGHT)
+    assert st.converged and so.converged
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+
+
+def test_step_bdf2_matches_oracle(fr):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 5, 5, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(gmres_max_restarts=40))
+    po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
+    U = _t(U0)
+    Up = ctx.empty()
+    Uo, Upo = U0.copy(), None
+    for k in range(3):
+        fr.step_bdf2(ctx, 0.1, U, Up, k == 0, po)
+        Uo, Upo, _ = o_bdf2(prob, 0.1, Uo, Upo, k == 0, PtcOpts(tol_nl=1e-12, tol_lin=1e-3), TIGHT)
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+    assert _rel(Up.cpu().numpy(), Upo) < TOL_RUN
+
+
+def test_ptc_rejection_path_on_gpu(fr):
+    """A one-iteration GMRES without preconditioner cannot cut the residual
+    by a decade: pseudo steps are rejected until the stall limit."""
+    p = 2
+    xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(precond=0, gmres_m=1, gmres_max_restarts=0))
+    po = fr.default_ptc_opts(tol_nl=1e-8, tol_lin=1e-1, max_rejections=3, max_iters=5)
+    U = _t(U0)
+    st = fr.step_esdirk(ctx, 2, 0.5, U, po, allow=(fr.FR_ERR_PTC_STALLED, fr.FR_ERR_NOT_CONVERGED))
+    assert st.rejections > 0 and not st.converged
+    assert np.array_equal(U.cpu().numpy(), U0)  # a stalled step leaves U unchanged
+
+
+def test_nonfinite_input_reported(fr):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    U0[3, 1, 2] = np.nan
+    ctx = fr.Context(xe, ye, p)
+    U = _t(U0)
+    with pytest.raises(fr.FrError) as ei:
+        fr.step_row(ctx, 2, 0.05, U)
+    assert ei.value.code == fr.FR_ERR_NONFINITE
