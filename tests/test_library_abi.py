@@ -27,10 +27,11 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_1904_04825_gb300 import _build
-    if not os.path.exists(_build.LIB):
-        _build.build()
-    return _build.LIB
+    import __graft_entry__
+    b = __graft_entry__._builder()
+    if not os.path.exists(b.LIB):
+        b.build()
+    return b.LIB
 
 
 def test_header_declares_the_hot_path():
