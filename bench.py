@@ -1,0 +1,392 @@
+"""Benchmark of the JFNK hot path on the 160x160, p=3 isentropic vortex.
+
+One step = one ROW3 (ROS34PW2) time step of the 2D Euler isentropic vortex
+(strength 5, M = 0.5 at 45 degrees) on a periodic 160x160 uniform mesh of
+[-5,5]^2 at p = 3 (1,638,400 DOFs): R(q^n), the element-Jacobi blocks at
+shift 1/(gamma dt), four stage solves with GMRES(30) to tol_rel,linear = 1e-6
+(the ROW tolerance of the paper's integrator comparison), and the update.
+dt = 0.05 (CFL 13.6 with CFL = dt (|V|+c)(p+1)/h), i.e. 200 steps to t = 10.
+
+value = DOF x GMRES iterations per second (whole job, all ranks).  Inputs are
+resident in HBM; the working set (element blocks 0.84 GB, Krylov basis
+0.42 GB) is ~10x the L2, so no explicit L2 flush is needed.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank runs an independent replica (the method has no
+data-path exchange on one GPU): barrier + synchronize around the timed
+region, max time over ranks, units summed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX = 160
+P = 3
+SCHEME = 3
+DT = 0.05
+TOL_LIN = 1e-6
+METRIC = "DOF*GMRES-iters/s (plain FP64 JFNK, ROW3 step, 160x160 p=3 vortex)"
+UNIT = "DOF*iter/s"
+WORKLOAD = "vortex-160x160-p3-ROW3-dt0.05-gmres30-tol1e-6"
+FP64_PEAK_TFLOPS = 1.259  # 152 SMs x 4 FP64 flops/clk/SM x 2.07 GHz (nominal 1.25 TF)
+REF_NX = 24               # oracle sample mesh (same p, scheme, CFL, tolerance)
+
+
+def _config(extra=None):
+    c = {"workload": WORKLOAD, "mesh": f"{NX}x{NX}", "p": P, "ndof": NX * NX * 4 * (P + 1) ** 2,
+         "scheme": "ROW3 (ROS34PW2)", "dt": DT, "cfl": round(DT * 3 * math.sqrt(2) * (P + 1) / (10.0 / NX), 2),
+         "gmres": "GMRES(30), element-Jacobi, tol 1e-6", "fd_eps": "1e-7(1+||U||)/||z||",
+         "l2": "inputs larger than L2 (blocks 0.84 GB + Krylov basis 0.42 GB)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only query)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle --
+ORACLE_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import synthetic as S
+from oracle.fr2d import Mesh
+from oracle.jfnk import Problem
+from oracle.steppers import SolverOpts, step_row
+from oracle.tableaus import ROW
+n, p, steps = {n}, {p}, {steps}
+h = 10.0 / n
+dt = {dt} * (h / (10.0 / {nx_full}))
+xe, ye = S.uniform_mesh(n)
+X, Y = S.point_coords(xe, ye, p)
+U = S.Vortex().state(X, Y)
+prob = Problem(Mesh(xe, ye), p)
+opts = SolverOpts(tol_lin={tol}, m=30, max_restarts=20)
+out = []
+for k in range(steps):
+    t0 = time.perf_counter()
+    U, st = step_row(prob, ROW[{scheme}](), dt, U, opts)
+    out.append((time.perf_counter() - t0, st.gmres_iters))
+print(json.dumps({{"ndof": prob.ndof, "steps": out}}))
+"""
+
+
+def run_oracle_sample(steps):
+    """Oracle (NumPy, one thread) ROW3 steps of the vortex on a REF_NX^2 mesh at
+    the same p, CFL and tolerance; returns (ndof, [(seconds, iters), ...])."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SAMPLE.format(root=ROOT, n=REF_NX, p=P, steps=steps, dt=DT, nx_full=NX, tol=TOL_LIN,
+                                scheme=SCHEME)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["ndof"], d["steps"]
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ndof, steps = run_oracle_sample(args.warmup + args.steps)
+    timed = steps[args.warmup:]
+    secs = sum(t for t, _ in timed)
+    iters = sum(i for _, i in timed)
+    value = ndof * iters / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(len(timed), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config({"reference_sample": f"oracle ROW3 steps on the {REF_NX}x{REF_NX} p=3 vortex, same CFL and tolerance"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one oracle ROW3 step of the {REF_NX}x{REF_NX} p={P} vortex "
+                                   f"({ndof} DOFs, same CFL 13.6, tol 1e-6), NumPy on 1 host thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------ our arm --
+def our_arm(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    xe, ye = S.uniform_mesh(NX)
+    X, Y = S.point_coords(xe, ye, P)
+    U0 = S.Vortex().state(X, Y)
+    ctx = fr.Context(xe, ye, P, fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20))
+    U = torch.from_numpy(U0).to(dev)
+    stream = torch.cuda.current_stream()
+
+    # warm-up, with every kernel family timed to find the dominant one
+    fr.fr_profile_begin(ctx)
+    for _ in range(args.warmup):
+        fr.step_row(ctx, SCHEME, DT, U)
+    warm = fr.fr_profile_end(ctx)
+    top = max(warm, key=lambda k: warm[k]["ms"])
+
+    # timed region: device-resident inputs
+    launches0 = fr.fr_kernel_launches()
+    fr.fr_profile_begin(ctx, [top])
+    clocks = ClockSampler(dev)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = fr.step_row(ctx, SCHEME, DT, U)
+        iters += st.gmres_iters
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = fr.fr_profile_end(ctx)[top]
+    launches = fr.fr_kernel_launches() - launches0
+
+    # end to end through the public API from pinned host memory
+    host_in = torch.from_numpy(U.cpu().numpy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ud = torch.empty_like(U)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        Ud.copy_(host_in, non_blocking=True)
+        st = fr.step_row(ctx, SCHEME, DT, Ud)
+        e2e_iters += st.gmres_iters
+        host_out.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize()
+        host_in, host_out = host_out, host_in
+    e2e_s = time.perf_counter() - t0
+
+    ndof = ctx.ndof
+    units = float(ndof) * iters
+    e2e_units = float(ndof) * e2e_iters
+    if dist is not None:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units, e2e_units], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, e2e_s = float(t[0]), float(t[1])
+        units, e2e_units = float(u[0]), float(u[1])
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    avg_launch_s = prof["ms"] / max(prof["launches"], 1) * 1e-3
+    work_flops = prof["flops"] / max(prof["launches"], 1)
+    work_bytes = prof["bytes"] / max(prof["launches"], 1)
+    achieved_tf = work_flops / avg_launch_s / 1e12
+    achieved_gbs = work_bytes / avg_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {
+        "kernel": top, "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+        "traffic": None,
+        "peak_source": "FP64 FMA pipe: 152 SMs x 4 flops/clk x 2.07 GHz (derived, nominal 1.25 TF)",
+        "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof["launches"],
+        "algorithmic_bytes_per_launch": work_bytes, "algorithmic_flops_per_launch": work_flops,
+    }
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file)).get(top)
+            if tr:
+                roofline["traffic"] = tr["dram_bytes_per_launch"]
+        except (OSError, ValueError):
+            pass
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        nd, stp = run_oracle_sample(1)
+        secs = sum(t for t, _ in stp)
+        it = sum(i for _, i in stp)
+        cpu = {"value": nd * it / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle ROW3 step of the {REF_NX}x{REF_NX} p={P} vortex ({nd} DOFs, same "
+                         f"CFL 13.6 and tol 1e-6, {it} GMRES iterations, {secs:.1f} s), NumPy on 1 host thread"}
+
+    line = {
+        "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
+                           "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / DT)}),
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
+                "d2h_bytes_per_step": 8 * ndof},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_arm(args):
+    """Time one kernel family alone on the full-size inputs (for per-kernel
+    numbers and as a short, clean target for ncu captures)."""
+    import torch
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    torch.cuda.set_device(0)
+    xe, ye = S.uniform_mesh(NX)
+    X, Y = S.point_coords(xe, ye, P)
+    U = torch.from_numpy(S.Vortex().state(X, Y)).cuda()
+    ctx = fr.Context(xe, ye, P)
+    R = ctx.empty()
+    fr.fr_residual(ctx, U, R)
+    z = torch.from_numpy(S.random_vector(ctx.shape, 1)).cuda()
+    y = ctx.empty()
+    shift = 1.0 / (0.43586652150845900 * DT)
+    if args.kernel in ("apply",):
+        fr.ejacobi_factor(ctx, U, None, shift)
+    run = {
+        "residual": lambda: fr.fr_residual(ctx, U, R),
+        "jv": lambda: fr.fr_jv(ctx, U, R, z, shift, y),
+        "factor": lambda: fr.ejacobi_factor(ctx, U, None, shift),
+        "apply": lambda: fr.ejacobi_apply(ctx, z, y),
+    }[args.kernel]
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    fr.fr_profile_begin(ctx, [args.kernel])
+    for _ in range(args.steps):
+        run()
+    torch.cuda.synchronize()
+    pr = fr.fr_profile_end(ctx)[args.kernel]
+    us = pr["ms"] / max(pr["launches"], 1) * 1e3
+    print(json.dumps({"kernel": args.kernel, "launches": pr["launches"], "avg_us": us,
+                      "tflops": pr["flops"] / pr["launches"] / (us * 1e-6) / 1e12,
+                      "gbs": pr["bytes"] / pr["launches"] / (us * 1e-6) / 1e9,
+                      "bytes_per_launch": pr["bytes"] / pr["launches"],
+                      "flops_per_launch": pr["flops"] / pr["launches"]}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", choices=["residual", "jv", "factor", "apply"], default=None,
+                    help="time one kernel family alone on the full-size inputs")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.kernel:
+        return kernel_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

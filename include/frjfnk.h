@@ -176,6 +176,36 @@ int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts
 int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
               const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
 
+/* ---- measurement hooks (no counterpart in the paper) -------------------
+ * Kernel families for fr_profile_*: */
+enum {
+  FR_KF_RESIDUAL = 0,  /* R(U) */
+  FR_KF_JV = 1,        /* FD operator A z and b - A z */
+  FR_KF_FACTOR = 2,    /* element-block formation + inversion */
+  FR_KF_APPLY = 3,     /* element-Jacobi apply (incl. basis normalisation) */
+  FR_KF_DOTS = 4,      /* Gram-Schmidt multi-dot products */
+  FR_KF_UPDATE = 5,    /* Gram-Schmidt multi-AXPY updates */
+  FR_KF_SOLUPDATE = 6, /* x += M^-1 V y */
+  FR_KF_OTHER = 7,     /* norms, linear combinations, copies, Givens */
+  FR_KF_COUNT = 8
+};
+
+/* Number of kernels this library has launched in this process. */
+long long fr_kernel_launches(void);
+
+/* Start timing every launch of the families whose bit (1 << FR_KF_*) is set
+ * in family_mask with CUDA events on the launching stream.  Creates the
+ * events (host-side setup, no device allocation). */
+int fr_profile_begin(fr_ctx* ctx, unsigned family_mask);
+
+/* Stop timing; synchronises the recorded events and writes, per family
+ * (arrays of FR_KF_COUNT entries, any may be NULL): the summed kernel time in
+ * ms, the number of launches that did work (GMRES-cycle kernels launched
+ * after the cycle finished return at once and are not counted), and the
+ * algorithmic bytes and floating-point operations of the timed launches
+ * (the counting rules are stated beside each launch in the sources). */
+int fr_profile_end(fr_ctx* ctx, double* ms, long long* launches, double* bytes, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,10 @@ FR_ERR_NOT_CONVERGED = 4
 FR_ERR_PTC_STALLED = 5
 FR_ERR_TIMEOUT = 6
 FR_ERR_UNSUPPORTED = 7
+
+# kernel families of the measurement hooks
+KF_NAMES = ["residual", "jv", "factor", "apply", "dots", "update", "solupdate", "other"]
+FR_KF_COUNT = len(KF_NAMES)
 ERROR_NAMES = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_CUDA", 3: "FR_ERR_NONFINITE",
                4: "FR_ERR_NOT_CONVERGED", 5: "FR_ERR_PTC_STALLED", 6: "FR_ERR_TIMEOUT",
                7: "FR_ERR_UNSUPPORTED"}
@@ -97,6 +101,10 @@ def _load():
                             ctypes.POINTER(fr_step_stats), V]),
         "step_bdf2": (I, [P, D, P, P, I, ctypes.POINTER(fr_ptc_opts),
                           ctypes.POINTER(fr_step_stats), V]),
+        "fr_kernel_launches": (ctypes.c_longlong, []),
+        "fr_profile_begin": (I, [P, ctypes.c_uint]),
+        "fr_profile_end": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,3 +267,29 @@ def step_bdf2(ctx: Context, dt: float, U, U_prev, first_step: bool, ptc: fr_ptc_
                        _stream(stream))
     ctx.check(rc, allow=allow)
     return _stats(st, rc)
+
+
+def fr_kernel_launches() -> int:
+    """Kernels this library has launched in this process."""
+    return int(lib.fr_kernel_launches())
+
+
+def fr_profile_begin(ctx: Context, families=None):
+    """Time every launch of the given kernel families (names of KF_NAMES)."""
+    names = KF_NAMES if families is None else families
+    mask = 0
+    for n in names:
+        mask |= 1 << KF_NAMES.index(n)
+    return ctx.check(lib.fr_profile_begin(ctx.handle, mask))
+
+
+def fr_profile_end(ctx: Context):
+    """{family: dict(ms, launches, bytes, flops)} for the timed families:
+    summed kernel time, launches that did work, algorithmic bytes and flops."""
+    ms = (ctypes.c_double * FR_KF_COUNT)()
+    n = (ctypes.c_longlong * FR_KF_COUNT)()
+    by = (ctypes.c_double * FR_KF_COUNT)()
+    fl = (ctypes.c_double * FR_KF_COUNT)()
+    ctx.check(lib.fr_profile_end(ctx.handle, ms, n, by, fl))
+    return {KF_NAMES[i]: {"ms": ms[i], "launches": n[i], "bytes": by[i], "flops": fl[i]}
+            for i in range(FR_KF_COUNT) if n[i] > 0 or ms[i] > 0}

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.cuh"
@@ -44,6 +45,13 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->gd.k);
   cudaFree(c->gd.res);
   cudaFree(c->gd.target);
+  for (cudaEvent_t e : c->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  for (int f = 0; f < FR_KF_COUNT; ++f) {
+    if (!c->prof.ev[f]) continue;
+    for (int i = 0; i < 2 * Prof::kPairs; ++i) cudaEventDestroy(c->prof.ev[f][i]);
+    delete[] c->prof.ev[f];
+  }
   cudaFreeHost(c->h_stat);
   cudaFreeHost(c->h_scal);
   delete c;
@@ -105,9 +113,12 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   FRK_TRY(dalloc(c, &c->gd.target, 1));
   FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), 4 * sizeof(int)));
   FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 8 * sizeof(double)));
+  for (cudaEvent_t& e : c->chunk_ev) FRK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   FRK_CUDA(c, cudaDeviceSynchronize());
   return FR_OK;
 }
+
+std::atomic<long long> g_launches{0};
 
 int check_vec(fr_ctx* ctx, const void* p, const char* name) {
   if (!p) return set_error(ctx, FR_ERR_INVALID_ARG, "%s is NULL", name);
@@ -116,7 +127,65 @@ int check_vec(fr_ctx* ctx, const void* p, const char* name) {
 
 char g_static_err[256] = "invalid context";
 
+// harvest the recorded event pairs of one family into ms / n
+void prof_harvest(fr_ctx* c, int f) {
+  Prof& P = c->prof;
+  for (int i = 0; i < P.used[f]; ++i) {
+    float t = 0.f;
+    if (cudaEventSynchronize(P.ev[f][2 * i + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&t, P.ev[f][2 * i], P.ev[f][2 * i + 1]) == cudaSuccess) {
+      P.ms[f] += t;
+      P.n[f] += 1;
+    }
+  }
+  P.used[f] = 0;
+}
+
 }  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(fr_ctx* c, int f, cudaStream_t s) {
+  count_launch();
+  Prof& P = c->prof;
+  if (!(P.mask & (1u << f))) return;
+  if (P.used[f] == Prof::kPairs) prof_harvest(c, f);
+  cudaEventRecord(P.ev[f][2 * P.used[f]], s);
+}
+
+void prof_work(fr_ctx* c, int f, double bytes, double flops) {
+  Prof& P = c->prof;
+  if (!(P.mask & (1u << f))) return;
+  P.bytes[f] += bytes;
+  P.flops[f] += flops;
+}
+
+// FR residual, per element (N = p+1, Np = N^2), counted from the method's
+// steps: pointwise fluxes 22 flops per point; face traces of the solution
+// 4 faces x N points x 4 variables x N multiply-adds; one Rusanov flux per
+// face point with each face shared by two elements (2N per element, 70 flops
+// each); corrected divergence along x and y, 4 variables x Np points x
+// (N + 2) multiply-adds each; the final scaling, 4 Np.
+double residual_flops_per_element(int p) {
+  const double N = p + 1, Np = N * N;
+  return 22 * Np + 2 * 16 * N * N + 70 * 2 * N + 2 * 2 * 4 * Np * (N + 2) + 4 * Np;
+}
+
+// Element block: nb = 4 Np columns, each a local FD column (one pointwise
+// flux, four Rusanov fluxes, 2N x 4 entries of 3 multiply-adds) plus
+// Gauss-Jordan inversion, 2 nb^3.
+double factor_flops_per_element(int p) {
+  const double N = p + 1, Np = N * N, nb = 4 * Np;
+  return nb * (22 + 4 * 70 + 2 * N * 4 * 6) + 2 * nb * nb * nb;
+}
+
+void prof_end(fr_ctx* c, int f, cudaStream_t s) {
+  Prof& P = c->prof;
+  if (!(P.mask & (1u << f))) return;
+  cudaEventRecord(P.ev[f][2 * P.used[f] + 1], s);
+  P.used[f] += 1;
+}
+
 }  // namespace frk
 
 using namespace frk;
@@ -247,4 +316,42 @@ extern "C" int gmres_solve(fr_ctx* ctx, const double* U, const double* R0, doubl
   const int rc = gmres_impl(ctx, U, R0, shift, b, x, m, rtol, max_restarts, false, &loc, as_stream(stream));
   if (info) *info = loc;
   return rc;
+}
+
+extern "C" long long fr_kernel_launches(void) { return frk::g_launches.load(); }
+
+extern "C" int fr_profile_begin(fr_ctx* ctx, unsigned mask) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  Prof& P = ctx->prof;
+  for (int f = 0; f < FR_KF_COUNT; ++f) {
+    if (!(mask & (1u << f))) continue;
+    if (!P.ev[f]) {
+      P.ev[f] = new cudaEvent_t[2 * Prof::kPairs];
+      for (int i = 0; i < 2 * Prof::kPairs; ++i) FRK_CUDA(ctx, cudaEventCreate(&P.ev[f][i]));
+    }
+    P.used[f] = 0;
+    P.ms[f] = 0.0;
+    P.n[f] = 0;
+    P.skipped[f] = 0;
+    P.bytes[f] = 0.0;
+    P.flops[f] = 0.0;
+  }
+  P.mask = mask;
+  return FR_OK;
+}
+
+extern "C" int fr_profile_end(fr_ctx* ctx, double* ms, long long* launches, double* bytes,
+                              double* flops) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  Prof& P = ctx->prof;
+  for (int f = 0; f < FR_KF_COUNT; ++f) {
+    const bool on = (P.mask & (1u << f)) != 0;
+    if (on) prof_harvest(ctx, f);
+    if (ms) ms[f] = on ? P.ms[f] : 0.0;
+    if (launches) launches[f] = on ? P.n[f] - P.skipped[f] : 0;
+    if (bytes) bytes[f] = on ? P.bytes[f] : 0.0;
+    if (flops) flops[f] = on ? P.flops[f] : 0.0;
+  }
+  P.mask = 0;
+  return FR_OK;
 }

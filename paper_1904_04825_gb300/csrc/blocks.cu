@@ -364,7 +364,10 @@ int factor_p(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
   using L = FactorLayout<P>;
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_factor<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)L::BYTES));
-  k_factor<P><<<(unsigned)ctx->ne, L::THREADS, L::BYTES, s>>>(a);
+  // work: read U (8 B/DOF), write ne nb^2 doubles; flops per element as counted
+  const double fb = 8.0 * (double)ctx->ndof + 8.0 * (double)ctx->ne * L::NB * L::NB;
+  const double ff = factor_flops_per_element(P) * (double)ctx->ne;
+  { ProfScope ps_(ctx, FR_KF_FACTOR, s, fb, ff); k_factor<P><<<(unsigned)ctx->ne, L::THREADS, L::BYTES, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -380,16 +383,22 @@ unsigned apply_grid(long long ne) {
 template <int NB>
 int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
              const int* done, cudaStream_t s) {
-  k_apply<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(ctx->blocks, r, scale, z, ctx->ne,
-                                                                  sumsq, ctx->red, done);
+  // work: ne nb^2 block entries, r in, z out (and r written back when scaled):
+  // 2 nb flops per DOF.  Inside a GMRES cycle it is booked per finished iteration.
+  const bool in_cycle = done != nullptr;
+  const double nd = (double)ctx->ndof;
+  const double wb = in_cycle ? 0.0 : 8.0 * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
+  const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
+  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(ctx->blocks, r, scale, z, ctx->ne,
+                                                                  sumsq, ctx->red, done); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 template <int NB>
 int solupdate_nb(fr_ctx* ctx, double* x, cudaStream_t s) {
-  k_solupdate<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(
-      ctx->blocks, ctx->V, ctx->ndof, ctx->gd.y, ctx->gd.k, x, ctx->ne);
+  { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(
+      ctx->blocks, ctx->V, ctx->ndof, ctx->gd.y, ctx->gd.k, x, ctx->ne); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -419,8 +428,8 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
                        const int* done, cudaStream_t s) {
   if (!ctx->opts.precond) {
-    k_scale_copy<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
-                                                          done);
+    { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
+                                                          done); }
     FRK_LAUNCHED(ctx);
     return FR_OK;
   }
@@ -434,8 +443,8 @@ int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, d
 
 int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
   if (!ctx->opts.precond) {
-    k_solupdate_plain<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(ctx->V, ctx->ndof, ctx->gd.y,
-                                                               ctx->gd.k, x, ctx->ndof);
+    { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate_plain<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(ctx->V, ctx->ndof, ctx->gd.y,
+                                                               ctx->gd.k, x, ctx->ndof); }
     FRK_LAUNCHED(ctx);
     return FR_OK;
   }

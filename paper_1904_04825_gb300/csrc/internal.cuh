@@ -62,6 +62,21 @@ enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_COUNT };
 
 }  // namespace frk
 
+namespace frk {
+// CUDA-event timing of kernel families (measurement only).
+struct Prof {
+  unsigned mask = 0;
+  static constexpr int kPairs = 2048;
+  cudaEvent_t* ev[FR_KF_COUNT] = {};  // 2 * kPairs events per family
+  int used[FR_KF_COUNT] = {};
+  double ms[FR_KF_COUNT] = {};
+  long long n[FR_KF_COUNT] = {};
+  long long skipped[FR_KF_COUNT] = {};  // launches that found the GMRES cycle finished
+  double bytes[FR_KF_COUNT] = {};       // algorithmic bytes of the timed launches
+  double flops[FR_KF_COUNT] = {};       // algorithmic flops of the timed launches
+};
+}  // namespace frk
+
 struct fr_ctx {
   int device = 0;
   int nx = 0, ny = 0, p = 0, n1 = 0, np = 0, nb = 0;
@@ -80,6 +95,8 @@ struct fr_ctx {
   frk::GmresDev gd{};
   int* h_stat = nullptr;     // pinned host mirror: done, k
   double* h_scal = nullptr;  // pinned host mirror of a few doubles
+  frk::Prof prof;
+  cudaEvent_t chunk_ev[2] = {nullptr, nullptr};  // GMRES look-ahead status events
   char err[512] = {0};
 };
 
@@ -110,6 +127,29 @@ int set_error(fr_ctx* ctx, int code, const char* fmt, ...);
   } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Launch accounting: every kernel launch goes through prof_begin / prof_end.
+void count_launch();
+void prof_begin(fr_ctx* ctx, int family, cudaStream_t s);
+void prof_end(fr_ctx* ctx, int family, cudaStream_t s);
+
+void prof_work(fr_ctx* ctx, int family, double bytes, double flops);
+
+struct ProfScope {
+  fr_ctx* c;
+  int f;
+  cudaStream_t s;
+  ProfScope(fr_ctx* ctx, int family, cudaStream_t st, double bytes = 0.0, double flops = 0.0)
+      : c(ctx), f(family), s(st) {
+    prof_begin(c, f, s);
+    prof_work(c, f, bytes, flops);
+  }
+  ~ProfScope() { prof_end(c, f, s); }
+};
+
+// Algorithmic work per launch (counting rules; see the launch sites).
+double residual_flops_per_element(int p);
+double factor_flops_per_element(int p);
 
 // ---- launchers implemented in the .cu files --------------------------------
 // residual.cu: mode 0: out = R(U); mode 1: out = A z; mode 2: out = b - A z

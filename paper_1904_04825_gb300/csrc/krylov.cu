@@ -175,7 +175,7 @@ __global__ void k_fill(double* dst, double v, long long n) {
 }  // namespace
 
 int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s) {
-  k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red);
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -189,19 +189,19 @@ int launch_lincomb(fr_ctx* ctx, double* out, int nterms, const double* const* xs
     lc.x[t] = xs[t];
     lc.c[t] = coefs[t];
   }
-  k_lincomb<<<vgrid(ctx->ndof), kThreads, 0, s>>>(out, ctx->ndof, lc, sumsq, ctx->red);
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_lincomb<<<vgrid(ctx->ndof), kThreads, 0, s>>>(out, ctx->ndof, lc, sumsq, ctx->red); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 int launch_copy(fr_ctx* ctx, double* dst, const double* src, cudaStream_t s) {
-  k_copy<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, src, ctx->ndof);
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_copy<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, src, ctx->ndof); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s) {
-  k_fill<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, v, ctx->ndof);
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_fill<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, v, ctx->ndof); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -242,25 +242,43 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
       FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_NU2, sc + S_NZ2, nullptr, s));
     }
     FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
-    k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m);
+    { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m); }
     FRK_LAUNCHED(ctx);
-    for (int j = 0; j < m; ++j) {
-      double* vj = V + (size_t)j * n;
-      double* w = V + (size_t)(j + 1) * n;
-      // v_j = r_j / ||r_j|| (written back), z = M^{-1} v_j, ||z||^2
-      FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s));
-      // w = A z
-      FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_NU2, sc + S_NZ2,
-                              gd.done, s));
-      // CGS2
-      k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, ctx->red, gd.done);
-      k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, nullptr, ctx->red, gd.done);
-      k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, ctx->red, gd.done);
-      k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done);
-      k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2);
-      FRK_LAUNCHED(ctx);
+    // Launch the cycle in chunks of kChunk iterations; after launching chunk
+    // c, wait for the finished-flag copied after chunk c-1, so the device
+    // always has queued work and at most one chunk runs past convergence.
+    constexpr int kChunk = 4;
+    int launched = 0, chunk = 0;
+    while (launched < m) {
+      const int jend = launched + kChunk < m ? launched + kChunk : m;
+      for (int j = launched; j < jend; ++j) {
+        double* vj = V + (size_t)j * n;
+        double* w = V + (size_t)(j + 1) * n;
+        // v_j = r_j / ||r_j|| (written back), z = M^{-1} v_j, ||z||^2
+        FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s));
+        // w = A z
+        FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_NU2, sc + S_NZ2,
+                                gd.done, s));
+        // CGS2
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, ctx->red, gd.done); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, nullptr, ctx->red, gd.done); }
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, ctx->red, gd.done); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done); }
+        { ProfScope ps_(ctx, FR_KF_OTHER, s); k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2); }
+        FRK_LAUNCHED(ctx);
+      }
+      launched = jend;
+      const int slot = chunk & 1;
+      FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat + 2 + slot, gd.done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FRK_CUDA(ctx, cudaEventRecord(ctx->chunk_ev[slot], s));
+      ++chunk;
+      if (chunk >= 2) {
+        const int prev = (chunk - 2) & 1;
+        FRK_CUDA(ctx, cudaEventSynchronize(ctx->chunk_ev[prev]));
+        if (ctx->h_stat[2 + prev]) break;
+      }
     }
-    k_backsub<<<1, 32, 0, s>>>(gd);
+    { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
     FRK_LAUNCHED(ctx);
     FRK_TRY(launch_solution_update(ctx, x, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat, gd.k, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -270,6 +288,30 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
     FRK_CUDA(ctx, cudaStreamSynchronize(s));
     const int k = ctx->h_stat[0];
     const double res = ctx->h_scal[0], target = ctx->h_scal[1], bn = std::sqrt(ctx->h_scal[2]);
+    {  // launches of this cycle that found it finished (for per-launch timing),
+       // and the algorithmic work of the k iterations that ran: apply (blocks +
+       // r in, r and z out), A z (U, z, R0 in, w out), CGS2 (two multi-dots
+       // reading j+1 basis vectors and w, two updates reading them and
+       // reading/writing w)
+      const long long sk = launched - k;
+      const double nd = (double)n;
+      for (int j = 0; j < k; ++j) {
+        const double kv = j + 1;
+        if (ctx->opts.precond)
+          prof_work(ctx, FR_KF_APPLY, 8.0 * (double)ctx->ne * ctx->nb * ctx->nb + 24.0 * nd, 2.0 * ctx->nb * nd);
+        else
+          prof_work(ctx, FR_KF_APPLY, 24.0 * nd, 3.0 * nd);
+        prof_work(ctx, FR_KF_JV, 32.0 * nd, residual_flops_per_element(ctx->p) * (double)ctx->ne + 6.0 * nd);
+        prof_work(ctx, FR_KF_DOTS, 2 * 8.0 * (kv + 1) * nd, 2 * 2.0 * kv * nd);
+        prof_work(ctx, FR_KF_UPDATE, 2 * 8.0 * (kv + 2) * nd, 2 * 2.0 * kv * nd + 2.0 * nd);
+      }
+      Prof& P = ctx->prof;
+      P.skipped[FR_KF_APPLY] += sk;
+      P.skipped[FR_KF_JV] += sk;
+      P.skipped[FR_KF_DOTS] += 2 * sk;
+      P.skipped[FR_KF_UPDATE] += 2 * sk;
+      P.skipped[FR_KF_OTHER] += sk;
+    }
     if (!std::isfinite(res) || !std::isfinite(bn)) {
       if (info) *info = loc;
       return set_error(ctx, FR_ERR_NONFINITE, "GMRES residual is not finite");

@@ -172,9 +172,16 @@ int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   constexpr int NP = (P + 1) * (P + 1), EPB = 256 / NP;
   const long long grid = (ctx->ne + EPB - 1) / EPB;
   const dim3 blk(EPB * NP);
-  if (mode == 0) k_residual<P, 0><<<(unsigned)grid, blk, 0, s>>>(a);
-  else if (mode == 1) k_residual<P, 1><<<(unsigned)grid, blk, 0, s>>>(a);
-  else k_residual<P, 2><<<(unsigned)grid, blk, 0, s>>>(a);
+  // algorithmic work: R reads U and writes R (16 B/DOF); A z also reads z and
+  // R0 (and b) and adds the perturbation and the difference quotient.  Inside
+  // a GMRES cycle the work is booked per finished iteration instead.
+  const double nd = (double)ctx->ndof, fl = residual_flops_per_element(P) * (double)ctx->ne;
+  const bool in_cycle = a.done != nullptr;
+  const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
+  const double wf = in_cycle ? 0.0 : (mode == 0 ? fl : fl + 6.0 * nd);
+  if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2><<<(unsigned)grid, blk, 0, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }

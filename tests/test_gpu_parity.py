@@ -3,13 +3,17 @@ seeded inputs.
 
 Tolerances:
 * R(U): 1e-12 relative L2 (two FP64 evaluations of the same formulas differ
-  only by rounding order); free stream 1e-13 absolute.
+  only by rounding order); free stream 1e-13 absolute.  On fine meshes the
+  residual is a small difference of large flux-derivative terms (at 160^2 the
+  vortex residual is ~1e-4 of its terms), so there the 1e-12 is measured
+  against the magnitude of those terms, sJ (|D| |F| + |D| |G|), which is the
+  scale the rounding error of any FP64 evaluation is proportional to.
 * FD products: the difference quotient (R(U+eps z) - R0)/eps multiplies the
   O(u |R terms|) rounding difference between two correct evaluations of R by
-  1/eps, with eps |z_i| ~ 1e-7 (1+||U||)/sqrt(N).  The bound used is
-  TOL_FD = 64 u S / min_i(eps |z_i|)-free form: relative L2 1e-6, which is
-  two orders above the measured differences and far below the O(eps) FD
-  truncation error itself.
+  1/eps, with eps |z_i| ~ 1e-7 (1+||U||)/sqrt(N): about u * 1e4 / 1e-6
+  ~ 1e-8 relative on these meshes.  TOL_FD = 1e-6 relative L2 sits above
+  that and well below the O(eps) truncation error of the FD product itself
+  (~1e-6 to 1e-4 relative), so a wrong eps, sign or shift still fails.
 * Element blocks: forward differences with step 1e-7 (1+|q_j|), compared
   through their action z = M^-1 r, relative L2 1e-6 (same reasoning).
 * End-of-run states with tol_lin = 1e-12: 1e-9 relative L2.
@@ -108,7 +112,27 @@ def test_residual_vortex_full_size_c2(fr):
     R = ctx.empty()
     fr.fr_residual(ctx, _t(U0), R)
     Ro = Problem(Mesh(xe, ye), p).R(U0)
-    assert _rel(R.cpu().numpy(), Ro) < TOL_R
+    scale = _term_scale(U0, xe, ye, p)
+    d = R.cpu().numpy() - Ro
+    assert np.linalg.norm(d) < TOL_R * np.linalg.norm(scale)
+    assert np.max(np.abs(d)) < TOL_R * np.max(scale)
+
+
+def _term_scale(U0, xe, ye, p):
+    """sJ (|D| |F| + |D| |G|) per point: magnitude of the terms whose
+    difference is R (oracle-side fluxes, test only)."""
+    from oracle.basis import Basis
+    from oracle.fr2d import as_grid, flux_x, flux_y, from_grid
+    m = Mesh(xe, ye)
+    b = Basis(p)
+    Q = as_grid(U0, m, p)
+    hx = m.hx[None, :, :, None, None]
+    hy = m.hy[None, :, :, None, None]
+    F = np.abs(0.5 * hy * flux_x(Q))
+    G = np.abs(0.5 * hx * flux_y(Q))
+    aD = np.abs(b.D)
+    S = np.einsum("ik,...jk->...ji", aD, F) + np.einsum("jk,...ki->...ji", aD, G)
+    return from_grid(S * 4.0 / (hx * hy), m, p)
 
 
 # -------------------------------------------------------------------- Jv --
@@ -207,9 +231,12 @@ def test_gmres_matches_oracle(fr, precond):
     assert _rel(x.cpu().numpy(), xo) < 1e-8
     # iteration counts agree to within the last restart's slack
     assert abs(info.iters - io.iters) <= 2
-    # the true residual of the GPU answer, measured by the oracle
-    rr = b0 - A(x.cpu().numpy())
-    assert np.linalg.norm(rr) <= 1e-9 * np.linalg.norm(b0)
+    # The FD operator is linear only to O(eps): one FD product on x differs
+    # from the Krylov combination of FD products on the basis.  The GPU
+    # answer's one-product residual must match the oracle answer's.
+    rg = np.linalg.norm(b0 - A(x.cpu().numpy()))
+    ro = np.linalg.norm(b0 - A(xo))
+    assert abs(rg - ro) <= 1e-3 * ro + 1e-9 * np.linalg.norm(b0)
 
 
 def test_gmres_restarts_and_not_converged_status(fr):
@@ -241,14 +268,23 @@ def test_gmres_nonzero_initial_guess(fr):
     R0 = prob.R(U0)
     b0 = S.random_vector(U0.shape, 4)
     shift = 30.0
-    ctx = fr.Context(xe, ye, p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(precond=0))
     U = _t(U0)
-    fr.ejacobi_factor(ctx, U, None, shift)
     x = ctx.empty().zero_()
     fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=30, rtol=1e-12)
+    # restarting from a converged answer: the first residual is the one FD
+    # product b - A x, already below 1e-6 ||b||, so no iteration is needed
     x2 = x.clone()
-    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x2, m=30, rtol=1e-10)
-    assert info.converged and info.iters <= 1
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x2, m=30, rtol=1e-6)
+    assert info.converged and info.iters == 0
+    assert float((x2 - x).abs().max()) == 0.0
+    # from a poor guess the GPU and the oracle take the same iterations
+    g0 = 0.5 * x.cpu().numpy()
+    x3 = _t(g0)
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x3, m=30, rtol=1e-10)
+    xo, io = gmres(lambda v: fd_jv(prob, U0, R0, v, shift), b0, g0, 30, 1e-10, 20, None)
+    assert abs(info.iters - io.iters) <= 1
+    assert _rel(x3.cpu().numpy(), xo) < 1e-8
 
 
 # -------------------------------------------------------------- steppers --
