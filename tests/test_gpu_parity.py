@@ -272,12 +272,13 @@ def test_gmres_nonzero_initial_guess(fr):
     U = _t(U0)
     x = ctx.empty().zero_()
     fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=30, rtol=1e-12)
-    # restarting from a converged answer: the first residual is the one FD
-    # product b - A x, already below 1e-6 ||b||, so no iteration is needed
+    # restarting from a converged answer costs few iterations (the one-product
+    # FD residual b - A x is ~1e-6 ||b|| here, not the Krylov 1e-12), and the
+    # GPU and the oracle take the same number
     x2 = x.clone()
     info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x2, m=30, rtol=1e-6)
-    assert info.converged and info.iters == 0
-    assert float((x2 - x).abs().max()) == 0.0
+    xo2, io2 = gmres(lambda v: fd_jv(prob, U0, R0, v, shift), b0, x.cpu().numpy(), 30, 1e-6, 20, None)
+    assert info.converged and abs(info.iters - io2.iters) <= 1 and info.iters < 10
     # from a poor guess the GPU and the oracle take the same iterations
     g0 = 0.5 * x.cpu().numpy()
     x3 = _t(g0)
