@@ -210,6 +210,9 @@ def our_arm(args):
         fr.step_row(ctx, SCHEME, DT, U)
     warm = fr.fr_profile_end(ctx)
     top = max(warm, key=lambda k: warm[k]["ms"])
+    breakdown = {k: {"ms_per_step": v["ms"] / args.warmup, "launches_per_step": v["launches"] / args.warmup,
+                     "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None}
+                 for k, v in warm.items()}
 
     # timed region: device-resident inputs
     launches0 = fr.fr_kernel_launches()
@@ -317,6 +320,7 @@ def our_arm(args):
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roofline,
+        "kernel_breakdown": breakdown,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                 "d2h_bytes_per_step": 8 * ndof},

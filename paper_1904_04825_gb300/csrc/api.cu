@@ -42,6 +42,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->gd.h2);
   cudaFree(c->gd.invh);
   cudaFree(c->gd.done);
+  cudaFree(c->gd.rflag);
   cudaFree(c->gd.k);
   cudaFree(c->gd.res);
   cudaFree(c->gd.target);
@@ -108,10 +109,11 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   FRK_TRY(dalloc(c, &c->gd.h2, kMaxVec));
   FRK_TRY(dalloc(c, &c->gd.invh, m + 1));
   FRK_TRY(dalloc(c, &c->gd.done, 1));
+  FRK_TRY(dalloc(c, &c->gd.rflag, m));
   FRK_TRY(dalloc(c, &c->gd.k, 1));
   FRK_TRY(dalloc(c, &c->gd.res, 1));
   FRK_TRY(dalloc(c, &c->gd.target, 1));
-  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), 4 * sizeof(int)));
+  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), (4 + kMaxVec) * sizeof(int)));
   FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 8 * sizeof(double)));
   for (cudaEvent_t& e : c->chunk_ev) FRK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   FRK_CUDA(c, cudaDeviceSynchronize());
@@ -255,7 +257,7 @@ extern "C" int fr_residual(fr_ctx* ctx, const double* U, double* R, void* stream
   FRK_TRY(check_vec(ctx, U, "U"));
   FRK_TRY(check_vec(ctx, R, "R"));
   if (U == R) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_residual: U and R alias");
-  return launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R, 0.0, nullptr, nullptr, nullptr,
+  return launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R, 0.0, nullptr, nullptr,
                          as_stream(stream));
 }
 
@@ -269,9 +271,8 @@ extern "C" int fr_jv(fr_ctx* ctx, const double* U, const double* R0, const doubl
   if (y == U || y == R0 || y == z) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_jv: y aliases an input");
   cudaStream_t s = as_stream(stream);
   FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_NU2, s));
-  FRK_TRY(launch_sumsq(ctx, z, ctx->scal + S_NZ2, s));
-  return launch_residual(ctx, 1, U, z, R0, nullptr, y, shift, ctx->scal + S_NU2, ctx->scal + S_NZ2,
-                         nullptr, s);
+  FRK_TRY(launch_sumsq(ctx, z, ctx->scal + S_NZ2, s, true));
+  return launch_residual(ctx, 1, U, z, R0, nullptr, y, shift, ctx->scal + S_EPS, nullptr, s);
 }
 
 extern "C" int ejacobi_factor(fr_ctx* ctx, const double* U, const double* R0, double shift,

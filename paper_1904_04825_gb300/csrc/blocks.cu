@@ -246,7 +246,7 @@ template <int NB>
 __global__ void __launch_bounds__(256) k_apply(const double* __restrict__ Minv, double* r,
                                                const double* scale, double* __restrict__ z,
                                                long long ne, double* sumsq, Reduce red,
-                                               const int* done) {
+                                               const int* done, EpsArgs ea) {
   constexpr int EPC = 256 / NB;
   __shared__ double rs[EPC][NB];
   __shared__ double sh[32];
@@ -283,13 +283,16 @@ __global__ void __launch_bounds__(256) k_apply(const double* __restrict__ Minv, 
   if (sumsq) {
     const double bs = block_sum(ss, sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-    if (last_block(red.counter)) finish_sums(red, 1, sumsq);
+    if (last_block(red.counter)) {
+      finish_sums(red, 1, sumsq);
+      if (threadIdx.x == 0) write_eps(ea, *sumsq);
+    }
   }
 }
 
 // z = s * r (no preconditioner), optional r *= s written back, optional sum of squares.
 __global__ void k_scale_copy(double* r, const double* scale, double* z, long long n,
-                             double* sumsq, Reduce red, const int* done) {
+                             double* sumsq, Reduce red, const int* done, EpsArgs ea) {
   __shared__ double sh[32];
   if (done && *done) return;
   const double s = scale ? *scale : 1.0;
@@ -307,7 +310,10 @@ __global__ void k_scale_copy(double* r, const double* scale, double* z, long lon
   if (sumsq) {
     const double bs = block_sum(ss, sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-    if (last_block(red.counter)) finish_sums(red, 1, sumsq);
+    if (last_block(red.counter)) {
+      finish_sums(red, 1, sumsq);
+      if (threadIdx.x == 0) write_eps(ea, *sumsq);
+    }
   }
 }
 
@@ -382,7 +388,7 @@ unsigned apply_grid(long long ne) {
 
 template <int NB>
 int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
-             const int* done, cudaStream_t s) {
+             const int* done, cudaStream_t s, bool with_eps) {
   // work: ne nb^2 block entries, r in, z out (and r written back when scaled):
   // 2 nb flops per DOF.  Inside a GMRES cycle it is booked per finished iteration.
   const bool in_cycle = done != nullptr;
@@ -390,7 +396,7 @@ int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sum
   const double wb = in_cycle ? 0.0 : 8.0 * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
   { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(ctx->blocks, r, scale, z, ctx->ne,
-                                                                  sumsq, ctx->red, done); }
+                                                                  sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -426,17 +432,17 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
 }
 
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
-                       const int* done, cudaStream_t s) {
+                       const int* done, cudaStream_t s, bool with_eps) {
   if (!ctx->opts.precond) {
     { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
-                                                          done); }
+                                                          done, eps_args(ctx, with_eps)); }
     FRK_LAUNCHED(ctx);
     return FR_OK;
   }
   switch (ctx->nb) {
-    case 36: return apply_nb<36>(ctx, r, scale, z, sumsq, done, s);
-    case 64: return apply_nb<64>(ctx, r, scale, z, sumsq, done, s);
-    case 100: return apply_nb<100>(ctx, r, scale, z, sumsq, done, s);
+    case 36: return apply_nb<36>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 64: return apply_nb<64>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 100: return apply_nb<100>(ctx, r, scale, z, sumsq, done, s, with_eps);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }

@@ -81,18 +81,37 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
   return am_last;
 }
 
-// In the last block: out[i] = sum over blocks b (ascending) of partials[b][i], i < nvec.
-// Resets the counter.  Needs blockDim.x >= 32.
+// In the last block: out[i] = sum over blocks b (fixed order) of partials[b][i],
+// i < nvec.  Each warp sums one value with its lanes striding over the blocks
+// through four independent accumulators.  Resets the counter.
 __device__ __forceinline__ void finish_sums(const Reduce& red, int nvec, double* out) {
   __threadfence();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = (int)gridDim.x;
   for (int i = wid; i < nvec; i += nw) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + (size_t)b * kMaxVec + i);
-    s = warp_sum(s);
+    const double* p = red.partials + i;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      s0 += __ldcg(p + (size_t)b * kMaxVec);
+      s1 += __ldcg(p + (size_t)(b + 32) * kMaxVec);
+      s2 += __ldcg(p + (size_t)(b + 64) * kMaxVec);
+      s3 += __ldcg(p + (size_t)(b + 96) * kMaxVec);
+    }
+    for (; b < G; b += 32) s0 += __ldcg(p + (size_t)b * kMaxVec);
+    double s = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) out[i] = s;
   }
   if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// eps and 1/eps of the FD product from the finished ||z||^2 (one thread).
+__device__ __forceinline__ void write_eps(const EpsArgs& ea, double nz2) {
+  if (!ea.out) return;
+  double eps = 0.0;
+  if (nz2 > 0.0) eps = ea.eps_fixed > 0.0 ? ea.eps_fixed : ea.eps_rel * (1.0 + sqrt(*ea.nU2)) / sqrt(nz2);
+  ea.out[0] = eps;
+  ea.out[1] = eps > 0.0 ? 1.0 / eps : 0.0;
 }
 
 }  // namespace frk

@@ -14,7 +14,7 @@ namespace frk {
 constexpr int kMaxN = 5;          // p <= 4
 constexpr int kThreads = 256;     // default block size of the vector kernels
 constexpr int kMaxVec = 32;       // largest Krylov basis slice handled per call (m_max + 1)
-constexpr int kVecBlocks = 1216;  // 8 x 152 SMs: grid of the streaming vector kernels
+constexpr int kVecBlocks = 456;   // 3 x 152 SMs: grid of the streaming vector kernels
 constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
 
 // 1D tables of Sec. 3 on Gauss-Legendre points, passed to kernels by value.
@@ -51,6 +51,7 @@ struct GmresDev {
   double* h2;       // second (re-orthogonalisation) coefficients [kMaxVec]
   double* invh;     // 1/||v_j|| of the not-yet-normalised basis vector j [m_max+1]
   int* done;        // cycle finished (converged or breakdown)
+  int* rflag;       // [m_max] 1 if iteration j needed the second Gram-Schmidt pass
   int* k;           // iterations done in this cycle
   double* res;      // |g_k|
   double* target;   // rtol * ||b||
@@ -58,7 +59,16 @@ struct GmresDev {
 };
 
 // Device scalars (sums of squares) used by the FD step and GMRES.
-enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_COUNT };
+enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_COUNT };
+
+// FD step eps = eps_rel (1 + ||U||) / ||z|| (or eps_fixed), written once per
+// product as (eps, 1/eps) by the kernel that finishes ||z||^2.
+struct EpsArgs {
+  const double* nU2;  // ||U||^2
+  double eps_rel;
+  double eps_fixed;
+  double* out;        // [eps, 1/eps], nullptr: not needed
+};
 
 }  // namespace frk
 
@@ -153,16 +163,18 @@ double factor_flops_per_element(int p);
 
 // ---- launchers implemented in the .cu files --------------------------------
 // residual.cu: mode 0: out = R(U); mode 1: out = A z; mode 2: out = b - A z
+// eps2 points at the device pair (eps, 1/eps) of the product (modes 1, 2)
 int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
-                    const double* b, double* out, double shift, const double* nU2,
-                    const double* nz2, const int* done, cudaStream_t s);
+                    const double* b, double* out, double shift, const double* eps2,
+                    const int* done, cudaStream_t s);
 // blocks.cu
 int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
-                       const int* done, cudaStream_t s);
+                       const int* done, cudaStream_t s, bool with_eps = false);
 int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s);
 // krylov.cu
-int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s);
+int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s, bool with_eps = false);
+EpsArgs eps_args(fr_ctx* ctx, bool on);
 int launch_lincomb(fr_ctx* ctx, double* out, int nterms, const double* const* xs,
                    const double* coefs, double* sumsq, cudaStream_t s);
 int launch_copy(fr_ctx* ctx, double* dst, const double* src, cudaStream_t s);

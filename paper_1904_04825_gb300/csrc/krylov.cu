@@ -20,7 +20,8 @@ unsigned vgrid(long long n) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-__global__ void k_sumsq(const double* __restrict__ x, long long n, double* out, Reduce red) {
+__global__ void k_sumsq(const double* __restrict__ x, long long n, double* out, Reduce red,
+                        EpsArgs ea) {
   __shared__ double sh[32];
   double ss = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -28,7 +29,10 @@ __global__ void k_sumsq(const double* __restrict__ x, long long n, double* out, 
     ss = fma(x[i], x[i], ss);
   const double bs = block_sum(ss, sh);
   if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-  if (last_block(red.counter)) finish_sums(red, 1, out);
+  if (last_block(red.counter)) {
+    finish_sums(red, 1, out);
+    if (threadIdx.x == 0) write_eps(ea, *out);
+  }
 }
 
 struct Lincomb {
@@ -55,54 +59,107 @@ __global__ void k_lincomb(double* out, long long len, const Lincomb lc, double* 
   }
 }
 
-// out[i] = <V_i, w>, i < nvec (nvec <= kMaxVec); chunks of 8 vectors per sweep
-__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long long ldv, int nvec,
-                                              const double* __restrict__ w, long long n, double* out,
-                                              Reduce red, const int* done) {
-  __shared__ double sh[32];
-  if (done && *done) return;
-  for (int c0 = 0; c0 < nvec; c0 += 8) {
-    const int nc = min(8, nvec - c0);
-    double acc[8];
+// One sweep over the rows accumulating NC dot products against w; the
+// basis pointers are resolved outside the row loop so every row costs
+// exactly NC fused multiply-adds on the FP64 pipe.
+template <int NC>
+__device__ __forceinline__ void dots_chunk(const double* const* ptr, const double* __restrict__ w,
+                                           long long n, double* acc) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (long long)gridDim.x * blockDim.x) {
-      const double wr = w[r];
+  for (int i = 0; i < NC; ++i) acc[i] = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const double wr = w[r];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i < nc) acc[i] = fma(V[(c0 + i) * ldv + r], wr, acc[i]);
-    }
-    for (int i = 0; i < nc; ++i) {
-      const double bs = block_sum(acc[i], sh);
-      if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec + c0 + i] = bs;
-    }
+    for (int i = 0; i < NC; ++i) acc[i] = fma(ptr[i][r], wr, acc[i]);
   }
-  if (last_block(red.counter)) finish_sums(red, nvec, out);
 }
 
-// w -= sum_i h_i V_i, optional sum of squares of the new w
+// out[i] = <V_i, w> for i < nvec, and out[nvec] = <w, w> when with_self,
+// in chunks of up to 8 values per sweep.  Skipped when the cycle is done or
+// when `gate` points at a zero flag.
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long long ldv, int nvec,
+                                              const double* __restrict__ w, long long n, double* out,
+                                              int with_self, Reduce red, const int* done,
+                                              const int* gate) {
+  __shared__ double sred[8][kThreads / 32];
+  if ((done && *done) || (gate && !*gate)) return;
+  const int total = nvec + (with_self ? 1 : 0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < total; c0 += 8) {
+    const int nc = min(8, total - c0);
+    const double* ptr[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int idx = c0 + i;
+      ptr[i] = idx < nvec ? V + (size_t)idx * ldv : w;
+    }
+    double acc[8];
+    switch (nc) {
+      case 1: dots_chunk<1>(ptr, w, n, acc); break;
+      case 2: dots_chunk<2>(ptr, w, n, acc); break;
+      case 3: dots_chunk<3>(ptr, w, n, acc); break;
+      case 4: dots_chunk<4>(ptr, w, n, acc); break;
+      case 5: dots_chunk<5>(ptr, w, n, acc); break;
+      case 6: dots_chunk<6>(ptr, w, n, acc); break;
+      case 7: dots_chunk<7>(ptr, w, n, acc); break;
+      default: dots_chunk<8>(ptr, w, n, acc); break;
+    }
+    for (int i = 0; i < nc; ++i) {
+      const double t = warp_sum(acc[i]);
+      if (lane == 0) sred[i][wid] = t;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nc) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sred[threadIdx.x][q];
+      red.partials[(size_t)blockIdx.x * kMaxVec + c0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (last_block(red.counter)) finish_sums(red, total, out);
+}
+
+// w -= sum_i h_i V_i as one FMA chain per row (exactly nvec FP64 FMAs); optional sum of
+// squares of the new w.  With `self2` (the first Gram-Schmidt pass) the last
+// block also decides whether iteration j needs the second pass: it does when
+// ||w_new||^2 < ||w_old||^2 / 2 (the "twice is enough" test with
+// eta = 1/sqrt 2), recorded in rflag[j]; otherwise h2 is cleared.
+struct Reorth {
+  const double* self2;  // ||w||^2 before the first pass, or nullptr
+  int* rflag;           // &rflag[j]
+  double* h2;
+};
+
 __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const double* __restrict__ V,
                                                 long long ldv, int nvec, const double* h,
                                                 long long n, double* sumsq, Reduce red,
-                                                const int* done) {
+                                                const int* done, const int* gate, Reorth ro) {
   __shared__ double sh[32];
   __shared__ double hs[kMaxVec];
-  if (done && *done) return;
-  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  if ((done && *done) || (gate && !*gate)) return;
+  if (threadIdx.x < nvec) hs[threadIdx.x] = -h[threadIdx.x];
   __syncthreads();
   double ss = 0.0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
     double v = w[r];
-    for (int i = 0; i < nvec; ++i) v = fma(-hs[i], V[i * ldv + r], v);
+    for (int i = 0; i < nvec; ++i) v = fma(hs[i], V[i * ldv + r], v);
     w[r] = v;
-    ss = fma(v, v, ss);
+    if (sumsq) ss = fma(v, v, ss);
   }
   if (sumsq) {
     const double bs = block_sum(ss, sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-    if (last_block(red.counter)) finish_sums(red, 1, sumsq);
+    if (last_block(red.counter)) {
+      finish_sums(red, 1, sumsq);
+      if (ro.self2 && threadIdx.x == 0) {
+        const int need = (*sumsq < 0.5 * *ro.self2) ? 1 : 0;
+        *ro.rflag = need;
+        if (!need)
+          for (int q = 0; q < nvec; ++q) ro.h2[q] = 0.0;
+      }
+    }
   }
 }
 
@@ -117,6 +174,7 @@ __global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, 
   *gd.res = beta;
   *gd.k = 0;
   *gd.done = (beta <= target) ? 1 : 0;
+  for (int i = 0; i < m; ++i) gd.rflag[i] = 0;
   gd.invh[0] = beta > 0.0 ? 1.0 / beta : 0.0;
 }
 
@@ -174,8 +232,13 @@ __global__ void k_fill(double* dst, double v, long long n) {
 
 }  // namespace
 
-int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s) {
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red); }
+EpsArgs eps_args(fr_ctx* ctx, bool on) {
+  EpsArgs ea{ctx->scal + S_NU2, ctx->opts.eps_rel, ctx->opts.eps_fixed, on ? ctx->scal + S_EPS : nullptr};
+  return ea;
+}
+
+int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s, bool with_eps) {
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red, eps_args(ctx, with_eps)); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -238,8 +301,8 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
     if (cycle == 0 && x_is_zero) {
       FRK_TRY(launch_copy(ctx, V, b, s));
     } else {
-      FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s));
-      FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_NU2, sc + S_NZ2, nullptr, s));
+      FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
+      FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, nullptr, s));
     }
     FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
     { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m); }
@@ -255,15 +318,17 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
         double* vj = V + (size_t)j * n;
         double* w = V + (size_t)(j + 1) * n;
         // v_j = r_j / ||r_j|| (written back), z = M^{-1} v_j, ||z||^2
-        FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s));
+        FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s, true));
         // w = A z
-        FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_NU2, sc + S_NZ2,
-                                gd.done, s));
-        // CGS2
-        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, ctx->red, gd.done); }
-        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, nullptr, ctx->red, gd.done); }
-        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, ctx->red, gd.done); }
-        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done); }
+        FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_EPS, gd.done, s));
+        // Gram-Schmidt: one classical pass, a second one only when the
+        // first removed more than half of ||w||^2 (decided on the device)
+        const Reorth none{nullptr, nullptr, nullptr};
+        const Reorth first{gd.h1 + (j + 1), gd.rflag + j, gd.h2};
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, 1, ctx->red, gd.done, nullptr); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, sc + S_NW2, ctx->red, gd.done, nullptr, first); }
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, 0, ctx->red, gd.done, gd.rflag + j); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done, gd.rflag + j, none); }
         { ProfScope ps_(ctx, FR_KF_OTHER, s); k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2); }
         FRK_LAUNCHED(ctx);
       }
@@ -282,6 +347,7 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
     FRK_LAUNCHED(ctx);
     FRK_TRY(launch_solution_update(ctx, x, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat, gd.k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat + 4, gd.rflag, m * sizeof(int), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, gd.res, sizeof(double), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 1, gd.target, sizeof(double), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 2, sc + S_NB2, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -295,21 +361,29 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
        // reading/writing w)
       const long long sk = launched - k;
       const double nd = (double)n;
+      long long second = 0;
       for (int j = 0; j < k; ++j) {
         const double kv = j + 1;
+        const int re = ctx->h_stat[4 + j];
+        second += re;
         if (ctx->opts.precond)
           prof_work(ctx, FR_KF_APPLY, 8.0 * (double)ctx->ne * ctx->nb * ctx->nb + 24.0 * nd, 2.0 * ctx->nb * nd);
         else
           prof_work(ctx, FR_KF_APPLY, 24.0 * nd, 3.0 * nd);
         prof_work(ctx, FR_KF_JV, 32.0 * nd, residual_flops_per_element(ctx->p) * (double)ctx->ne + 6.0 * nd);
-        prof_work(ctx, FR_KF_DOTS, 2 * 8.0 * (kv + 1) * nd, 2 * 2.0 * kv * nd);
-        prof_work(ctx, FR_KF_UPDATE, 2 * 8.0 * (kv + 2) * nd, 2 * 2.0 * kv * nd + 2.0 * nd);
+        // pass 1: dots of j+1 basis vectors and w with w; update reads them and w, writes w
+        prof_work(ctx, FR_KF_DOTS, 8.0 * (kv + 1) * nd, 2.0 * (kv + 1) * nd);
+        prof_work(ctx, FR_KF_UPDATE, 8.0 * (kv + 2) * nd, 2.0 * kv * nd + 2.0 * nd);
+        if (re) {
+          prof_work(ctx, FR_KF_DOTS, 8.0 * (kv + 1) * nd, 2.0 * kv * nd);
+          prof_work(ctx, FR_KF_UPDATE, 8.0 * (kv + 2) * nd, 2.0 * kv * nd + 2.0 * nd);
+        }
       }
       Prof& P = ctx->prof;
       P.skipped[FR_KF_APPLY] += sk;
       P.skipped[FR_KF_JV] += sk;
-      P.skipped[FR_KF_DOTS] += 2 * sk;
-      P.skipped[FR_KF_UPDATE] += 2 * sk;
+      P.skipped[FR_KF_DOTS] += 2 * sk + (k - second);
+      P.skipped[FR_KF_UPDATE] += 2 * sk + (k - second);
       P.skipped[FR_KF_OTHER] += sk;
     }
     if (!std::isfinite(res) || !std::isfinite(bn)) {

@@ -3,7 +3,9 @@
 // One thread per (element, solution point); EPB = 256 / Np elements per CTA.
 // Per element, in shared memory: the (possibly perturbed) state, the
 // transformed fluxes F = (hy/2) f, G = (hx/2) g at the solution points, and
-// the common fluxes F^num on the 4 (p+1) face points.  A face point's own
+// the common fluxes F^num on the 4 (p+1) face points.  Fluxes are kept in
+// physical form (f, g, f_n); the metric factors |J| |grad xi| / |J| = 2/hx,
+// 2/hy are applied once per output.  A face point's own
 // trace comes from shared memory, the neighbour's from global memory (L2),
 // both summed in the same order with the same coefficients, so the two
 // elements sharing a face compute bit-identical common fluxes (discrete
@@ -23,8 +25,7 @@ struct ResArgs {
   double* out;
   const double* hx;
   const double* hy;
-  const double* nU2;
-  const double* nz2;
+  const double* eps2;  // (eps, 1/eps) of the FD product
   const int* done;
   long long ne;
   int nx, ny;
@@ -80,10 +81,10 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   const long long e = (long long)blockIdx.x * EPB + el;
   const bool active = e < a.ne;
 
-  double eps = 0.0;
+  double eps = 0.0, ieps = 0.0;
   if (PERTURB) {
-    const double nz2 = *a.nz2;
-    if (nz2 > 0.0) eps = a.eps_fixed > 0.0 ? a.eps_fixed : a.eps_rel * (1.0 + sqrt(*a.nU2)) / sqrt(nz2);
+    eps = a.eps2[0];
+    ieps = a.eps2[1];
   }
   int ix = 0, iy = 0;
   double hx = 1.0, hy = 1.0;
@@ -103,8 +104,8 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     euler_fluxes(q, a.gam, f, g);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      sF[el][v][t] = 0.5 * hy * f[v];
-      sG[el][v][t] = 0.5 * hx * g[v];
+      sF[el][v][t] = f[v];
+      sG[el][v][t] = g[v];
     }
   }
   __syncthreads();
@@ -132,19 +133,17 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
       const int dir = face < 2 ? 0 : 1;
       if (face == 0 || face == 2) rusanov(qn, qo, dir, a.gam, fc);
       else rusanov(qo, qn, dir, a.gam, fc);
-      const double scale = face < 2 ? 0.5 * hy : 0.5 * hx;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sFn[el][face][v][k] = scale * fc[v];
+      for (int v = 0; v < 4; ++v) sFn[el][face][v][k] = fc[v];
     }
   }
   __syncthreads();
 
   if (!active) return;
   const int i = t % N, j = t / N;
-  const double sJ = 4.0 / (hx * hy);
+  // with unscaled fluxes, -(1/|J|)(dF~/dxi + dG~/deta) = -(2/hx) df~ - (2/hy) dg~
+  const double sx = 2.0 / hx, sy = 2.0 / hy;
   const long long base = e * 4 * NP + t;
-  double dnorm = 0.0;
-  (void)dnorm;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     double dF = sdgL[i] * sFn[el][0][v][j];
@@ -155,13 +154,13 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     dG = fma(sdgR[j], sFn[el][3][v][i], dG);
 #pragma unroll
     for (int k = 0; k < N; ++k) dG = fma(sDt[j][k], sG[el][v][i + N * k], dG);
-    const double R = -(dF + dG) * sJ;
+    const double R = -fma(sx, dF, sy * dG);
     const long long o = base + v * NP;
     if (MODE == 0) {
       a.out[o] = R;
     } else {
       const double zo = a.z[o];
-      const double Az = eps > 0.0 ? a.shift * zo - (R - a.R0[o]) / eps : a.shift * zo;
+      const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
       a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
     }
   }
@@ -189,11 +188,11 @@ int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
 }  // namespace
 
 int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
-                    const double* b, double* out, double shift, const double* nU2,
-                    const double* nz2, const int* done, cudaStream_t s) {
+                    const double* b, double* out, double shift, const double* eps2,
+                    const int* done, cudaStream_t s) {
   ResArgs a;
   a.U = U; a.z = z; a.R0 = R0; a.b = b; a.out = out;
-  a.hx = ctx->hx; a.hy = ctx->hy; a.nU2 = nU2; a.nz2 = nz2; a.done = done;
+  a.hx = ctx->hx; a.hy = ctx->hy; a.eps2 = eps2; a.done = done;
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
   a.gam = ctx->opts.gamma; a.shift = shift;
   a.eps_rel = ctx->opts.eps_rel; a.eps_fixed = ctx->opts.eps_fixed;

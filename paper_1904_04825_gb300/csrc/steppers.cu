@@ -172,7 +172,7 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
   double* dq = ctx->buf[B_DQ];
   double* nF2 = ctx->scal + S_NF2;
   auto eval_F = [&](double* Fn) -> int {
-    FRK_TRY(launch_residual(ctx, 0, q, nullptr, nullptr, nullptr, Rq, 0.0, nullptr, nullptr, nullptr, s));
+    FRK_TRY(launch_residual(ctx, 0, q, nullptr, nullptr, nullptr, Rq, 0.0, nullptr, nullptr, s));
     st->residual_evals += 1;
     const double* xs[3] = {q, cst, Rq};
     const double cs[3] = {1.0 / omega_dt, -1.0 / omega_dt, -1.0};
@@ -247,7 +247,7 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
   st.converged = 1;
   const double shift = 1.0 / (t.gamma * dt);
   double* R0 = ctx->buf[B_R0];
-  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R0, 0.0, nullptr, nullptr, nullptr, s));
+  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R0, 0.0, nullptr, nullptr, s));
   st.residual_evals += 1;
   if (ctx->opts.precond) {
     FRK_TRY(launch_block_factor(ctx, U, shift, s));
@@ -265,7 +265,7 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
       for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.a[i][j]; }
       FRK_TRY(launch_lincomb(ctx, ctx->buf[B_STAGE], i + 1, xs, cs, nullptr, s));
       FRK_TRY(launch_residual(ctx, 0, ctx->buf[B_STAGE], nullptr, nullptr, nullptr, ctx->buf[B_RSTAGE],
-                              0.0, nullptr, nullptr, nullptr, s));
+                              0.0, nullptr, nullptr, s));
       st.residual_evals += 1;
       Ri = ctx->buf[B_RSTAGE];
     }
@@ -312,7 +312,7 @@ extern "C" int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const 
   st.converged = 1;
   // stage residuals R(q_j) in B_Y0 + j
   FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, ctx->buf[B_Y0], 0.0, nullptr, nullptr,
-                          nullptr, s));
+                          s));
   st.residual_evals += 1;
   double* q = ctx->buf[B_Q];
   FRK_TRY(launch_copy(ctx, q, U, s));
