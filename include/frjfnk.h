@@ -67,6 +67,9 @@ typedef struct fr_opts {
   int gmres_m;           /* restart length used by the steppers (30) */
   int gmres_max_restarts;/* restart limit used by the steppers (20) */
   double tol_lin;        /* ROW: GMRES relative tolerance tol_rel,linear (1e-8) */
+  double reorth_eta;     /* Arnoldi: classical Gram-Schmidt, repeated once when the
+                            first pass leaves ||w|| < reorth_eta ||w_in|| (1/64);
+                            1 = always two passes (the paper names no variant) */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with

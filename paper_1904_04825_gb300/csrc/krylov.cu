@@ -61,17 +61,34 @@ __global__ void k_lincomb(double* out, long long len, const Lincomb lc, double* 
 
 // One sweep over the rows accumulating NC dot products against w; the
 // basis pointers are resolved outside the row loop so every row costs
-// exactly NC fused multiply-adds on the FP64 pipe.
+// exactly NC fused multiply-adds on the FP64 pipe.  UR rows are in flight per
+// thread (NC x UR independent accumulation chains hide the FMA latency).
 template <int NC>
 __device__ __forceinline__ void dots_chunk(const double* const* ptr, const double* __restrict__ w,
                                            long long n, double* acc) {
+  constexpr int UR = NC >= 8 ? 1 : (NC >= 4 ? 2 : 4);
+  double a[NC][UR];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) acc[i] = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-       r += (long long)gridDim.x * blockDim.x) {
-    const double wr = w[r];
+  for (int i = 0; i < NC; ++i)
 #pragma unroll
-    for (int i = 0; i < NC; ++i) acc[i] = fma(ptr[i][r], wr, acc[i]);
+    for (int u = 0; u < UR; ++u) a[i][u] = 0.0;
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
+    double wr[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) wr[u] = (r0 + u * S < n) ? w[r0 + u * S] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i)
+#pragma unroll
+      for (int u = 0; u < UR; ++u)
+        if (r0 + u * S < n) a[i][u] = fma(ptr[i][r0 + u * S], wr[u], a[i][u]);
+  }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    double s = a[i][0];
+#pragma unroll
+    for (int u = 1; u < UR; ++u) s += a[i][u];
+    acc[i] = s;
   }
 }
 
@@ -123,10 +140,13 @@ __global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long
 // w -= sum_i h_i V_i as one FMA chain per row (exactly nvec FP64 FMAs); optional sum of
 // squares of the new w.  With `self2` (the first Gram-Schmidt pass) the last
 // block also decides whether iteration j needs the second pass: it does when
-// ||w_new||^2 < ||w_old||^2 / 2 (the "twice is enough" test with
-// eta = 1/sqrt 2), recorded in rflag[j]; otherwise h2 is cleared.
+// ||w_new|| < eta ||w_old|| (the test of Daniel, Gragg, Kaufman and Stewart;
+// one classical pass leaves an orthogonality error of about
+// u ||w_old|| / ||w_new||, so eta = 1/64 keeps it below ~64 u), recorded in
+// rflag[j]; otherwise h2 is cleared.
 struct Reorth {
   const double* self2;  // ||w||^2 before the first pass, or nullptr
+  double eta2;          // second pass when ||w_new||^2 < eta2 ||w_old||^2
   int* rflag;           // &rflag[j]
   double* h2;
 };
@@ -140,21 +160,36 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
   if ((done && *done) || (gate && !*gate)) return;
   if (threadIdx.x < nvec) hs[threadIdx.x] = -h[threadIdx.x];
   __syncthreads();
-  double ss = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-       r += (long long)gridDim.x * blockDim.x) {
-    double v = w[r];
-    for (int i = 0; i < nvec; ++i) v = fma(hs[i], V[i * ldv + r], v);
-    w[r] = v;
-    if (sumsq) ss = fma(v, v, ss);
+  // four rows per thread in flight: four independent FMA chains of length nvec
+  constexpr int UR = 4;
+  double ss[UR] = {0.0, 0.0, 0.0, 0.0};
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
+    double v[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) v[u] = (r0 + u * S < n) ? w[r0 + u * S] : 0.0;
+    for (int i = 0; i < nvec; ++i) {
+      const double hi = hs[i];
+      const double* Vi = V + i * ldv;
+#pragma unroll
+      for (int u = 0; u < UR; ++u)
+        if (r0 + u * S < n) v[u] = fma(hi, Vi[r0 + u * S], v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      if (r0 + u * S < n) {
+        w[r0 + u * S] = v[u];
+        if (sumsq) ss[u] = fma(v[u], v[u], ss[u]);
+      }
+    }
   }
   if (sumsq) {
-    const double bs = block_sum(ss, sh);
+    const double bs = block_sum((ss[0] + ss[1]) + (ss[2] + ss[3]), sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
     if (last_block(red.counter)) {
       finish_sums(red, 1, sumsq);
       if (ro.self2 && threadIdx.x == 0) {
-        const int need = (*sumsq < 0.5 * *ro.self2) ? 1 : 0;
+        const int need = (*sumsq < ro.eta2 * *ro.self2) ? 1 : 0;
         *ro.rflag = need;
         if (!need)
           for (int q = 0; q < nvec; ++q) ro.h2[q] = 0.0;
@@ -322,9 +357,9 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
         // w = A z
         FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_EPS, gd.done, s));
         // Gram-Schmidt: one classical pass, a second one only when the
-        // first removed more than half of ||w||^2 (decided on the device)
-        const Reorth none{nullptr, nullptr, nullptr};
-        const Reorth first{gd.h1 + (j + 1), gd.rflag + j, gd.h2};
+        // first shrank ||w|| below reorth_eta ||w|| (decided on the device)
+        const Reorth none{nullptr, 0.0, nullptr, nullptr};
+        const Reorth first{gd.h1 + (j + 1), ctx->opts.reorth_eta * ctx->opts.reorth_eta, gd.rflag + j, gd.h2};
         { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, 1, ctx->red, gd.done, nullptr); }
         { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, sc + S_NW2, ctx->red, gd.done, nullptr, first); }
         { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, 0, ctx->red, gd.done, gd.rflag + j); }

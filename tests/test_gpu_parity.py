@@ -239,6 +239,30 @@ def test_gmres_matches_oracle(fr, precond):
     assert abs(rg - ro) <= 1e-3 * ro + 1e-9 * np.linalg.norm(b0)
 
 
+@pytest.mark.parametrize("eta", [0.0, 1.0 / 64.0, 1.0])
+def test_gmres_orthogonalisation_variants_track_mgs(fr, eta):
+    """One classical Gram-Schmidt pass (eta = 0), the selective second pass
+    (default) and always two passes (eta = 1) all follow the oracle's
+    modified Gram-Schmidt: same iterations, same answer."""
+    p = 3
+    xe, ye, X, Y = _case("uniform", 8, 8, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    b0 = R0.copy()
+    shift = 1.0 / (0.43586652150845900 * 0.2)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(reorth_eta=eta))
+    U = _t(U0)
+    fr.ejacobi_factor(ctx, U, None, shift)
+    x = ctx.empty().zero_()
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=30, rtol=1e-10, max_restarts=20)
+    Minv = ElementJacobi(element_blocks(prob, U0, shift))
+    xo, io = gmres(lambda v: fd_jv(prob, U0, R0, v, shift), b0, None, 30, 1e-10, 20, Minv)
+    assert info.converged and io.converged
+    assert abs(info.iters - io.iters) <= 1
+    assert _rel(x.cpu().numpy(), xo) < 1e-7
+
+
 def test_gmres_restarts_and_not_converged_status(fr):
     p = 2
     xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)

@@ -59,6 +59,7 @@ def test_defaults_and_argument_checks_without_gpu(libpath):
     import paper_1904_04825_gb300 as fr
     o = fr.default_opts()
     assert o.gamma == 1.4 and o.m_max == 30 and o.eps_rel == 1e-7 and o.precond == 1
+    assert o.reorth_eta == 1.0 / 64.0
     po = fr.default_ptc_opts()
     assert po.dtau_max == 1e20 and po.tol_lin == 0.1 and po.reject_above == 0.1
     h = ctypes.c_void_p()
