@@ -179,6 +179,28 @@ int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts
 int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
               const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
 
+/* ---- allocation-free variant (no counterpart in the paper) -------------
+ * y = shift*z - (R(U + eps z) - R0)/eps exactly as fr_jv computes it, but
+ * without a context and without allocating device memory.  It is for
+ * callers that cannot call cudaMalloc at the point where they need the
+ * product: applications whose own allocator has reserved the GPU's memory
+ * up front, or code that must not allocate after start-up (cudaMalloc can
+ * synchronise the device and fail under memory pressure).
+ *  - Working memory is one fixed static device array inside the library
+ *    (about 250 KB, held on every GPU that loads the library until the
+ *    process exits).  It limits the mesh to 2 <= nx, ny <= 4096; larger
+ *    meshes are rejected with FR_ERR_INVALID_ARG.  p must be 2, 3 or 4.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; calls
+ *    that overlap on the GPU (other streams, other host threads) race.
+ *    Serialise them on one stream.
+ *  - mesh: HOST edge arrays (copied on `stream`); opts may be NULL
+ *    (defaults; gamma, eps_rel and eps_fixed are used).  U, R0, z, y: device,
+ *    ndof doubles as for fr_jv.  Errors are reported by fr_last_error(NULL). */
+int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opts, const double* U,
+                  const double* R0, const double* z, double shift, double* y, void* stream);
+
 /* ---- measurement hooks (no counterpart in the paper) -------------------
  * Kernel families for fr_profile_*: */
 enum {

@@ -102,6 +102,7 @@ def _load():
         "step_bdf2": (I, [P, D, P, P, I, ctypes.POINTER(fr_ptc_opts),
                           ctypes.POINTER(fr_step_stats), V]),
         "fr_kernel_launches": (ctypes.c_longlong, []),
+        "fr_jv_noalloc": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts), P, P, P, D, P, V]),
         "fr_profile_begin": (I, [P, ctypes.c_uint]),
         "fr_profile_end": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -293,3 +294,19 @@ def fr_profile_end(ctx: Context):
     ctx.check(lib.fr_profile_end(ctx.handle, ms, n, by, fl))
     return {KF_NAMES[i]: {"ms": ms[i], "launches": n[i], "bytes": by[i], "flops": fl[i]}
             for i in range(FR_KF_COUNT) if n[i] > 0 or ms[i] > 0}
+
+
+def fr_jv_noalloc(x_edges, y_edges, p: int, U, R0, z, shift, y, opts: fr_opts | None = None, stream=None):
+    """fr_jv without a context and without device allocation (see the C
+    header: fixed static working memory, meshes up to 4096 x 4096, calls must
+    not overlap on the GPU)."""
+    xe = np.ascontiguousarray(x_edges, dtype=np.float64)
+    ye = np.ascontiguousarray(y_edges, dtype=np.float64)
+    desc = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
+                        xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    rc = lib.fr_jv_noalloc(ctypes.byref(desc), int(p), ctypes.byref(opts) if opts is not None else None,
+                           _ptr(U), _ptr(R0), _ptr(z), float(shift), _ptr(y), _stream(stream))
+    if rc != FR_OK:
+        raise FrError(rc, lib.fr_last_error(None).decode())
+    return rc

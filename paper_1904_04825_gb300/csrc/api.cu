@@ -127,7 +127,7 @@ int check_vec(fr_ctx* ctx, const void* p, const char* name) {
   return FR_OK;
 }
 
-char g_static_err[256] = "invalid context";
+char g_static_err[512] = "invalid context";
 
 // harvest the recorded event pairs of one family into ms / n
 void prof_harvest(fr_ctx* c, int f) {
@@ -146,6 +146,11 @@ void prof_harvest(fr_ctx* c, int f) {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_static_error(const char* msg) {
+  std::strncpy(g_static_err, msg, sizeof(g_static_err) - 1);
+  g_static_err[sizeof(g_static_err) - 1] = 0;
+}
 
 void prof_begin(fr_ctx* c, int f, cudaStream_t s) {
   count_launch();

@@ -113,6 +113,8 @@ struct fr_ctx {
 namespace frk {
 
 int set_error(fr_ctx* ctx, int code, const char* fmt, ...);
+// message returned by fr_last_error(NULL) (calls without a context)
+void set_static_error(const char* msg);
 
 #define FRK_CUDA(ctx, call)                                                           \
   do {                                                                               \
