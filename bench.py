@@ -200,7 +200,9 @@ def our_arm(args):
     xe, ye = S.uniform_mesh(NX)
     X, Y = S.point_coords(xe, ye, P)
     U0 = S.Vortex().state(X, Y)
-    ctx = fr.Context(xe, ye, P, fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20))
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
+    ctx = fr.Context(xe, ye, P, fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20,
+                                                block_precision=prec))
     U = torch.from_numpy(U0).to(dev)
     stream = torch.cuda.current_stream()
 
@@ -311,11 +313,14 @@ def our_arm(args):
                          f"CFL 13.6 and tol 1e-6, {it} GMRES iterations, {secs:.1f} s), NumPy on 1 host thread"}
 
     line = {
-        "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC if prec == 0 else METRIC.replace("plain FP64", f"{args.block_precision} blocks"),
+        "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
+                           "block_precision": args.block_precision,
+                           "workload": WORKLOAD if prec == 0 else WORKLOAD + f"-{args.block_precision}blocks",
                            "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / DT)}),
         "gpu_launches": launches,
         "clocks": clk,
@@ -382,6 +387,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
+                    help="element-Jacobi block precision (fp64 = the plain method)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -70,6 +70,11 @@ typedef struct fr_opts {
   double reorth_eta;     /* Arnoldi: classical Gram-Schmidt, repeated once when the
                             first pass leaves ||w|| < reorth_eta ||w_in|| (1/64);
                             1 = always two passes (the paper names no variant) */
+  int block_precision;   /* element-Jacobi blocks: 0 = FP64 (default); 1 = FP32
+                            inversion and storage; 2 = FP32 inversion, BF16
+                            storage.  The FD columns, the FD matvec, Arnoldi and
+                            all updates stay FP64 (reduced precision changes
+                            only the preconditioner, not the converged answer) */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with

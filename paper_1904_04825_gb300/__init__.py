@@ -55,7 +55,8 @@ class fr_opts(ctypes.Structure):
                 ("eps_rel", ctypes.c_double), ("eps_fixed", ctypes.c_double),
                 ("block_eps_rel", ctypes.c_double), ("precond", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("gmres_max_restarts", ctypes.c_int),
-                ("tol_lin", ctypes.c_double), ("reorth_eta", ctypes.c_double)]
+                ("tol_lin", ctypes.c_double), ("reorth_eta", ctypes.c_double),
+                ("block_precision", ctypes.c_int)]
 
 
 class fr_ptc_opts(ctypes.Structure):

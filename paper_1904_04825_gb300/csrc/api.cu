@@ -209,6 +209,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->gmres_max_restarts = 20;
   o->tol_lin = 1e-8;
   o->reorth_eta = 1.0 / 64.0;
+  o->block_precision = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -233,7 +234,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
   if (opts) o = *opts;
   if (o.m_max < 1 || o.m_max > kMaxVec - 1 || o.gmres_m < 1 || o.gmres_m > o.m_max ||
       o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
-      !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0))
+      !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2)
     return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

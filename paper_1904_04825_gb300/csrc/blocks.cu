@@ -9,6 +9,8 @@
 // and column a changes.  Each thread forms one column from those changes
 // (mathematically the same forward difference R_e(q + eps e_j) - R_e(q)
 // over eps; entries outside the cross are exactly zero in both forms).
+#include <cuda_bf16.h>
+
 #include "device.cuh"
 
 namespace frk {
@@ -16,7 +18,7 @@ namespace {
 
 struct FactorArgs {
   const double* U;
-  double* blocks;    // [ne][nb][nb], column-major inverse per element: Minv[k*nb + i]
+  void* blocks;      // [ne][nb][nb] of S, column-major inverse per element: Minv[k*nb + i]
   const double* hx;
   const double* hy;
   long long ne;
@@ -27,22 +29,31 @@ struct FactorArgs {
   Tables tab;
 };
 
-template <int P>
+template <int P, typename T>
 struct FactorLayout {
   static constexpr int N = P + 1, NP = N * N, NB = 4 * NP, LD = NB + 1;
   static constexpr int THREADS = NB <= 64 ? 128 : 256;
-  // shared memory (doubles)
-  static constexpr int OFF_M = 0;                       // NB x LD
-  static constexpr int OFF_Q = OFF_M + NB * LD;         // 4 x NP state
+  // shared memory: doubles first, then the block (type T), its pivot column and pivots
+  static constexpr int OFF_Q = 0;                       // 4 x NP state
   static constexpr int OFF_F = OFF_Q + 4 * NP;          // 4 x NP  (hy/2) f
   static constexpr int OFF_G = OFF_F + 4 * NP;          // 4 x NP  (hx/2) g
   static constexpr int OFF_TR = OFF_G + 4 * NP;         // own traces [4 faces][4 vars][N]
   static constexpr int OFF_NT = OFF_TR + 16 * N;        // neighbour traces [4][4][N]
   static constexpr int OFF_FN = OFF_NT + 16 * N;        // base common fluxes [4][4][N] (scaled)
-  static constexpr int OFF_COL = OFF_FN + 16 * N;       // pivot column NB
-  static constexpr int TOTAL = OFF_COL + NB;
-  static constexpr size_t BYTES = TOTAL * sizeof(double) + 2 * NB * sizeof(int) + 64;
+  static constexpr int DOUBLES = OFF_FN + 16 * N;
+  static constexpr size_t BYTES = DOUBLES * sizeof(double) + (size_t)(NB * LD + NB) * sizeof(T) +
+                                  NB * sizeof(int) + 64;
 };
+
+template <typename S> struct StoreT;
+template <> struct StoreT<double> { __device__ static double to(double x) { return x; } };
+template <> struct StoreT<float> { __device__ static float to(float x) { return x; } };
+template <> struct StoreT<__nv_bfloat16> {
+  __device__ static __nv_bfloat16 to(float x) { return __float2bfloat16_rn(x); }
+};
+__device__ __forceinline__ double load_acc(const double* p) { return *p; }
+__device__ __forceinline__ float load_acc(const float* p) { return *p; }
+__device__ __forceinline__ float load_acc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
 template <int N>
 __device__ __forceinline__ double tsum(const double* x, int stride, const double* c) {
@@ -52,27 +63,29 @@ __device__ __forceinline__ double tsum(const double* x, int stride, const double
   return s;
 }
 
-template <int P>
-__global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const FactorArgs a) {
-  using L = FactorLayout<P>;
+// T: arithmetic of the Gauss-Jordan inversion (double, or float for the
+// reduced-precision preconditioner); S: storage type of the inverse blocks.
+// The finite-difference columns are always formed in FP64.
+template <int P, typename T, typename S>
+__global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const FactorArgs a) {
+  using L = FactorLayout<P, T>;
   constexpr int N = L::N, NP = L::NP, NB = L::NB, LD = L::LD;
   extern __shared__ double smem[];
-  double* M = smem + L::OFF_M;
   double* q = smem + L::OFF_Q;
   double* F = smem + L::OFF_F;
   double* G = smem + L::OFF_G;
   double* tr = smem + L::OFF_TR;
   double* nt = smem + L::OFF_NT;
   double* fn = smem + L::OFF_FN;
-  double* col = smem + L::OFF_COL;
-  int* piv = reinterpret_cast<int*>(smem + L::TOTAL);
-  __shared__ int s_prow;
+  T* M = reinterpret_cast<T*>(smem + L::DOUBLES);
+  T* col = M + NB * LD;
+  int* piv = reinterpret_cast<int*>(col + NB);
 
   const long long e = blockIdx.x;
   const int ix = (int)(e % a.nx), iy = (int)(e / a.nx);
   const double hx = a.hx[ix], hy = a.hy[iy];
   const double sJ = 4.0 / (hx * hy);
-  const Tables& T = a.tab;
+  const Tables& T_ = a.tab;
 
   // ---- base state, pointwise fluxes ----
   for (int t = threadIdx.x; t < NP; t += blockDim.x) {
@@ -100,8 +113,8 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
     else nbr = (long long)ix + (long long)a.nx * ((iy + 1) % a.ny);
     const int off = face < 2 ? N * k : k;
     const int stride = face < 2 ? 1 : N;
-    const double* co = (face == 0 || face == 2) ? T.lm : T.lp;
-    const double* cn = (face == 0 || face == 2) ? T.lp : T.lm;
+    const double* co = (face == 0 || face == 2) ? T_.lm : T_.lp;
+    const double* cn = (face == 0 || face == 2) ? T_.lp : T_.lm;
     double qo[4], qn[4], fc[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -122,8 +135,8 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
   // ---- columns of M = shift*I - J_ee ----
   for (int c = threadIdx.x; c < NB; c += blockDim.x) {
     const int vv = c / NP, pt = c % NP, ia = pt % N, jb = pt / N;
-    double* Mc = M + c;  // column c, row stride LD
-    for (int r = 0; r < NB; ++r) Mc[r * LD] = (r == c) ? a.shift : 0.0;
+    T* Mc = M + c;  // column c, row stride LD
+    for (int r = 0; r < NB; ++r) Mc[r * LD] = (r == c) ? (T)a.shift : (T)0;
     const double eps = a.beps * (1.0 + fabs(q[vv * NP + pt]));
     const double inv = 1.0 / eps;
     double qp[4], f[4], g[4], dF[4], dG[4];
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
 #pragma unroll
     for (int face = 0; face < 4; ++face) {
       const int k = face < 2 ? jb : ia;
-      const double cf = face == 0 ? T.lm[ia] : face == 1 ? T.lp[ia] : face == 2 ? T.lm[jb] : T.lp[jb];
+      const double cf = face == 0 ? T_.lm[ia] : face == 1 ? T_.lp[ia] : face == 2 ? T_.lm[jb] : T_.lp[jb];
       double qo[4], qn[4], fc[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -156,43 +169,52 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
 #pragma unroll
       for (int v = 0; v < 4; ++v) dFn[face][v] = sc * fc[v] - fn[(face * 4 + v) * N + k];
     }
-    // row jb: points (i, jb), x-direction change
+    // M = shift I - J with J = -sJ d / eps: row jb (x-direction change) and
+    // column ia (y-direction change); the point (ia, jb) gets both.  Each
+    // entry is formed in FP64 and stored once.
     for (int i = 0; i < N; ++i) {
       const int pnt = i + N * jb;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        double d = T.Dt[i][ia] * dF[v];
-        d = fma(T.dgL[i], dFn[0][v], d);
-        d = fma(T.dgR[i], dFn[1][v], d);
-        Mc[(v * NP + pnt) * LD] += sJ * d * inv;   // M = shift I - J, J = -sJ * d / eps
+        double d = T_.Dt[i][ia] * dF[v];
+        d = fma(T_.dgL[i], dFn[0][v], d);
+        d = fma(T_.dgR[i], dFn[1][v], d);
+        if (i == ia) {
+          d = fma(T_.Dt[jb][jb], dG[v], d);
+          d = fma(T_.dgL[jb], dFn[2][v], d);
+          d = fma(T_.dgR[jb], dFn[3][v], d);
+        }
+        const int row = v * NP + pnt;
+        Mc[row * LD] = (T)((row == c ? a.shift : 0.0) + sJ * d * inv);
       }
     }
-    // column ia: points (ia, j), y-direction change
     for (int j = 0; j < N; ++j) {
+      if (j == jb) continue;
       const int pnt = ia + N * j;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        double d = T.Dt[j][jb] * dG[v];
-        d = fma(T.dgL[j], dFn[2][v], d);
-        d = fma(T.dgR[j], dFn[3][v], d);
-        Mc[(v * NP + pnt) * LD] += sJ * d * inv;
+        double d = T_.Dt[j][jb] * dG[v];
+        d = fma(T_.dgL[j], dFn[2][v], d);
+        d = fma(T_.dgR[j], dFn[3][v], d);
+        Mc[(v * NP + pnt) * LD] = (T)(sJ * d * inv);
       }
     }
   }
   __syncthreads();
 
   // ---- in-place Gauss-Jordan inversion with partial (row) pivoting ----
+  __shared__ int s_prow;
   for (int k = 0; k < NB; ++k) {
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      T best = (T)-1;
       int bi = k;
       for (int r = k + (int)threadIdx.x; r < NB; r += 32) {
-        const double val = fabs(M[r * LD + k]);
+        const T val = fabs(M[r * LD + k]);
         if (val > best) { best = val; bi = r; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const T ob = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
@@ -202,7 +224,7 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
     const int r = s_prow;
     if (r != k) {
       for (int jj = threadIdx.x; jj < NB; jj += blockDim.x) {
-        const double tmp = M[k * LD + jj];
+        const T tmp = M[k * LD + jj];
         M[k * LD + jj] = M[r * LD + jj];
         M[r * LD + jj] = tmp;
       }
@@ -210,14 +232,14 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
     __syncthreads();
     for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) col[ii] = M[ii * LD + k];
     __syncthreads();
-    const double pinv = 1.0 / col[k];
+    const T pinv = (T)1 / col[k];
     for (int jj = threadIdx.x; jj < NB; jj += blockDim.x)
-      M[k * LD + jj] = (jj == k ? 1.0 : M[k * LD + jj]) * pinv;
+      M[k * LD + jj] = (jj == k ? (T)1 : M[k * LD + jj]) * pinv;
     __syncthreads();
     for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
       const int ii = idx / NB, jj = idx % NB;
       if (ii == k) continue;
-      M[ii * LD + jj] = (jj == k ? 0.0 : M[ii * LD + jj]) - col[ii] * M[k * LD + jj];
+      M[ii * LD + jj] = (jj == k ? (T)0 : M[ii * LD + jj]) - col[ii] * M[k * LD + jj];
     }
     __syncthreads();
   }
@@ -225,7 +247,7 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
     const int r = piv[k];
     if (r != k) {
       for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) {
-        const double tmp = M[ii * LD + k];
+        const T tmp = M[ii * LD + k];
         M[ii * LD + k] = M[ii * LD + r];
         M[ii * LD + r] = tmp;
       }
@@ -233,22 +255,23 @@ __global__ void __launch_bounds__(FactorLayout<P>::THREADS) k_factor(const Facto
     __syncthreads();
   }
   // ---- store column-major: Minv[k*NB + i] = inverse(i, k) ----
-  double* out = a.blocks + e * (long long)NB * NB;
+  S* out = reinterpret_cast<S*>(a.blocks) + e * (long long)NB * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     const int kk = idx / NB, ii = idx % NB;
-    out[idx] = M[ii * LD + kk];
+    out[idx] = StoreT<S>::to(M[ii * LD + kk]);
   }
 }
 
 // z = Minv r (optionally r scaled by *scale first and written back), optional
 // sum of squares of z.  EPC elements per CTA, one thread per block row.
-template <int NB>
-__global__ void __launch_bounds__(256) k_apply(const double* __restrict__ Minv, double* r,
+// S: block storage type; A: accumulation type (FP64 for FP64 blocks, FP32 otherwise).
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(256) k_apply(const S* __restrict__ Minv, double* r,
                                                const double* scale, double* __restrict__ z,
                                                long long ne, double* sumsq, Reduce red,
                                                const int* done, EpsArgs ea) {
   constexpr int EPC = 256 / NB;
-  __shared__ double rs[EPC][NB];
+  __shared__ A rs[EPC][NB];
   __shared__ double sh[32];
   if (done && *done) return;
   const int el = threadIdx.x / NB, i = threadIdx.x % NB;
@@ -264,18 +287,18 @@ __global__ void __launch_bounds__(256) k_apply(const double* __restrict__ Minv, 
         v *= s;
         r[e * NB + i] = v;
       }
-      rs[el][i] = v;
+      rs[el][i] = (A)v;
     }
     __syncthreads();
     if (act) {
-      const double* Me = Minv + e * (long long)NB * NB;
-      double acc0 = 0.0, acc1 = 0.0;
+      const S* Me = Minv + e * (long long)NB * NB;
+      A acc0 = 0, acc1 = 0;
 #pragma unroll 8
       for (int k = 0; k < NB; k += 2) {
-        acc0 = fma(Me[k * NB + i], rs[el][k], acc0);
-        if (k + 1 < NB) acc1 = fma(Me[(k + 1) * NB + i], rs[el][k + 1], acc1);
+        acc0 = fma(load_acc(Me + k * NB + i), rs[el][k], acc0);
+        if (k + 1 < NB) acc1 = fma(load_acc(Me + (k + 1) * NB + i), rs[el][k + 1], acc1);
       }
-      const double zi = acc0 + acc1;
+      const double zi = (double)(acc0 + acc1);
       z[e * NB + i] = zi;
       ss = fma(zi, zi, ss);
     }
@@ -318,13 +341,13 @@ __global__ void k_scale_copy(double* r, const double* scale, double* z, long lon
 }
 
 // x += Minv (sum_{l<k} y_l V_l) per element (precond) -- right-preconditioned update.
-template <int NB>
-__global__ void __launch_bounds__(256) k_solupdate(const double* __restrict__ Minv,
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(256) k_solupdate(const S* __restrict__ Minv,
                                                    const double* __restrict__ V, long long ldv,
                                                    const double* y, const int* kp, double* x,
                                                    long long ne) {
   constexpr int EPC = 256 / NB;
-  __shared__ double ts[EPC][NB];
+  __shared__ A ts[EPC][NB];
   __shared__ double ys[kMaxVec];
   const int k = *kp;
   if (k <= 0) return;
@@ -337,14 +360,14 @@ __global__ void __launch_bounds__(256) k_solupdate(const double* __restrict__ Mi
     if (act) {
       double t = 0.0;
       for (int l = 0; l < k; ++l) t = fma(ys[l], V[l * ldv + e * NB + i], t);
-      ts[el][i] = t;
+      ts[el][i] = (A)t;
     }
     __syncthreads();
     if (act) {
-      const double* Me = Minv + e * (long long)NB * NB;
-      double acc = 0.0;
-      for (int kk = 0; kk < NB; ++kk) acc = fma(Me[kk * NB + i], ts[el][kk], acc);
-      x[e * NB + i] += acc;
+      const S* Me = Minv + e * (long long)NB * NB;
+      A acc = 0;
+      for (int kk = 0; kk < NB; ++kk) acc = fma(load_acc(Me + kk * NB + i), ts[el][kk], acc);
+      x[e * NB + i] += (double)acc;
     }
   }
 }
@@ -365,17 +388,26 @@ __global__ void k_solupdate_plain(const double* __restrict__ V, long long ldv, c
   }
 }
 
-template <int P>
-int factor_p(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
-  using L = FactorLayout<P>;
-  FRK_CUDA(ctx, cudaFuncSetAttribute(k_factor<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int P, typename T, typename S>
+int factor_pts(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
+  using L = FactorLayout<P, T>;
+  FRK_CUDA(ctx, cudaFuncSetAttribute(k_factor<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)L::BYTES));
-  // work: read U (8 B/DOF), write ne nb^2 doubles; flops per element as counted
-  const double fb = 8.0 * (double)ctx->ndof + 8.0 * (double)ctx->ne * L::NB * L::NB;
+  // work: read U (8 B/DOF), write ne nb^2 entries of S; flops per element as counted
+  const double fb = 8.0 * (double)ctx->ndof + (double)sizeof(S) * (double)ctx->ne * L::NB * L::NB;
   const double ff = factor_flops_per_element(P) * (double)ctx->ne;
-  { ProfScope ps_(ctx, FR_KF_FACTOR, s, fb, ff); k_factor<P><<<(unsigned)ctx->ne, L::THREADS, L::BYTES, s>>>(a); }
+  { ProfScope ps_(ctx, FR_KF_FACTOR, s, fb, ff); k_factor<P, T, S><<<(unsigned)ctx->ne, L::THREADS, L::BYTES, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+template <int P>
+int factor_p(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
+  switch (ctx->opts.block_precision) {
+    case 1: return factor_pts<P, float, float>(ctx, a, s);
+    case 2: return factor_pts<P, float, __nv_bfloat16>(ctx, a, s);
+    default: return factor_pts<P, double, double>(ctx, a, s);
+  }
 }
 
 template <int NB>
@@ -386,27 +418,46 @@ unsigned apply_grid(long long ne) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-template <int NB>
-int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
-             const int* done, cudaStream_t s, bool with_eps) {
+template <int NB, typename S, typename A>
+int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
+              const int* done, cudaStream_t s, bool with_eps) {
   // work: ne nb^2 block entries, r in, z out (and r written back when scaled):
   // 2 nb flops per DOF.  Inside a GMRES cycle it is booked per finished iteration.
   const bool in_cycle = done != nullptr;
   const double nd = (double)ctx->ndof;
-  const double wb = in_cycle ? 0.0 : 8.0 * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
+  const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
-  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(ctx->blocks, r, scale, z, ctx->ne,
+  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB, S, A><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
                                                                   sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 template <int NB>
-int solupdate_nb(fr_ctx* ctx, double* x, cudaStream_t s) {
-  { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate<NB><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(
-      ctx->blocks, ctx->V, ctx->ndof, ctx->gd.y, ctx->gd.k, x, ctx->ne); }
+int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
+             const int* done, cudaStream_t s, bool with_eps) {
+  switch (ctx->opts.block_precision) {
+    case 1: return apply_nbs<NB, float, float>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 2: return apply_nbs<NB, __nv_bfloat16, float>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    default: return apply_nbs<NB, double, double>(ctx, r, scale, z, sumsq, done, s, with_eps);
+  }
+}
+
+template <int NB, typename S, typename A>
+int solupdate_nbs(fr_ctx* ctx, double* x, cudaStream_t s) {
+  { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate<NB, S, A><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(
+      reinterpret_cast<const S*>(ctx->blocks), ctx->V, ctx->ndof, ctx->gd.y, ctx->gd.k, x, ctx->ne); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+template <int NB>
+int solupdate_nb(fr_ctx* ctx, double* x, cudaStream_t s) {
+  switch (ctx->opts.block_precision) {
+    case 1: return solupdate_nbs<NB, float, float>(ctx, x, s);
+    case 2: return solupdate_nbs<NB, __nv_bfloat16, float>(ctx, x, s);
+    default: return solupdate_nbs<NB, double, double>(ctx, x, s);
+  }
 }
 
 unsigned vec_grid(long long n) {
