@@ -58,14 +58,25 @@ __device__ __forceinline__ double trace_global(const double* __restrict__ U,
   return s;
 }
 
+// Element tile handled by one CTA (TX x TY elements, one thread per point).
+template <int P> struct Tile;
+template <> struct Tile<2> { static constexpr int TX = 5, TY = 5; };
+template <> struct Tile<3> { static constexpr int TX = 4, TY = 4; };
+template <> struct Tile<4> { static constexpr int TX = 3, TY = 3; };
+
 template <int P, int MODE>
 __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
-  constexpr int N = P + 1, NP = N * N, EPB = 256 / NP, NFP = 4 * N;
+  constexpr int N = P + 1, NP = N * N;
+  constexpr int TX = Tile<P>::TX, TY = Tile<P>::TY, NE = TX * TY;
+  constexpr int NXF = (TX + 1) * TY * N;  // points on the tile's x-faces (normal +x)
+  constexpr int NYF = (TY + 1) * TX * N;  // points on the tile's y-faces (normal +y)
   constexpr bool PERTURB = MODE > 0;
-  __shared__ double sq[EPB][4][NP];
-  __shared__ double sF[EPB][4][NP];
-  __shared__ double sG[EPB][4][NP];
-  __shared__ double sFn[EPB][4][4][N];  // [face W,E,S,N][var][k]
+  __shared__ double sq[NE][4][NP];
+  __shared__ double sF[NE][4][NP];
+  __shared__ double sG[NE][4][NP];
+  __shared__ double str[NE][4][4][N];       // own traces [face W,E,S,N][var][k]
+  __shared__ double sfx[TY][TX + 1][4][N];  // common flux f_n on x-face xf of tile row ly
+  __shared__ double sfy[TX][TY + 1][4][N];  // common flux g_n on y-face yf of tile column lx
   __shared__ double sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
 
   if (a.done && *a.done) return;
@@ -77,22 +88,21 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     sdgR[threadIdx.x] = a.tab.dgR[threadIdx.x];
   }
 
+  const int tiles_x = (a.nx + TX - 1) / TX;
+  const int ix0 = (int)(blockIdx.x % tiles_x) * TX, iy0 = (int)(blockIdx.x / tiles_x) * TY;
+  const int ax = min(TX, a.nx - ix0), ay = min(TY, a.ny - iy0);  // active tile extent
   const int el = threadIdx.x / NP, t = threadIdx.x % NP;
-  const long long e = (long long)blockIdx.x * EPB + el;
-  const bool active = e < a.ne;
+  const int lx = el % TX, ly = el / TX;
+  const bool active = el < NE && lx < ax && ly < ay;
+  const long long e = (long long)(ix0 + lx) + (long long)a.nx * (iy0 + ly);
 
   double eps = 0.0, ieps = 0.0;
   if (PERTURB) {
     eps = a.eps2[0];
     ieps = a.eps2[1];
   }
-  int ix = 0, iy = 0;
-  double hx = 1.0, hy = 1.0;
+  // ---- 1: state (perturbed for A z) and pointwise fluxes ----
   if (active) {
-    ix = (int)(e % a.nx);
-    iy = (int)(e / a.nx);
-    hx = a.hx[ix];
-    hy = a.hy[iy];
     const long long base = e * 4 * NP + t;
     double q[4], f[4], g[4];
 #pragma unroll
@@ -109,49 +119,91 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     }
   }
   __syncthreads();
-
-  if (active) {
-    for (int fp = t; fp < NFP; fp += NP) {
-      const int face = fp / N, k = fp % N;
-      double qo[4], qn[4], fc[4];
-      long long nbr;
-      if (face == 0) nbr = (long long)((ix + a.nx - 1) % a.nx) + (long long)a.nx * iy;
-      else if (face == 1) nbr = (long long)((ix + 1) % a.nx) + (long long)a.nx * iy;
-      else if (face == 2) nbr = (long long)ix + (long long)a.nx * ((iy + a.ny - 1) % a.ny);
-      else nbr = (long long)ix + (long long)a.nx * ((iy + 1) % a.ny);
-      // own trace: faces W/E run along row k (stride 1), S/N along column k (stride N)
-      const int off_own = face < 2 ? N * k : k;
-      const int stride = face < 2 ? 1 : N;
-      const double* c_own = (face == 0 || face == 2) ? slm : slp;   // own -1 or +1 end
-      const double* c_nbr = (face == 0 || face == 2) ? slp : slm;   // neighbour's opposite end
+  // ---- 2a: own solution traces on the four faces of every tile element ----
+  for (int idx = threadIdx.x; idx < NE * 4 * N; idx += blockDim.x) {
+    const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
+    if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
+    const int off = face < 2 ? N * k : k;
+    const int stride = face < 2 ? 1 : N;
+    const double* c = (face == 0 || face == 2) ? slm : slp;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        qo[v] = trace_sum<N>(&sq[el][v][off_own], stride, c_own);
-        qn[v] = trace_global<N, PERTURB>(a.U, a.z, nbr * 4 * NP + v * NP + off_own, stride, c_nbr,
-                                          eps);
+    for (int v = 0; v < 4; ++v) str[e2][face][v][k] = trace_sum<N>(&sq[e2][v][off], stride, c);
+  }
+  __syncthreads();
+  // ---- 2b: one Rusanov flux per face point; faces on the tile boundary take
+  //      the outside neighbour's trace from global memory ----
+  for (int idx = threadIdx.x; idx < NXF + NYF; idx += blockDim.x) {
+    double qm[4], qp[4], fc[4];
+    if (idx < NXF) {
+      const int k = idx % N, rr = idx / N, xf = rr % (TX + 1), fy = rr / (TX + 1);
+      if (fy >= ay || xf > ax) continue;
+      const int gy = iy0 + fy;
+      if (xf >= 1) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qm[v] = str[xf - 1 + TX * fy][1][v][k];
+      } else {
+        const long long nb = (long long)((ix0 + a.nx - 1) % a.nx) + (long long)a.nx * gy;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          qm[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slp, eps);
       }
-      const int dir = face < 2 ? 0 : 1;
-      if (face == 0 || face == 2) rusanov(qn, qo, dir, a.gam, fc);
-      else rusanov(qo, qn, dir, a.gam, fc);
+      if (xf < ax) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sFn[el][face][v][k] = fc[v];
+        for (int v = 0; v < 4; ++v) qp[v] = str[xf + TX * fy][0][v][k];
+      } else {
+        const long long nb = (long long)((ix0 + ax) % a.nx) + (long long)a.nx * gy;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slm, eps);
+      }
+      rusanov(qm, qp, 0, a.gam, fc);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sfx[fy][xf][v][k] = fc[v];
+    } else {
+      const int i2 = idx - NXF;
+      const int k = i2 % N, rr = i2 / N, yf = rr % (TY + 1), fx = rr / (TY + 1);
+      if (fx >= ax || yf > ay) continue;
+      const int gx = ix0 + fx;
+      if (yf >= 1) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qm[v] = str[fx + TX * (yf - 1)][3][v][k];
+      } else {
+        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + a.ny - 1) % a.ny);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          qm[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slp, eps);
+      }
+      if (yf < ay) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qp[v] = str[fx + TX * yf][2][v][k];
+      } else {
+        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + ay) % a.ny);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slm, eps);
+      }
+      rusanov(qm, qp, 1, a.gam, fc);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sfy[fx][yf][v][k] = fc[v];
     }
   }
   __syncthreads();
 
+  // ---- 3: corrected divergence and the output ----
   if (!active) return;
+  const double hx = a.hx[ix0 + lx], hy = a.hy[iy0 + ly];
   const int i = t % N, j = t / N;
   // with unscaled fluxes, -(1/|J|)(dF~/dxi + dG~/deta) = -(2/hx) df~ - (2/hy) dg~
   const double sx = 2.0 / hx, sy = 2.0 / hy;
   const long long base = e * 4 * NP + t;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double dF = sdgL[i] * sFn[el][0][v][j];
-    dF = fma(sdgR[i], sFn[el][1][v][j], dF);
+    double dF = sdgL[i] * sfx[ly][lx][v][j];
+    dF = fma(sdgR[i], sfx[ly][lx + 1][v][j], dF);
 #pragma unroll
     for (int k = 0; k < N; ++k) dF = fma(sDt[i][k], sF[el][v][k + N * j], dF);
-    double dG = sdgL[j] * sFn[el][2][v][i];
-    dG = fma(sdgR[j], sFn[el][3][v][i], dG);
+    double dG = sdgL[j] * sfy[lx][ly][v][i];
+    dG = fma(sdgR[j], sfy[lx][ly + 1][v][i], dG);
 #pragma unroll
     for (int k = 0; k < N; ++k) dG = fma(sDt[j][k], sG[el][v][i + N * k], dG);
     const double R = -fma(sx, dF, sy * dG);
@@ -168,9 +220,9 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
 
 template <int P>
 int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
-  constexpr int NP = (P + 1) * (P + 1), EPB = 256 / NP;
-  const long long grid = (ctx->ne + EPB - 1) / EPB;
-  const dim3 blk(EPB * NP);
+  constexpr int NP = (P + 1) * (P + 1), TX = Tile<P>::TX, TY = Tile<P>::TY;
+  const long long grid = (long long)((ctx->nx + TX - 1) / TX) * ((ctx->ny + TY - 1) / TY);
+  const dim3 blk(TX * TY * NP);
   // algorithmic work: R reads U and writes R (16 B/DOF); A z also reads z and
   // R0 (and b) and adds the perturbation and the difference quotient.  Inside
   // a GMRES cycle the work is booked per finished iteration instead.
