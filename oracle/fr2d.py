@@ -46,7 +46,8 @@ class Mesh:
     [y_edges[iy], y_edges[iy+1]].
     """
 
-    def __init__(self, x_edges, y_edges):
+    def __init__(self, x_edges, y_edges, wall_y: bool = False):
+        self.wall_y = bool(wall_y)   # isothermal no-slip walls at the y ends (viscous residual)
         self.x_edges = np.asarray(x_edges, dtype=np.float64)
         self.y_edges = np.asarray(y_edges, dtype=np.float64)
         self.nx = len(self.x_edges) - 1

@@ -35,15 +35,17 @@ from .fr2d import Mesh, as_grid, from_grid, local_residual, neighbour_traces, re
 
 
 class Problem:
-    """A mesh, a degree and the 1D basis: what R(q) needs."""
+    """A mesh, a degree and the 1D basis: what R(q) needs.  With ``viscous``
+    (an ``ns2d.Viscous``) R is the Navier-Stokes BR2 residual."""
 
-    def __init__(self, mesh: Mesh, p: int, gamma: float = 1.4):
+    def __init__(self, mesh: Mesh, p: int, gamma: float = 1.4, viscous=None):
         self.mesh = mesh
         self.p = p
         self.np = (p + 1) ** 2
         self.nb = 4 * self.np
         self.basis = Basis(p)
         self.gamma = gamma
+        self.viscous = viscous
         self.n_residuals = 0
 
     @property
@@ -52,6 +54,9 @@ class Problem:
 
     def R(self, U):
         self.n_residuals += 1
+        if self.viscous is not None:
+            from .ns2d import ns_residual
+            return ns_residual(U, self.mesh, self.p, self.viscous, self.basis)
         return residual(U, self.mesh, self.p, self.basis, self.gamma)
 
 
@@ -118,7 +123,11 @@ def element_jacobians(prob: Problem, U, elements=None, eps_rel=1e-7):
 
 def element_blocks(prob: Problem, U, shift, elements=None, eps_rel=1e-7):
     """M_e = shift * I - J_ee for each requested element."""
-    J = element_jacobians(prob, U, elements, eps_rel)
+    if prob.viscous is not None:
+        from .ns2d import ns_element_jacobians
+        J = ns_element_jacobians(U, prob.mesh, prob.p, prob.viscous, elements, eps_rel, prob.basis)
+    else:
+        J = element_jacobians(prob, U, elements, eps_rel)
     return shift * np.eye(J.shape[1])[None] - J
 
 
