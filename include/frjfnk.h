@@ -54,6 +54,8 @@ typedef struct fr_mesh_desc {
   int nx, ny;
   const double* x_edges;
   const double* y_edges;
+  int wall_y;            /* 0: periodic in y; 1: isothermal no-slip walls at
+                            y_edges[0] and y_edges[ny] (viscous runs only) */
 } fr_mesh_desc;
 
 /* Options (fill with fr_default_opts first). */
@@ -70,6 +72,11 @@ typedef struct fr_opts {
   double reorth_eta;     /* Arnoldi: classical Gram-Schmidt, repeated once when the
                             first pass leaves ||w|| < reorth_eta ||w_in|| (1/64);
                             1 = always two passes (the paper names no variant) */
+  double mu;             /* dynamic viscosity; > 0 selects the Navier-Stokes
+                            residual with BR2 viscous fluxes (Sec. 2-3), 0 = Euler */
+  double prandtl;        /* Pr (0.72); kappa = mu Cp / Pr, gas constant R = 1 */
+  double body_force_x;   /* force per unit mass along x (drives channel flow) */
+  double wall_temperature; /* T at isothermal walls */
   int block_precision;   /* element-Jacobi blocks: 0 = FP64 (default); 1 = FP32
                             inversion and storage; 2 = FP32 inversion, BF16
                             storage.  The FD columns, the FD matvec, Arnoldi and

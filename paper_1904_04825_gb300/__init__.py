@@ -47,7 +47,8 @@ class FrError(RuntimeError):
 class fr_mesh_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x_edges", ctypes.POINTER(ctypes.c_double)),
-                ("y_edges", ctypes.POINTER(ctypes.c_double))]
+                ("y_edges", ctypes.POINTER(ctypes.c_double)),
+                ("wall_y", ctypes.c_int)]
 
 
 class fr_opts(ctypes.Structure):
@@ -56,6 +57,8 @@ class fr_opts(ctypes.Structure):
                 ("block_eps_rel", ctypes.c_double), ("precond", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("gmres_max_restarts", ctypes.c_int),
                 ("tol_lin", ctypes.c_double), ("reorth_eta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("body_force_x", ctypes.c_double), ("wall_temperature", ctypes.c_double),
                 ("block_precision", ctypes.c_int)]
 
 
@@ -153,12 +156,12 @@ def _stream(stream):
 class Context:
     """Owns an ``fr_ctx`` (mesh, degree, options, device workspace)."""
 
-    def __init__(self, x_edges, y_edges, p: int, opts: fr_opts | None = None):
+    def __init__(self, x_edges, y_edges, p: int, opts: fr_opts | None = None, wall_y: bool = False):
         xe = np.ascontiguousarray(x_edges, dtype=np.float64)
         ye = np.ascontiguousarray(y_edges, dtype=np.float64)
         desc = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
                             xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                            ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                            ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(bool(wall_y)))
         self.opts = opts if opts is not None else default_opts()
         h = ctypes.c_void_p()
         rc = lib.fr_ctx_create(ctypes.byref(desc), p, ctypes.byref(self.opts), ctypes.byref(h))
@@ -305,7 +308,7 @@ def fr_jv_noalloc(x_edges, y_edges, p: int, U, R0, z, shift, y, opts: fr_opts | 
     ye = np.ascontiguousarray(y_edges, dtype=np.float64)
     desc = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
                         xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                        ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                        ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
     rc = lib.fr_jv_noalloc(ctypes.byref(desc), int(p), ctypes.byref(opts) if opts is not None else None,
                            _ptr(U), _ptr(R0), _ptr(z), float(shift), _ptr(y), _stream(stream))
     if rc != FR_OK:

@@ -27,6 +27,9 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->hx);
   cudaFree(c->hy);
   cudaFree(c->blocks);
+  cudaFree(c->tb);
+  cudaFree(c->mst);
+  cudaFree(c->rloc);
   cudaFree(c->V);
   cudaFree(c->z);
   for (double* b : c->buf) cudaFree(b);
@@ -93,6 +96,13 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   const size_t n = (size_t)c->ndof;
   const int m = o->m_max;
   FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * c->nb * c->nb));
+  c->wall_y = mesh->wall_y ? 1 : 0;
+  c->viscous = (o->mu > 0.0 || c->wall_y) ? 1 : 0;
+  if (c->viscous) {
+    FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 4 * c->n1 * 4 * 3));
+    FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
+    FRK_TRY(dalloc(c, &c->rloc, n));
+  }
   FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
   FRK_TRY(dalloc(c, &c->z, n));
   for (double*& b : c->buf) FRK_TRY(dalloc(c, &b, n));
@@ -210,6 +220,10 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->tol_lin = 1e-8;
   o->reorth_eta = 1.0 / 64.0;
   o->block_precision = 0;
+  o->mu = 0.0;
+  o->prandtl = 0.72;
+  o->body_force_x = 0.0;
+  o->wall_temperature = 1.0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -234,7 +248,9 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
   if (opts) o = *opts;
   if (o.m_max < 1 || o.m_max > kMaxVec - 1 || o.gmres_m < 1 || o.gmres_m > o.m_max ||
       o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
-      !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2)
+      !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
+      !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
+      (mesh->wall_y && !(o.wall_temperature > 0.0)))
     return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

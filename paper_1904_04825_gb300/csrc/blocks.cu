@@ -63,6 +63,64 @@ __device__ __forceinline__ double tsum(const double* x, int stride, const double
   return s;
 }
 
+// In-place Gauss-Jordan inversion with partial (row) pivoting of the NB x NB
+// matrix M (row stride LD) in shared memory, by the whole CTA; col holds the
+// pivot column, piv the row exchanges (undone on the columns at the end).
+template <typename T, int NB, int LD>
+__device__ void gauss_jordan(T* M, T* col, int* piv) {
+  __shared__ int s_prow;
+  for (int k = 0; k < NB; ++k) {
+    if (threadIdx.x < 32) {
+      T best = (T)-1;
+      int bi = k;
+      for (int r = k + (int)threadIdx.x; r < NB; r += 32) {
+        const T val = fabs(M[r * LD + k]);
+        if (val > best) { best = val; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) { s_prow = bi; piv[k] = bi; }
+    }
+    __syncthreads();
+    const int r = s_prow;
+    if (r != k) {
+      for (int jj = threadIdx.x; jj < NB; jj += blockDim.x) {
+        const T tmp = M[k * LD + jj];
+        M[k * LD + jj] = M[r * LD + jj];
+        M[r * LD + jj] = tmp;
+      }
+    }
+    __syncthreads();
+    for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) col[ii] = M[ii * LD + k];
+    __syncthreads();
+    const T pinv = (T)1 / col[k];
+    for (int jj = threadIdx.x; jj < NB; jj += blockDim.x)
+      M[k * LD + jj] = (jj == k ? (T)1 : M[k * LD + jj]) * pinv;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int ii = idx / NB, jj = idx % NB;
+      if (ii == k) continue;
+      M[ii * LD + jj] = (jj == k ? (T)0 : M[ii * LD + jj]) - col[ii] * M[k * LD + jj];
+    }
+    __syncthreads();
+  }
+  for (int k = NB - 1; k >= 0; --k) {
+    const int r = piv[k];
+    if (r != k) {
+      for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) {
+        const T tmp = M[ii * LD + k];
+        M[ii * LD + k] = M[ii * LD + r];
+        M[ii * LD + r] = tmp;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // T: arithmetic of the Gauss-Jordan inversion (double, or float for the
 // reduced-precision preconditioner); S: storage type of the inverse blocks.
 // The finite-difference columns are always formed in FP64.
@@ -202,60 +260,33 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
   }
   __syncthreads();
 
-  // ---- in-place Gauss-Jordan inversion with partial (row) pivoting ----
-  __shared__ int s_prow;
-  for (int k = 0; k < NB; ++k) {
-    if (threadIdx.x < 32) {
-      T best = (T)-1;
-      int bi = k;
-      for (int r = k + (int)threadIdx.x; r < NB; r += 32) {
-        const T val = fabs(M[r * LD + k]);
-        if (val > best) { best = val; bi = r; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (threadIdx.x == 0) { s_prow = bi; piv[k] = bi; }
-    }
-    __syncthreads();
-    const int r = s_prow;
-    if (r != k) {
-      for (int jj = threadIdx.x; jj < NB; jj += blockDim.x) {
-        const T tmp = M[k * LD + jj];
-        M[k * LD + jj] = M[r * LD + jj];
-        M[r * LD + jj] = tmp;
-      }
-    }
-    __syncthreads();
-    for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) col[ii] = M[ii * LD + k];
-    __syncthreads();
-    const T pinv = (T)1 / col[k];
-    for (int jj = threadIdx.x; jj < NB; jj += blockDim.x)
-      M[k * LD + jj] = (jj == k ? (T)1 : M[k * LD + jj]) * pinv;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      const int ii = idx / NB, jj = idx % NB;
-      if (ii == k) continue;
-      M[ii * LD + jj] = (jj == k ? (T)0 : M[ii * LD + jj]) - col[ii] * M[k * LD + jj];
-    }
-    __syncthreads();
-  }
-  for (int k = NB - 1; k >= 0; --k) {
-    const int r = piv[k];
-    if (r != k) {
-      for (int ii = threadIdx.x; ii < NB; ii += blockDim.x) {
-        const T tmp = M[ii * LD + k];
-        M[ii * LD + k] = M[ii * LD + r];
-        M[ii * LD + r] = tmp;
-      }
-    }
-    __syncthreads();
-  }
+  gauss_jordan<T, NB, LD>(M, col, piv);
   // ---- store column-major: Minv[k*NB + i] = inverse(i, k) ----
   S* out = reinterpret_cast<S*>(a.blocks) + e * (long long)NB * NB;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int kk = idx / NB, ii = idx % NB;
+    out[idx] = StoreT<S>::to(M[ii * LD + kk]);
+  }
+}
+
+// Invert staged FP64 blocks (column-major per element: mst[e][c][row]) into
+// the preconditioner storage; one CTA per element.
+template <int NB, typename T, typename S>
+__global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long ne) {
+  constexpr int LD = NB + 1;
+  extern __shared__ double smem_inv[];
+  T* M = reinterpret_cast<T*>(smem_inv);
+  T* col = M + NB * LD;
+  int* piv = reinterpret_cast<int*>(col + NB);
+  const long long e = blockIdx.x;
+  const double* src = mst + e * (long long)NB * NB;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int c = idx / NB, r = idx % NB;
+    M[r * LD + c] = (T)src[idx];
+  }
+  __syncthreads();
+  gauss_jordan<T, NB, LD>(M, col, piv);
+  S* out = reinterpret_cast<S*>(blocks) + e * (long long)NB * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     const int kk = idx / NB, ii = idx % NB;
     out[idx] = StoreT<S>::to(M[ii * LD + kk]);
@@ -468,7 +499,37 @@ unsigned vec_grid(long long n) {
 
 }  // namespace
 
+template <int NB, typename T, typename S>
+int invert_nbts(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+  const size_t bytes = (size_t)(NB * (NB + 1) + NB) * sizeof(T) + NB * sizeof(int) + 64;
+  FRK_CUDA(ctx, cudaFuncSetAttribute(k_invert<NB, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes));
+  { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, 2.0 * NB * NB * (double)NB * (double)ctx->ne);
+    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+template <int NB>
+int invert_nb(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+  switch (ctx->opts.block_precision) {
+    case 1: return invert_nbts<NB, float, float>(ctx, mst, s);
+    case 2: return invert_nbts<NB, float, __nv_bfloat16>(ctx, mst, s);
+    default: return invert_nbts<NB, double, double>(ctx, mst, s);
+  }
+}
+
+int launch_block_invert(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+  switch (ctx->nb) {
+    case 36: return invert_nb<36>(ctx, mst, s);
+    case 64: return invert_nb<64>(ctx, mst, s);
+    case 100: return invert_nb<100>(ctx, mst, s);
+    default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
+  }
+}
+
 int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
+  if (ctx->viscous) return launch_ns_factor(ctx, U, shift, s);
   FactorArgs a;
   a.U = U; a.blocks = ctx->blocks; a.hx = ctx->hx; a.hy = ctx->hy;
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;

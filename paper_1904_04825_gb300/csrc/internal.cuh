@@ -22,6 +22,7 @@ constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
 // folds the local-flux traces F^l(+-1) into the derivative matrix, so the
 // corrected divergence is  sum_k Dt_ik F_k + g_L'_i F^num_L + g_R'_i F^num_R.
 struct Tables {
+  double D[kMaxN][kMaxN];   // D_ik = l_k'(xi_i)
   double Dt[kMaxN][kMaxN];
   double lm[kMaxN];   // l_k(-1)
   double lp[kMaxN];   // l_k(+1)
@@ -95,6 +96,11 @@ struct fr_ctx {
   frk::Tables tab{};
   double* hx = nullptr;      // [nx] element widths (device)
   double* hy = nullptr;      // [ny] element heights (device)
+  int wall_y = 0;            // isothermal no-slip walls at the y ends (viscous runs)
+  int viscous = 0;           // Navier-Stokes (BR2) residual instead of Euler
+  double* tb = nullptr;      // viscous: face traces (q, grad q) of every element
+  double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
+  double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   double* blocks = nullptr;  // [ne][nb][nb] inverse blocks, column-major per element
   int blocks_valid = 0;
   double* V = nullptr;       // (m_max+1) x ndof Krylov basis
@@ -186,5 +192,12 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
                fr_gmres_info* info, cudaStream_t s);
 // tables.cu
 void build_tables(int p, Tables* t);
+// ns.cu (viscous path): mode 0 R, 1 A z, 2 b - A z; block formation + inversion
+int launch_ns_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
+                       const double* b, double* out, double shift, const double* eps2,
+                       const int* done, cudaStream_t s);
+int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
+// blocks.cu: invert staged FP64 blocks (column-major M[c][row]) into ctx->blocks
+int launch_block_invert(fr_ctx* ctx, const double* mst, cudaStream_t s);
 
 }  // namespace frk

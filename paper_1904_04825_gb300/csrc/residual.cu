@@ -242,6 +242,7 @@ int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
 int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
                     const double* b, double* out, double shift, const double* eps2,
                     const int* done, cudaStream_t s) {
+  if (ctx->viscous) return launch_ns_residual(ctx, mode, U, z, R0, b, out, shift, eps2, done, s);
   ResArgs a;
   a.U = U; a.z = z; a.R0 = R0; a.b = b; a.out = out;
   a.hx = ctx->hx; a.hy = ctx->hy; a.eps2 = eps2; a.done = done;

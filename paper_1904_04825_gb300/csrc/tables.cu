@@ -79,8 +79,10 @@ void build_tables(int p, Tables* t) {
     t->dgR[i] = 0.5 * (dPa + dPb);
   }
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k) {
+      t->D[i][k] = D[i][k];
       t->Dt[i][k] = D[i][k] - t->dgL[i] * t->lm[k] - t->dgR[i] * t->lp[k];
+    }
 }
 
 }  // namespace frk

@@ -67,10 +67,10 @@ def test_defaults_and_argument_checks_without_gpu(libpath):
     import numpy as np
     xe = np.linspace(0, 1, 3)
     desc = fr.fr_mesh_desc(2, 2, xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                           xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                           xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
     assert fr.lib.fr_ctx_create(ctypes.byref(desc), 7, None, ctypes.byref(h)) == fr.FR_ERR_UNSUPPORTED
     desc1 = fr.fr_mesh_desc(1, 2, xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                            xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                            xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
     assert fr.lib.fr_ctx_create(ctypes.byref(desc1), 2, None, ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
     bad = fr.default_opts(m_max=64)
     assert fr.lib.fr_ctx_create(ctypes.byref(desc), 2, ctypes.byref(bad), ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
