@@ -197,19 +197,49 @@ def our_arm(args):
         if dist is not None:
             dist.barrier()
 
-    xe, ye = S.uniform_mesh(NX)
-    X, Y = S.point_coords(xe, ye, P)
-    U0 = S.Vortex().state(X, Y)
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
-    ctx = fr.Context(xe, ye, P, fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20,
-                                                block_precision=prec))
+    kind, order = args.scheme[:-1], int(args.scheme[-1])
+    if args.workload == "vortex":
+        xe, ye = S.uniform_mesh(NX)
+        X, Y = S.point_coords(xe, ye, P)
+        U0 = S.Vortex().state(X, Y)
+        p, dt, wall = P, (args.dt or DT), False
+        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec)
+        wl = f"vortex-160x160-p3-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
+    else:
+        ch = S.Channel()
+        xe = np.linspace(0.0, ch.lx, 257)
+        ye = S.channel_y_edges(128, first=1e-3, ratio=1.15)
+        X, Y = S.point_coords(xe, ye, P)
+        U0 = ch.state(X, Y, seed=0)
+        p, dt, wall = P, (args.dt or 1e-3), True
+        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
+                               mu=ch.mu, prandtl=ch.prandtl, body_force_x=ch.body_force,
+                               wall_temperature=ch.temperature)
+        wl = f"channel-256x128-p3-Re1000-M0.2-{args.scheme.upper()}-dt{dt:g}"
+    if prec:
+        wl += f"-{args.block_precision}blocks"
+    ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
     U = torch.from_numpy(U0).to(dev)
+    Uprev = torch.empty_like(U)
     stream = torch.cuda.current_stream()
+    ptc = fr.default_ptc_opts(tol_nl=1e-6, tol_lin=1e-1)
+    nstep = [0]
+
+    def one_step(Ucur):
+        if kind == "row":
+            st = fr.step_row(ctx, order, dt, Ucur)
+        elif kind == "esdirk":
+            st = fr.step_esdirk(ctx, order, dt, Ucur, ptc)
+        else:
+            st = fr.step_bdf2(ctx, dt, Ucur, Uprev, nstep[0] == 0, ptc)
+        nstep[0] += 1
+        return st
 
     # warm-up, with every kernel family timed to find the dominant one
     fr.fr_profile_begin(ctx)
     for _ in range(args.warmup):
-        fr.step_row(ctx, SCHEME, DT, U)
+        one_step(U)
     warm = fr.fr_profile_end(ctx)
     top = max(warm, key=lambda k: warm[k]["ms"])
     breakdown = {k: {"ms_per_step": v["ms"] / args.warmup, "launches_per_step": v["launches"] / args.warmup,
@@ -229,7 +259,7 @@ def our_arm(args):
     iters = 0
     e0.record(stream)
     for _ in range(args.steps):
-        st = fr.step_row(ctx, SCHEME, DT, U)
+        st = one_step(U)
         iters += st.gmres_iters
     e1.record(stream)
     torch.cuda.synchronize()
@@ -250,7 +280,7 @@ def our_arm(args):
     e2e_iters = 0
     for _ in range(args.steps):
         Ud.copy_(host_in, non_blocking=True)
-        st = fr.step_row(ctx, SCHEME, DT, Ud)
+        st = one_step(Ud)
         e2e_iters += st.gmres_iters
         host_out.copy_(Ud, non_blocking=True)
         torch.cuda.synchronize()
@@ -304,7 +334,7 @@ def our_arm(args):
             pass
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "vortex" and args.scheme == "row3":
         nd, stp = run_oracle_sample(1)
         secs = sum(t for t, _ in stp)
         it = sum(i for _, i in stp)
@@ -313,15 +343,17 @@ def our_arm(args):
                          f"CFL 13.6 and tol 1e-6, {it} GMRES iterations, {secs:.1f} s), NumPy on 1 host thread"}
 
     line = {
-        "metric": METRIC if prec == 0 else METRIC.replace("plain FP64", f"{args.block_precision} blocks"),
+        "metric": METRIC if (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt)
+        else f"DOF*GMRES-iters/s ({wl})",
         "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
-                           "block_precision": args.block_precision,
-                           "workload": WORKLOAD if prec == 0 else WORKLOAD + f"-{args.block_precision}blocks",
-                           "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / DT)}),
+                           "block_precision": args.block_precision, "workload": wl,
+                           "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
+                           "mesh": f"{ctx.nx}x{ctx.ny}",
+                           "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / dt) if args.workload == "vortex" else None}),
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roofline,
@@ -389,6 +421,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
+    ap.add_argument("--workload", choices=["vortex", "channel"], default="vortex")
+    ap.add_argument("--scheme", default="row3",
+                    choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2"])
+    ap.add_argument("--dt", type=float, default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -203,3 +203,54 @@ def stretched_mesh(nx: int, ny: int, seed: int = 0, amp: float = 0.3,
         e[1:-1] += rng.uniform(-amp, amp, n - 1) * h
         return e
     return jitter(nx, box[0], box[1]), jitter(ny, box[2], box[3])
+
+
+@dataclass(frozen=True)
+class Channel:
+    """Plane channel between walls y = 0 and y = 1, periodic in x over
+    [0, lx]: laminar Poiseuille profile u = 4 uc y (1 - y), uniform density
+    and temperature (Mach ``mach`` on uc, gas constant 1), plus a seeded
+    divergence-free perturbation from a stream function
+    psi = y^2 (1-y)^2 sum_m a_m sin(kx_m x + phi_m) cos(ky_m y + theta_m)
+    (u' = dpsi/dy, v' = -dpsi/dx vanish at the walls), scaled so that
+    max |u'| = amp * uc over the sample points."""
+    lx: float = 2.0
+    uc: float = 1.0
+    mach: float = 0.2
+    reynolds: float = 1000.0     # rho uc lx / mu
+    prandtl: float = 0.72
+    gamma: float = GAMMA
+
+    @property
+    def temperature(self) -> float:
+        return (self.uc / self.mach) ** 2 / self.gamma
+
+    @property
+    def mu(self) -> float:
+        return self.uc * self.lx / self.reynolds
+
+    @property
+    def body_force(self) -> float:
+        """Force per unit mass that balances the Poiseuille wall shear."""
+        return 8.0 * self.mu * self.uc
+
+    def state(self, X, Y, seed: int, amp: float = 1e-2, modes: int = 4) -> np.ndarray:
+        rng = np.random.default_rng(seed)
+        w = Y * Y * (1 - Y) ** 2
+        dw = 2 * Y * (1 - Y) * (1 - 2 * Y)
+        up = np.zeros_like(X)
+        vp = np.zeros_like(X)
+        for _ in range(modes):
+            kx = 2 * math.pi * rng.integers(1, 4) / self.lx
+            ky = math.pi * rng.integers(0, 3)
+            a = rng.uniform(-1, 1)
+            ph, th = rng.uniform(0, 2 * math.pi, 2)
+            sx, cx = np.sin(kx * X + ph), np.cos(kx * X + ph)
+            cy, sy = np.cos(ky * Y + th), np.sin(ky * Y + th)
+            up += a * sx * (dw * cy - w * ky * sy)
+            vp += -a * w * kx * cx * cy
+        scale = amp * self.uc / max(np.max(np.abs(up)), 1e-300)
+        u = 4 * self.uc * Y * (1 - Y) + scale * up
+        v = scale * vp
+        T = self.temperature
+        return conserved(np.ones_like(X), u, v, T * np.ones_like(X), self.gamma)
