@@ -82,6 +82,11 @@ typedef struct fr_opts {
                             storage.  The FD columns, the FD matvec, Arnoldi and
                             all updates stay FP64 (reduced precision changes
                             only the preconditioner, not the converged answer) */
+  int precond_refresh;   /* pseudo-transient continuation (ESDIRK, BDF2): 0 = form
+                            J_ee once per stage at its first pseudo iterate and
+                            re-invert shift*I - J_ee when dtau changes (default);
+                            1 = form the blocks again at every pseudo iterate.
+                            The paper does not say; ROW forms them once per step */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with

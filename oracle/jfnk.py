@@ -121,13 +121,17 @@ def element_jacobians(prob: Problem, U, elements=None, eps_rel=1e-7):
     return J
 
 
-def element_blocks(prob: Problem, U, shift, elements=None, eps_rel=1e-7):
-    """M_e = shift * I - J_ee for each requested element."""
+def diagonal_blocks(prob: Problem, U, elements=None, eps_rel=1e-7):
+    """J_ee for the Euler or the Navier-Stokes residual of ``prob``."""
     if prob.viscous is not None:
         from .ns2d import ns_element_jacobians
-        J = ns_element_jacobians(U, prob.mesh, prob.p, prob.viscous, elements, eps_rel, prob.basis)
-    else:
-        J = element_jacobians(prob, U, elements, eps_rel)
+        return ns_element_jacobians(U, prob.mesh, prob.p, prob.viscous, elements, eps_rel, prob.basis)
+    return element_jacobians(prob, U, elements, eps_rel)
+
+
+def element_blocks(prob: Problem, U, shift, elements=None, eps_rel=1e-7):
+    """M_e = shift * I - J_ee for each requested element."""
+    J = diagonal_blocks(prob, U, elements, eps_rel)
     return shift * np.eye(J.shape[1])[None] - J
 
 

@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .jfnk import ElementJacobi, Problem, element_blocks, fd_jv, gmres
+from .jfnk import ElementJacobi, Problem, diagonal_blocks, element_blocks, fd_jv, gmres
 from .tableaus import BDF2_A, BDF2_OMEGA, EsdirkTableau, RowTableau
 
 
@@ -54,6 +54,7 @@ class PtcOpts:
     max_iters: int = 200
     max_rejections: int = 30
     reject_above: float = 0.1        # GMRES relres above this -> reject
+    refresh: str = "stage"           # "stage" or "iterate" (element-Jacobi J_ee)
 
 
 @dataclass
@@ -116,12 +117,19 @@ def ptc_solve(prob: Problem, rhs_const, omega_dt, q0, dt, popts: PtcOpts, sopts:
     dtau_max = popts.dtau_max
     k = 0
     rejections = 0
+    J = None
+    J_k = -1
     while F0 > 0.0 and Fn / F0 >= popts.tol_nl:
         if k >= popts.max_iters:
             stats.converged = False
             break
         shift = 1.0 / dtau + 1.0 / omega_dt
-        blocks = element_blocks(prob, q, shift, eps_rel=sopts.eps_rel) if sopts.precond else None
+        blocks = None
+        if sopts.precond:
+            if J is None or (popts.refresh == "iterate" and J_k != k):
+                J = diagonal_blocks(prob, q, eps_rel=sopts.eps_rel)
+                J_k = k
+            blocks = shift * np.eye(J.shape[1])[None] - J
         dq, info = _linear_solve(prob, q, Rq, shift, -F, sopts, popts.tol_lin, stats, blocks)
         if info.relres > popts.reject_above:
             rejections += 1

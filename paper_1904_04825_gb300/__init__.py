@@ -59,7 +59,7 @@ class fr_opts(ctypes.Structure):
                 ("tol_lin", ctypes.c_double), ("reorth_eta", ctypes.c_double),
                 ("mu", ctypes.c_double), ("prandtl", ctypes.c_double),
                 ("body_force_x", ctypes.c_double), ("wall_temperature", ctypes.c_double),
-                ("block_precision", ctypes.c_int)]
+                ("block_precision", ctypes.c_int), ("precond_refresh", ctypes.c_int)]
 
 
 class fr_ptc_opts(ctypes.Structure):

@@ -100,9 +100,9 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   c->viscous = (o->mu > 0.0 || c->wall_y) ? 1 : 0;
   if (c->viscous) {
     FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 4 * c->n1 * 4 * 3));
-    FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
     FRK_TRY(dalloc(c, &c->rloc, n));
   }
+  FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
   FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
   FRK_TRY(dalloc(c, &c->z, n));
   for (double*& b : c->buf) FRK_TRY(dalloc(c, &b, n));
@@ -224,6 +224,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->prandtl = 0.72;
   o->body_force_x = 0.0;
   o->wall_temperature = 1.0;
+  o->precond_refresh = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -250,7 +251,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
       !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
-      (mesh->wall_y && !(o.wall_temperature > 0.0)))
+      (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1)
     return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

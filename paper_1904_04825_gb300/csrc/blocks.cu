@@ -19,6 +19,7 @@ namespace {
 struct FactorArgs {
   const double* U;
   void* blocks;      // [ne][nb][nb] of S, column-major inverse per element: Minv[k*nb + i]
+  double* mst;       // staged M = shift I - J_ee before inversion, [ne][c][row] (FP64)
   const double* hx;
   const double* hy;
   long long ne;
@@ -260,6 +261,15 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
   }
   __syncthreads();
 
+  // stage M (column-major) so a later shift change only re-inverts
+  {
+    double* st = a.mst + e * (long long)NB * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int c = idx / NB, r = idx % NB;
+      st[idx] = (double)M[r * LD + c];
+    }
+  }
+  __syncthreads();
   gauss_jordan<T, NB, LD>(M, col, piv);
   // ---- store column-major: Minv[k*NB + i] = inverse(i, k) ----
   S* out = reinterpret_cast<S*>(a.blocks) + e * (long long)NB * NB;
@@ -272,7 +282,8 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
 // Invert staged FP64 blocks (column-major per element: mst[e][c][row]) into
 // the preconditioner storage; one CTA per element.
 template <int NB, typename T, typename S>
-__global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long ne) {
+__global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long ne,
+                                                double dshift) {
   constexpr int LD = NB + 1;
   extern __shared__ double smem_inv[];
   T* M = reinterpret_cast<T*>(smem_inv);
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, 
   const double* src = mst + e * (long long)NB * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     const int c = idx / NB, r = idx % NB;
-    M[r * LD + c] = (T)src[idx];
+    M[r * LD + c] = (T)(r == c ? src[idx] + dshift : src[idx]);
   }
   __syncthreads();
   gauss_jordan<T, NB, LD>(M, col, piv);
@@ -500,38 +511,45 @@ unsigned vec_grid(long long n) {
 }  // namespace
 
 template <int NB, typename T, typename S>
-int invert_nbts(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+int invert_nbts(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
   const size_t bytes = (size_t)(NB * (NB + 1) + NB) * sizeof(T) + NB * sizeof(int) + 64;
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_invert<NB, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)bytes));
   { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, 2.0 * NB * NB * (double)NB * (double)ctx->ne);
-    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne); }
+    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne, dshift); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 template <int NB>
-int invert_nb(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+int invert_nb(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
   switch (ctx->opts.block_precision) {
-    case 1: return invert_nbts<NB, float, float>(ctx, mst, s);
-    case 2: return invert_nbts<NB, float, __nv_bfloat16>(ctx, mst, s);
-    default: return invert_nbts<NB, double, double>(ctx, mst, s);
+    case 1: return invert_nbts<NB, float, float>(ctx, mst, dshift, s);
+    case 2: return invert_nbts<NB, float, __nv_bfloat16>(ctx, mst, dshift, s);
+    default: return invert_nbts<NB, double, double>(ctx, mst, dshift, s);
   }
 }
 
-int launch_block_invert(fr_ctx* ctx, const double* mst, cudaStream_t s) {
+int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
   switch (ctx->nb) {
-    case 36: return invert_nb<36>(ctx, mst, s);
-    case 64: return invert_nb<64>(ctx, mst, s);
-    case 100: return invert_nb<100>(ctx, mst, s);
+    case 36: return invert_nb<36>(ctx, mst, dshift, s);
+    case 64: return invert_nb<64>(ctx, mst, dshift, s);
+    case 100: return invert_nb<100>(ctx, mst, dshift, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }
 
+int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s) {
+  FRK_TRY(launch_block_invert(ctx, ctx->mst, shift - ctx->staged_shift, s));
+  ctx->blocks_valid = 1;
+  return FR_OK;
+}
+
 int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
+  ctx->staged_shift = shift;
   if (ctx->viscous) return launch_ns_factor(ctx, U, shift, s);
   FactorArgs a;
-  a.U = U; a.blocks = ctx->blocks; a.hx = ctx->hx; a.hy = ctx->hy;
+  a.U = U; a.blocks = ctx->blocks; a.mst = ctx->mst; a.hx = ctx->hx; a.hy = ctx->hy;
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
   a.gam = ctx->opts.gamma; a.shift = shift; a.beps = ctx->opts.block_eps_rel;
   a.tab = ctx->tab;

@@ -101,6 +101,7 @@ struct fr_ctx {
   double* tb = nullptr;      // viscous: face traces (q, grad q) of every element
   double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
+  double staged_shift = 0.0; // shift the staged blocks in mst were formed with
   double* blocks = nullptr;  // [ne][nb][nb] inverse blocks, column-major per element
   int blocks_valid = 0;
   double* V = nullptr;       // (m_max+1) x ndof Krylov basis
@@ -197,7 +198,9 @@ int launch_ns_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
                        const double* b, double* out, double shift, const double* eps2,
                        const int* done, cudaStream_t s);
 int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
-// blocks.cu: invert staged FP64 blocks (column-major M[c][row]) into ctx->blocks
-int launch_block_invert(fr_ctx* ctx, const double* mst, cudaStream_t s);
+// blocks.cu: invert staged FP64 blocks (column-major M[c][row], dshift added to
+// the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
+int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
+int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s);
 
 }  // namespace frk

@@ -454,7 +454,7 @@ int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
   a.out = ctx->mst;
   a.shift = shift;
   FRK_TRY(dispatch(ctx, 3, a, false, s, 0.0, 0.0));
-  return launch_block_invert(ctx, ctx->mst, s);
+  return launch_block_invert(ctx, ctx->mst, 0.0, s);
 }
 
 }  // namespace frk

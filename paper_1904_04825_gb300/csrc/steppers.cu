@@ -189,6 +189,8 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
   double dtau = po.dtau_init > 0.0 ? po.dtau_init : dt;
   double dtau_max = po.dtau_max;
   int k = 0, rejections = 0;
+  int formed_k = -1;          // pseudo iterate the staged blocks were formed at
+  double blocks_shift = 0.0;  // shift of the current inverse blocks
   while (F0 > 0.0 && Fn / F0 >= po.tol_nl) {
     if (k >= po.max_iters) {
       st->converged = 0;
@@ -196,7 +198,20 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
                        k, Fn / F0);
     }
     const double shift = 1.0 / dtau + 1.0 / omega_dt;
-    if (ctx->opts.precond) FRK_TRY(launch_block_factor(ctx, q, shift, s));
+    if (ctx->opts.precond) {
+      // blocks formed at the stage's first iterate (or every iterate with
+      // precond_refresh = 1); a new shift only re-inverts the staged blocks
+      if (k == 0 && rejections == 0 && formed_k < 0) {
+        FRK_TRY(launch_block_factor(ctx, q, shift, s));
+        formed_k = 0;
+      } else if (ctx->opts.precond_refresh == 1 && formed_k != k) {
+        FRK_TRY(launch_block_factor(ctx, q, shift, s));
+        formed_k = k;
+      } else if (blocks_shift != shift) {
+        FRK_TRY(launch_block_reshift(ctx, shift, s));
+      }
+      blocks_shift = shift;
+    }
     ctx->blocks_valid = ctx->opts.precond;
     // b = -F into B_RHS
     const double* xs[1] = {F};

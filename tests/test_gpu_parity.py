@@ -405,3 +405,20 @@ def test_nonfinite_input_reported(fr):
     with pytest.raises(fr.FrError) as ei:
         fr.step_row(ctx, 2, 0.05, U)
     assert ei.value.code == fr.FR_ERR_NONFINITE
+
+
+def test_step_esdirk_refresh_every_iterate_matches_oracle(fr):
+    """precond_refresh = 1 (blocks formed again at every pseudo iterate)
+    against the oracle's refresh = "iterate"."""
+    p = 2
+    xe, ye, X, Y = _case("uniform", 5, 5, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(gmres_max_restarts=40, precond_refresh=1))
+    po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
+    U = _t(U0)
+    st = fr.step_esdirk(ctx, 3, 0.1, U, po)
+    Uo, so = o_esdirk(prob, ESDIRK[3](), 0.1, U0,
+                      PtcOpts(tol_nl=1e-12, tol_lin=1e-3, refresh="iterate"), TIGHT)
+    assert st.converged and so.converged
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
