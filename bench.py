@@ -368,6 +368,62 @@ def our_arm(args):
     return 0
 
 
+def t_end_arm(args):
+    """Run the vortex workload to t_end; report wall time and E(rho), the L2
+    density error against the advected exact vortex (Sec. 5.1 error norm,
+    Gauss-Legendre quadrature at the solution points)."""
+    import numpy as np
+    import torch
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    torch.cuda.set_device(0)
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
+    kind, order = args.scheme[:-1], int(args.scheme[-1])
+    nx = args.nx or NX
+    p = args.p or P
+    xe, ye = S.uniform_mesh(nx)
+    X, Y = S.point_coords(xe, ye, p)
+    vort = S.Vortex()
+    U = torch.from_numpy(vort.state(X, Y)).cuda()
+    Uprev = torch.empty_like(U)
+    h = 10.0 / nx
+    dt = args.dt if args.dt else args.cfl * h / (3 * math.sqrt(2) * (p + 1))
+    nsteps = int(round(args.t_end / dt))
+    dt = args.t_end / nsteps
+    tol = args.tol
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else 1e-1, gmres_m=30,
+                                                gmres_max_restarts=20, block_precision=prec))
+    ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=args.tol_lin)
+    iters = 0
+    bad = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(nsteps):
+        if kind == "row":
+            st = fr.step_row(ctx, order, dt, U)
+        elif kind == "esdirk":
+            st = fr.step_esdirk(ctx, order, dt, U, ptc)
+        else:
+            st = fr.step_bdf2(ctx, dt, U, Uprev, k == 0, ptc)
+        iters += st.gmres_iters
+        bad += 0 if st.converged else 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    x, w = np.polynomial.legendre.leggauss(p + 1)
+    w2 = np.outer(w, w).reshape(-1)
+    exact = vort.state(X, Y, t=args.t_end)
+    rho = U[:, 0].cpu().numpy()
+    err = math.sqrt(np.sum((exact[:, 0] - rho) ** 2 * w2[None, :]) * (h * h / 4) / 100.0)
+    print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
+                      "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
+                      "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
+                      "block_precision": args.block_precision, "t_end": args.t_end,
+                      "time_to_t_end_s": wall, "E_rho": err, "gmres_iters": iters,
+                      "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
+    return 0
+
+
 def kernel_arm(args):
     """Time one kernel family alone on the full-size inputs (for per-kernel
     numbers and as a short, clean target for ncu captures)."""
@@ -425,6 +481,14 @@ def main():
     ap.add_argument("--scheme", default="row3",
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2"])
     ap.add_argument("--dt", type=float, default=None)
+    ap.add_argument("--t-end", type=float, default=None,
+                    help="vortex only: run to t_end, report time-to-t_end and E(rho)")
+    ap.add_argument("--cfl", type=float, default=13.6)
+    ap.add_argument("--tol", type=float, default=1e-6,
+                    help="--t-end: tol_rel,linear for ROW, tol_rel,nonlinear for ESDIRK/BDF2")
+    ap.add_argument("--tol-lin", type=float, default=1e-1, help="--t-end: ESDIRK/BDF2 GMRES tolerance")
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--p", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -432,6 +496,8 @@ def main():
         return reference_arm(args)
     if args.kernel:
         return kernel_arm(args)
+    if args.t_end:
+        return t_end_arm(args)
     return our_arm(args)
 
 
