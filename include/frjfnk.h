@@ -196,6 +196,46 @@ int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts
 int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
               const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
 
+/* ---- learned initial guess (no counterpart in the paper) ---------------
+ * A per-element MLP, features [b_e/s, Y_prev,e/s, U_e/rms(U)] -> Y_e/s with
+ * s = ||b||_2/sqrt(ndof), network 3nb -> hidden -> hidden -> nb with ReLU,
+ * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
+ * (gradients checkable against an FP64 reference); inference runs BF16
+ * operands on the tensor cores with FP32 accumulation.  GMRES judges the
+ * guess: a stage solved from it still stops at tol_lin * ||b||. */
+typedef struct fr_mlp fr_mlp;
+/* Create a model (device memory for up to max_batch samples). */
+int fr_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, fr_mlp** out);
+int fr_mlp_destroy(fr_mlp* m);
+const char* fr_mlp_last_error(const fr_mlp* m);
+/* Parameter count and the flat FP32 layout [W1 b1 W2 b2 W3 b3], W row-major (out x in). */
+long long fr_mlp_num_params(const fr_mlp* m);
+/* HOST parameter arrays of fr_mlp_num_params floats; set also resets Adam. */
+int fr_mlp_set_params(fr_mlp* m, const float* host, void* stream);
+int fr_mlp_get_params(fr_mlp* m, float* host, void* stream);
+int fr_mlp_get_grads(fr_mlp* m, float* host, void* stream);
+/* Y[M][n_out] = MLP(X[M][n_in]) (device FP32 arrays, M <= max_batch);
+ * bf16 = 0: FP32 training path (keeps the activations for fr_mlp_backward);
+ * bf16 = 1: BF16 tensor-core inference. */
+int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf16, void* stream);
+/* Gradients of mean((Y - T)^2)/2 after an FP32 forward on the same X;
+ * loss_host (may be NULL) receives the loss (synchronises). */
+int fr_mlp_backward(fr_mlp* m, const float* X, const float* T, int M, double* loss_host, void* stream);
+/* One Adam step (with bias correction) on the FP32 weights; refreshes the BF16 copy. */
+int fr_mlp_adam(fr_mlp* m, float lr, float beta1, float beta2, float eps, void* stream);
+/* Use the model for the initial guess of every ROW stage solve of ctx
+ * (NULL detaches; x0 = 0 then).  Allocates the feature buffers once. */
+int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model);
+/* Record training pairs from step_row: after each stage solve, features and
+ * targets Y_e/s of every elem_stride-th element (offset rotating per stage)
+ * into the device arrays X [max][3nb] and T [max][nb] until max samples.
+ * X = T = NULL stops.  fr_stage_capture_count gives the samples recorded. */
+int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long max_samples, int elem_stride);
+long long fr_stage_capture_count(const fr_ctx* ctx);
+/* Features of every element for (b, Y_prev (may be NULL), U) into X [ne][3nb]. */
+int fr_stage_features(fr_ctx* ctx, const double* b, const double* yprev, const double* U, float* X,
+                      void* stream);
+
 /* ---- allocation-free variant (no counterpart in the paper) -------------
  * y = shift*z - (R(U + eps z) - R0)/eps exactly as fr_jv computes it, but
  * without a context and without allocating device memory.  It is for

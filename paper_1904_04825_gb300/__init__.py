@@ -107,6 +107,20 @@ def _load():
                           ctypes.POINTER(fr_step_stats), V]),
         "fr_kernel_launches": (ctypes.c_longlong, []),
         "fr_jv_noalloc": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts), P, P, P, D, P, V]),
+        "fr_mlp_create": (I, [I, I, I, I, ctypes.POINTER(ctypes.c_void_p)]),
+        "fr_mlp_destroy": (I, [P]),
+        "fr_mlp_last_error": (ctypes.c_char_p, [P]),
+        "fr_mlp_num_params": (ctypes.c_longlong, [P]),
+        "fr_mlp_set_params": (I, [P, P, V]),
+        "fr_mlp_get_params": (I, [P, P, V]),
+        "fr_mlp_get_grads": (I, [P, P, V]),
+        "fr_mlp_forward": (I, [P, P, I, P, I, V]),
+        "fr_mlp_backward": (I, [P, P, P, I, ctypes.POINTER(ctypes.c_double), V]),
+        "fr_mlp_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, V]),
+        "fr_attach_guess_model": (I, [P, P]),
+        "fr_set_stage_capture": (I, [P, P, P, ctypes.c_longlong, I]),
+        "fr_stage_capture_count": (ctypes.c_longlong, [P]),
+        "fr_stage_features": (I, [P, P, P, P, P, V]),
         "fr_profile_begin": (I, [P, ctypes.c_uint]),
         "fr_profile_end": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -314,3 +328,101 @@ def fr_jv_noalloc(x_edges, y_edges, p: int, U, R0, z, shift, y, opts: fr_opts | 
     if rc != FR_OK:
         raise FrError(rc, lib.fr_last_error(None).decode())
     return rc
+
+
+def _fptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class MLP:
+    """Per-element MLP of the learned initial guess (see the C header)."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int, max_batch: int):
+        h = ctypes.c_void_p()
+        rc = lib.fr_mlp_create(n_in, n_hidden, n_out, max_batch, ctypes.byref(h))
+        if rc != FR_OK:
+            raise FrError(rc, "fr_mlp_create failed")
+        self.handle = h
+        self.sizes = (n_in, n_hidden, n_hidden, n_out)
+        self.nparam = int(lib.fr_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.fr_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != FR_OK:
+            raise FrError(rc, lib.fr_mlp_last_error(self.handle).decode())
+        return rc
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparam
+        return self.check(lib.fr_mlp_set_params(self.handle, a.ctypes.data_as(ctypes.c_void_p), _stream(None)))
+
+    def get_params(self):
+        a = np.empty(self.nparam, dtype=np.float32)
+        self.check(lib.fr_mlp_get_params(self.handle, a.ctypes.data_as(ctypes.c_void_p), _stream(None)))
+        return a
+
+    def get_grads(self):
+        a = np.empty(self.nparam, dtype=np.float32)
+        self.check(lib.fr_mlp_get_grads(self.handle, a.ctypes.data_as(ctypes.c_void_p), _stream(None)))
+        return a
+
+    def forward(self, X, Y, bf16=False):
+        return self.check(lib.fr_mlp_forward(self.handle, _fptr(X), int(X.shape[0]), _fptr(Y), int(bool(bf16)),
+                                             _stream(None)))
+
+    def backward(self, X, T):
+        loss = ctypes.c_double()
+        self.check(lib.fr_mlp_backward(self.handle, _fptr(X), _fptr(T), int(X.shape[0]), ctypes.byref(loss),
+                                       _stream(None)))
+        return loss.value
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        return self.check(lib.fr_mlp_adam(self.handle, lr, beta1, beta2, eps, _stream(None)))
+
+
+def flat_params(params):
+    """Oracle (W, b) list -> the flat [W1 b1 W2 b2 W3 b3] layout."""
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in params])
+
+
+def unflat_params(flat, sizes):
+    out, o = [], 0
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        W = flat[o:o + fo * fi].reshape(fo, fi)
+        o += fo * fi
+        b = flat[o:o + fo]
+        o += fo
+        out.append((W, b))
+    return out
+
+
+def fr_attach_guess_model(ctx: Context, model):
+    return ctx.check(lib.fr_attach_guess_model(ctx.handle, model.handle if model is not None else None))
+
+
+def fr_set_stage_capture(ctx: Context, X, T, max_samples, elem_stride):
+    return ctx.check(lib.fr_set_stage_capture(ctx.handle, _fptr(X) if X is not None else None,
+                                              _fptr(T) if T is not None else None, int(max_samples),
+                                              int(elem_stride)))
+
+
+def fr_stage_capture_count(ctx: Context) -> int:
+    return int(lib.fr_stage_capture_count(ctx.handle))
+
+
+def fr_stage_features(ctx: Context, b, yprev, U, X, stream=None):
+    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(yprev), _ptr(U), _fptr(X), _stream(stream)))

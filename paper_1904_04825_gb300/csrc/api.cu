@@ -30,6 +30,8 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->tb);
   cudaFree(c->mst);
   cudaFree(c->rloc);
+  cudaFree(c->gfeat);
+  cudaFree(c->gout);
   cudaFree(c->V);
   cudaFree(c->z);
   for (double* b : c->buf) cudaFree(b);

@@ -60,7 +60,7 @@ struct GmresDev {
 };
 
 // Device scalars (sums of squares) used by the FD step and GMRES.
-enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_COUNT };
+enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_COUNT };
 
 // FD step eps = eps_rel (1 + ||U||) / ||z|| (or eps_fixed), written once per
 // product as (eps, 1/eps) by the kernel that finishes ||z||^2.
@@ -88,6 +88,18 @@ struct Prof {
 };
 }  // namespace frk
 
+struct fr_mlp;
+
+namespace frk {
+// Training-pair capture of ROW stage solves (features and scaled targets).
+struct StageCapture {
+  float* X = nullptr;       // [max][3 nb]
+  float* T = nullptr;       // [max][nb]
+  long long max = 0, count = 0, offset = 0;
+  int stride = 1;           // sample every stride-th element, rotating the offset per stage
+};
+}  // namespace frk
+
 struct fr_ctx {
   int device = 0;
   int nx = 0, ny = 0, p = 0, n1 = 0, np = 0, nb = 0;
@@ -102,6 +114,10 @@ struct fr_ctx {
   double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
+  fr_mlp* guess = nullptr;   // learned initial-guess model (ROW stages), or null
+  float* gfeat = nullptr;    // [ne][3 nb] features for the guess
+  float* gout = nullptr;     // [ne][nb] model output
+  frk::StageCapture cap;
   double* blocks = nullptr;  // [ne][nb][nb] inverse blocks, column-major per element
   int blocks_valid = 0;
   double* V = nullptr;       // (m_max+1) x ndof Krylov basis
@@ -202,5 +218,10 @@ int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
 int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s);
+// guess.cu
+int stage_guess(fr_ctx* ctx, const double* b, const double* yprev, const double* U, double* x0,
+                cudaStream_t s);
+int stage_capture(fr_ctx* ctx, const double* b, const double* yprev, const double* U, const double* y,
+                  cudaStream_t s);
 
 }  // namespace frk

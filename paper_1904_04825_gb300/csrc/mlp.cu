@@ -1,0 +1,457 @@
+// Per-element MLP that predicts a stage solve's initial Krylov guess (not in
+// the paper; the GMRES solve still judges the guess and converges to the
+// same tolerance).
+//
+// Network 3nb -> 256 -> 256 -> nb, ReLU, FP32 master weights.
+//  * training path (forward with stored activations, backward, Adam): FP32
+//    tiled GEMMs on the CUDA cores, so the gradients can be checked against
+//    the FP64 oracle;
+//  * inference path: BF16 operands on the tensor cores (mma.sync m16n8k16,
+//    FP32 accumulation) with bias + ReLU fused into the epilogue.
+// Loss: mean of (y - t)^2 / 2 over all outputs; Adam with bias correction.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "device.cuh"
+
+struct fr_mlp {
+  int n[4] = {0, 0, 0, 0};  // layer widths: in, hidden, hidden, out
+  int max_batch = 0;
+  long long nparam = 0;
+  float* P = nullptr;       // FP32 master parameters [W1 b1 W2 b2 W3 b3]
+  float* G = nullptr;       // gradients (same layout)
+  float* Mo = nullptr;      // Adam first moments
+  float* Vo = nullptr;      // Adam second moments
+  __nv_bfloat16* P16 = nullptr;  // BF16 copy of the weights (biases stay FP32 in P)
+  float* Z[3] = {};         // pre-activations [M x n[l+1]]
+  float* A[2] = {};         // hidden activations [M x n[l+1]]
+  float* D[3] = {};         // loss gradients w.r.t. Z
+  float* part = nullptr;    // split-M partial weight gradients
+  __nv_bfloat16* X16 = nullptr;   // BF16 input / hidden activations for inference
+  __nv_bfloat16* H16[2] = {};
+  double* loss = nullptr;   // device scalar
+  int step = 0;
+  char err[256] = {0};
+};
+
+namespace frk {
+namespace {
+
+constexpr int kSplitRows = 4096;  // rows per partial in the weight-gradient reduction
+
+long long off_W(const fr_mlp* m, int l) {
+  long long o = 0;
+  for (int i = 0; i < l; ++i) o += (long long)m->n[i + 1] * m->n[i] + m->n[i + 1];
+  return o;
+}
+long long off_b(const fr_mlp* m, int l) { return off_W(m, l) + (long long)m->n[l + 1] * m->n[l]; }
+
+// ---- FP32 tiled GEMM: C[i][j] = sum_k A(i,k) B(k,j) (+ bias[j]) (ReLU) ----
+// A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj], C row-major ldc.
+// 64x64 tile, 16-deep k slices, 256 threads x (4x4) outputs.
+template <bool RELU>
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A,
+                                               long long sai, long long sak, const float* __restrict__ B,
+                                               long long sbk, long long sbj, float* __restrict__ C, int ldc,
+                                               const float* __restrict__ bias, float* __restrict__ Zout,
+                                               int kbeg, int kend) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  if (kend < 0) kend = K;
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+      const int kk = t / 64, r = t % 64;
+      const int i = i0 + r, k = k0 + kk, j = j0 + r;
+      As[kk][r] = (i < M && k < kend) ? A[i * sai + k * sak] : 0.f;
+      Bs[kk][r] = (j < N && k < kend) ? B[k * sbk + j * sbj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < M && j < N) {
+        float c = acc[u][v] + (bias ? bias[j] : 0.f);
+        if (Zout) Zout[(long long)i * ldc + j] = c;
+        if (RELU) c = fmaxf(c, 0.f);
+        C[(long long)i * ldc + j] = c;
+      }
+    }
+}
+
+// ---- BF16 tensor-core GEMM for inference: Y = act(X W^T + b) ----
+// X [M x K] row-major BF16, W [N x K] row-major BF16, K % 16 == 0 handled by
+// zero padding in shared memory.  CTA 128 threads = 4 warps, tile 64 (rows) x
+// 64 (cols); each warp owns 16 rows x 64 cols = 8 m16n8k16 tiles.
+template <bool RELU, bool OUT_BF16>
+__global__ void __launch_bounds__(128) k_hgemm(int M, int N, int K, const __nv_bfloat16* __restrict__ X,
+                                               const __nv_bfloat16* __restrict__ W,
+                                               const float* __restrict__ bias, void* out) {
+  __shared__ __align__(16) __nv_bfloat16 Xs[64][16 + 8];
+  __shared__ __align__(16) __nv_bfloat16 Ws[64][16 + 8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int g = lane / 4, tq = lane % 4;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int t = threadIdx.x; t < 64 * 16; t += 128) {
+      const int r = t / 16, kk = t % 16;
+      const int i = i0 + r, j = j0 + r, k = k0 + kk;
+      Xs[r][kk] = (i < M && k < K) ? X[(long long)i * K + k] : zero;
+      Ws[r][kk] = (j < N && k < K) ? W[(long long)j * K + k] : zero;
+    }
+    __syncthreads();
+    const int r = warp * 16;
+    unsigned a[4];
+    a[0] = *reinterpret_cast<const unsigned*>(&Xs[r + g][2 * tq]);
+    a[1] = *reinterpret_cast<const unsigned*>(&Xs[r + g + 8][2 * tq]);
+    a[2] = *reinterpret_cast<const unsigned*>(&Xs[r + g][2 * tq + 8]);
+    a[3] = *reinterpret_cast<const unsigned*>(&Xs[r + g + 8][2 * tq + 8]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      unsigned b[2];
+      b[0] = *reinterpret_cast<const unsigned*>(&Ws[nt * 8 + g][2 * tq]);
+      b[1] = *reinterpret_cast<const unsigned*>(&Ws[nt * 8 + g][2 * tq + 8]);
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+          "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+          : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + warp * 16 + g + (c >= 2 ? 8 : 0);
+      const int j = j0 + nt * 8 + 2 * tq + (c & 1);
+      if (i < M && j < N) {
+        float v = acc[nt][c] + bias[j];
+        if (RELU) v = fmaxf(v, 0.f);
+        if (OUT_BF16) reinterpret_cast<__nv_bfloat16*>(out)[(long long)i * N + j] = __float2bfloat16_rn(v);
+        else reinterpret_cast<float*>(out)[(long long)i * N + j] = v;
+      }
+    }
+}
+
+__global__ void k_f2bf(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// dZ_out = (y - t) / (M * n_out), loss partial sums (FP64)
+__global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ d,
+                            long long n, double* loss, Reduce red) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  const float inv = 1.0f / (float)n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float e = y[i] - t[i];
+    d[i] = e * inv;
+    s += 0.5 * (double)e * (double)e;
+  }
+  const double bs = block_sum(s, sh);
+  if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+  if (last_block(red.counter)) {
+    finish_sums(red, 1, loss);
+    if (threadIdx.x == 0) *loss /= (double)n;
+  }
+}
+
+// d = d * (z > 0)
+__global__ void k_relu_back(float* __restrict__ d, const float* __restrict__ z, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(z[i] > 0.f)) d[i] = 0.f;
+}
+
+// sum of the split-M partials (fixed order) into the weight gradient; bias
+// gradient = column sums of dZ (fixed order)
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, long long n, float* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += part[(long long)p * n + i];
+    out[i] = s;
+  }
+}
+
+__global__ void k_colsum(const float* __restrict__ d, int M, int N, float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  float s = 0.f;
+  for (int i = 0; i < M; ++i) s += d[(long long)i * N + j];
+  out[j] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+int mlp_err(fr_mlp* m, int code, const char* msg) {
+  if (m) {
+    std::strncpy(m->err, msg, sizeof(m->err) - 1);
+    m->err[sizeof(m->err) - 1] = 0;
+  }
+  return code;
+}
+
+#define MLP_CUDA(m, call)                                                  \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return mlp_err((m), FR_ERR_CUDA, cudaGetErrorString(e_)); \
+  } while (0)
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+int refresh_bf16(fr_mlp* m, cudaStream_t s) {
+  for (int l = 0; l < 3; ++l) {
+    const long long n = (long long)m->n[l + 1] * m->n[l];
+    count_launch();
+    k_f2bf<<<grid_for(n), 256, 0, s>>>(m->P + off_W(m, l), m->P16 + off_W(m, l), n);
+  }
+  MLP_CUDA(m, cudaGetLastError());
+  return FR_OK;
+}
+
+void free_mlp(fr_mlp* m) {
+  if (!m) return;
+  cudaFree(m->P); cudaFree(m->G); cudaFree(m->Mo); cudaFree(m->Vo); cudaFree(m->P16);
+  for (auto* p : m->Z) cudaFree(p);
+  for (auto* p : m->A) cudaFree(p);
+  for (auto* p : m->D) cudaFree(p);
+  cudaFree(m->part); cudaFree(m->X16);
+  for (auto* p : m->H16) cudaFree(p);
+  cudaFree(m->loss);
+  delete m;
+}
+
+// Reduction scratch for the loss (own copy, independent of any fr_ctx).
+struct MlpRed {
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+};
+MlpRed g_mlp_red[64];
+
+}  // namespace
+}  // namespace frk
+
+using namespace frk;
+
+extern "C" int fr_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, fr_mlp** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_in < 1 || n_hidden < 1 || n_out < 1 || max_batch < 1) return FR_ERR_INVALID_ARG;
+  fr_mlp* m = new (std::nothrow) fr_mlp();
+  if (!m) return FR_ERR_CUDA;
+  m->n[0] = n_in; m->n[1] = n_hidden; m->n[2] = n_hidden; m->n[3] = n_out;
+  m->max_batch = max_batch;
+  m->nparam = off_b(m, 2) + n_out;
+  auto fail = [&](cudaError_t e) { free_mlp(m); return e == cudaSuccess ? FR_OK : FR_ERR_CUDA; };
+  cudaError_t e = cudaSuccess;
+  const size_t np = (size_t)m->nparam;
+  if (e == cudaSuccess) e = cudaMalloc(&m->P, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->G, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->Mo, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->Vo, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->P16, np * sizeof(__nv_bfloat16));
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+    e = cudaMalloc(&m->Z[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->D[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
+  }
+  for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+    e = cudaMalloc(&m->A[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->H16[l], (size_t)max_batch * m->n[l + 1] * sizeof(__nv_bfloat16));
+  }
+  const int nparts = (max_batch + kSplitRows - 1) / kSplitRows;
+  long long maxw = 0;
+  for (int l = 0; l < 3; ++l) maxw = std::max(maxw, (long long)m->n[l + 1] * m->n[l]);
+  if (e == cudaSuccess) e = cudaMalloc(&m->part, (size_t)nparts * maxw * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->X16, (size_t)max_batch * n_in * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(m->Mo, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->Vo, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->P, 0, np * sizeof(float));
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && dev >= 0 && dev < 64 && !g_mlp_red[dev].partials) {
+    e = cudaMalloc(&g_mlp_red[dev].partials, (size_t)kRedBlocks * kMaxVec * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&g_mlp_red[dev].counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(g_mlp_red[dev].counter, 0, sizeof(unsigned));
+  }
+  if (e != cudaSuccess) return fail(e);
+  *out = m;
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_destroy(fr_mlp* m) {
+  free_mlp(m);
+  return FR_OK;
+}
+
+extern "C" const char* fr_mlp_last_error(const fr_mlp* m) { return m ? m->err : "invalid model"; }
+
+extern "C" long long fr_mlp_num_params(const fr_mlp* m) { return m ? m->nparam : 0; }
+
+extern "C" int fr_mlp_set_params(fr_mlp* m, const float* host, void* stream) {
+  if (!m || !host) return FR_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  MLP_CUDA(m, cudaMemcpyAsync(m->P, host, m->nparam * sizeof(float), cudaMemcpyHostToDevice, s));
+  MLP_CUDA(m, cudaMemsetAsync(m->Mo, 0, m->nparam * sizeof(float), s));
+  MLP_CUDA(m, cudaMemsetAsync(m->Vo, 0, m->nparam * sizeof(float), s));
+  m->step = 0;
+  FRK_TRY(refresh_bf16(m, s));
+  MLP_CUDA(m, cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_get_params(fr_mlp* m, float* host, void* stream) {
+  if (!m || !host) return FR_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  MLP_CUDA(m, cudaMemcpyAsync(host, m->P, m->nparam * sizeof(float), cudaMemcpyDeviceToHost, s));
+  MLP_CUDA(m, cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_get_grads(fr_mlp* m, float* host, void* stream) {
+  if (!m || !host) return FR_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  MLP_CUDA(m, cudaMemcpyAsync(host, m->G, m->nparam * sizeof(float), cudaMemcpyDeviceToHost, s));
+  MLP_CUDA(m, cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf16, void* stream) {
+  if (!m || !X || !Y || M < 1 || M > m->max_batch) return mlp_err(m, FR_ERR_INVALID_ARG, "bad forward arguments");
+  cudaStream_t s = as_stream(stream);
+  if (!bf16) {
+    const float* in = X;
+    for (int l = 0; l < 3; ++l) {
+      const int K = m->n[l], N = m->n[l + 1];
+      const dim3 grid((N + 63) / 64, (M + 63) / 64);
+      float* C = l < 2 ? m->A[l] : Y;
+      count_launch();
+      if (l < 2)
+        k_sgemm<true><<<grid, 256, 0, s>>>(M, N, K, in, K, 1, m->P + off_W(m, l), 1, K, C, N,
+                                           m->P + off_b(m, l), m->Z[l], 0, -1);
+      else
+        k_sgemm<false><<<grid, 256, 0, s>>>(M, N, K, in, K, 1, m->P + off_W(m, l), 1, K, C, N,
+                                            m->P + off_b(m, l), m->Z[l], 0, -1);
+      in = C;
+    }
+  } else {
+    count_launch();
+    k_f2bf<<<grid_for((long long)M * m->n[0]), 256, 0, s>>>(X, m->X16, (long long)M * m->n[0]);
+    const __nv_bfloat16* in = m->X16;
+    for (int l = 0; l < 3; ++l) {
+      const int K = m->n[l], N = m->n[l + 1];
+      const dim3 grid((N + 63) / 64, (M + 63) / 64);
+      count_launch();
+      if (l < 2)
+        k_hgemm<true, true><<<grid, 128, 0, s>>>(M, N, K, in, m->P16 + off_W(m, l), m->P + off_b(m, l), m->H16[l]);
+      else
+        k_hgemm<false, false><<<grid, 128, 0, s>>>(M, N, K, in, m->P16 + off_W(m, l), m->P + off_b(m, l), Y);
+      in = l < 2 ? m->H16[l] : nullptr;
+    }
+  }
+  MLP_CUDA(m, cudaGetLastError());
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_backward(fr_mlp* m, const float* X, const float* T, int M, double* loss_host,
+                               void* stream) {
+  if (!m || !X || !T || M < 1 || M > m->max_batch) return mlp_err(m, FR_ERR_INVALID_ARG, "bad backward arguments");
+  cudaStream_t s = as_stream(stream);
+  int dev = 0;
+  MLP_CUDA(m, cudaGetDevice(&dev));
+  Reduce red{g_mlp_red[dev].partials, g_mlp_red[dev].counter};
+  const long long nout = (long long)M * m->n[3];
+  // output: Y = Z[2] (forward_train stored it)
+  count_launch();
+  k_loss_grad<<<grid_for(nout) > 1024 ? 1024 : grid_for(nout), 256, 0, s>>>(m->Z[2], T, m->D[2], nout, m->loss, red);
+  const int nparts = (M + kSplitRows - 1) / kSplitRows;
+  for (int l = 2; l >= 0; --l) {
+    const int K = m->n[l], N = m->n[l + 1];
+    const float* in = l == 0 ? X : m->A[l - 1];
+    // dW[N x K] = sum over rows of D[l]^T (rows) x in (rows): split by rows
+    for (int p = 0; p < nparts; ++p) {
+      const int r0 = p * kSplitRows, r1 = std::min(M, r0 + kSplitRows);
+      const dim3 grid((K + 63) / 64, (N + 63) / 64);
+      count_launch();
+      // C[i=n][j=k] = sum_r D[r][n] in[r][k]; A(i,kr) = D[kr*N + i], B(kr,j) = in[kr*K + j]
+      k_sgemm<false><<<grid, 256, 0, s>>>(N, K, r1, m->D[l], 1, N, in, K, 1,
+                                          m->part + (long long)p * N * K, K, nullptr, nullptr, r0, r1);
+    }
+    count_launch();
+    k_sum_parts<<<grid_for((long long)N * K), 256, 0, s>>>(m->part, nparts, (long long)N * K, m->G + off_W(m, l));
+    count_launch();
+    k_colsum<<<(N + 127) / 128, 128, 0, s>>>(m->D[l], M, N, m->G + off_b(m, l));
+    if (l > 0) {
+      // D[l-1] = (D[l] W_l) * relu'(Z[l-1]);  D[l] [M x N], W_l [N x K]
+      const dim3 grid((K + 63) / 64, (M + 63) / 64);
+      count_launch();
+      k_sgemm<false><<<grid, 256, 0, s>>>(M, K, N, m->D[l], N, 1, m->P + off_W(m, l), K, 1, m->D[l - 1], K,
+                                          nullptr, nullptr, 0, -1);
+      count_launch();
+      k_relu_back<<<grid_for((long long)M * K), 256, 0, s>>>(m->D[l - 1], m->Z[l - 1], (long long)M * K);
+    }
+  }
+  MLP_CUDA(m, cudaGetLastError());
+  if (loss_host) {
+    MLP_CUDA(m, cudaMemcpyAsync(loss_host, m->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MLP_CUDA(m, cudaStreamSynchronize(s));
+  }
+  return FR_OK;
+}
+
+extern "C" int fr_mlp_adam(fr_mlp* m, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!m) return FR_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  m->step += 1;
+  const float c1 = 1.f - std::pow(beta1, (float)m->step);
+  const float c2 = 1.f - std::pow(beta2, (float)m->step);
+  count_launch();
+  k_adam<<<grid_for(m->nparam), 256, 0, s>>>(m->P, m->G, m->Mo, m->Vo, m->nparam, lr, beta1, beta2, eps, c1, c2);
+  MLP_CUDA(m, cudaGetLastError());
+  return refresh_bf16(m, s);
+}

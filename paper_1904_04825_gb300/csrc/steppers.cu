@@ -294,8 +294,22 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
       b = ctx->buf[B_RHS];
     }
     fr_gmres_info info{};
-    FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
+    const double* yprev = i > 0 ? ctx->buf[B_Y0 + i - 1] : nullptr;
+    if (ctx->guess) {
+      // learned initial guess; GMRES still stops at tol_lin * ||b||
+      FRK_TRY(stage_guess(ctx, b, yprev, U, Yi, s));
+      const int rc = gmres_impl(ctx, U, R0, shift, b, Yi, ctx->opts.gmres_m, ctx->opts.tol_lin,
+                                ctx->opts.gmres_max_restarts, false, &info, s);
+      st.gmres_iters += info.iters;
+      st.gmres_calls += 1;
+      if (rc == FR_ERR_NOT_CONVERGED) st.converged = 0;
+      else FRK_TRY(rc);
+    } else {
+      FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
+    }
+    FRK_TRY(stage_capture(ctx, b, yprev, U, Yi, s));
   }
+
   // q^{n+1} = q^n + sum m_j Y_j, checked before it overwrites U
   const double* xs[7];
   double cs[7];

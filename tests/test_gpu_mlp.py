@@ -1,0 +1,152 @@
+"""Learned initial guess: the MLP kernels against the oracle MLP, and the
+guess inside ROW stage solves.
+
+Tolerances: the training path runs FP32 GEMMs (u_32 = 6e-8, K <= 300 terms),
+so forward outputs and gradients match the FP64 oracle to 1e-5 relative; the
+BF16 inference path rounds inputs and weights to 8 bits, so it matches the
+oracle evaluated on BF16-rounded inputs and weights to 1e-3 relative (FP32
+accumulation) and the FP64 network to 3e-2."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle.fr2d import Mesh
+from oracle.jfnk import Problem
+from oracle.mlp import Adam, backward, forward, init_params
+from oracle.steppers import SolverOpts
+from oracle.steppers import step_row as o_row
+from oracle.tableaus import ROW
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1904_04825_gb300 as mod
+    return mod
+
+
+def _f32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _bf16_round(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+SIZES = [108, 256, 256, 36]
+
+
+def _setup(fr, M=300, seed=0):
+    rng = np.random.default_rng(seed)
+    params = init_params(SIZES, seed=seed + 1)
+    params = [(W.astype(np.float32).astype(np.float64), (0.1 * rng.standard_normal(b.shape)).astype(np.float32).astype(np.float64))
+              for W, b in params]
+    X = rng.standard_normal((M, SIZES[0])).astype(np.float32).astype(np.float64)
+    T = rng.standard_normal((M, SIZES[-1])).astype(np.float32).astype(np.float64)
+    m = fr.MLP(SIZES[0], 256, SIZES[-1], max_batch=M)
+    m.set_params(fr.flat_params(params))
+    return m, params, X, T
+
+
+def test_fp32_forward_and_gradients_match_oracle(fr):
+    import torch
+    m, params, X, T = _setup(fr)
+    Y = torch.empty((X.shape[0], SIZES[-1]), dtype=torch.float32, device="cuda")
+    m.forward(_f32(X), Y)
+    yo, _, _ = forward(params, X)
+    assert np.linalg.norm(Y.cpu().numpy() - yo) / np.linalg.norm(yo) < 1e-5
+    loss = m.backward(_f32(X), _f32(T))
+    assert abs(loss - 0.5 * np.mean((yo - T) ** 2)) < 1e-5 * loss
+    g = fr.unflat_params(m.get_grads().astype(np.float64), SIZES)
+    go = backward(params, X, T)
+    for (gW, gb), (oW, ob) in zip(g, go):
+        assert np.linalg.norm(gW - oW) / np.linalg.norm(oW) < 1e-5
+        assert np.linalg.norm(gb - ob) / np.linalg.norm(ob) < 1e-5
+
+
+def test_adam_steps_match_oracle(fr):
+    m, params, X, T = _setup(fr, M=200, seed=3)
+    opt = Adam(params, lr=1e-3)
+    import torch
+    Y = torch.empty((X.shape[0], SIZES[-1]), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        m.forward(_f32(X), Y)
+        m.backward(_f32(X), _f32(T))
+        m.adam(1e-3)
+        params = opt.step(params, backward(params, X, T))
+    got = fr.unflat_params(m.get_params().astype(np.float64), SIZES)
+    for (W, b), (Wo, bo) in zip(got, params):
+        assert np.max(np.abs(W - Wo)) < 1e-5
+        assert np.max(np.abs(b - bo)) < 1e-5
+
+
+def test_bf16_tensor_core_inference(fr):
+    import torch
+    m, params, X, T = _setup(fr, M=333, seed=5)
+    Y = torch.empty((X.shape[0], SIZES[-1]), dtype=torch.float32, device="cuda")
+    m.forward(_f32(X), Y, bf16=True)
+    yg = Y.cpu().numpy()
+    # oracle with BF16-rounded operands at every layer input (FP32 accumulation on the GPU)
+    h = _bf16_round(X)
+    for li, (W, b) in enumerate(params):
+        z = h @ _bf16_round(W).T + b
+        h = _bf16_round(np.maximum(z, 0.0)) if li < 2 else z
+    assert np.linalg.norm(yg - h) / np.linalg.norm(h) < 1e-3
+    yo, _, _ = forward(params, X)
+    assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) < 3e-2
+
+
+def test_learned_guess_in_row_stages(fr):
+    """Train on stage solves captured from plain ROW2 steps of a 20 x 20,
+    p = 2 vortex; then solve new steps from the learned guess.  GMRES still
+    meets tol_lin = 1e-12 * ||b||, so the end state matches the oracle's
+    zero-guess run to 1e-9; the initial guess cuts iterations."""
+    import torch
+    p = 2
+    xe, ye = S.uniform_mesh(20)
+    X0, Y0 = S.point_coords(xe, ye, p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=60))
+    nb = 36
+    maxs = 40000
+    Xc = torch.empty((maxs, 3 * nb), dtype=torch.float32, device="cuda")
+    Tc = torch.empty((maxs, nb), dtype=torch.float32, device="cuda")
+    fr.fr_set_stage_capture(ctx, Xc, Tc, maxs, 4)
+    for seed in range(4):
+        v = S.Vortex(x0=float(np.random.default_rng(seed).uniform(-2, 2)), alpha=4.0 + seed * 0.5)
+        U = torch.from_numpy(v.state(X0, Y0)).cuda()
+        for _ in range(3):
+            fr.step_row(ctx, 2, 0.05, U)
+    n = fr.fr_stage_capture_count(ctx)
+    assert n > 10000
+    fr.fr_set_stage_capture(ctx, None, None, 0, 1)
+    m = fr.MLP(3 * nb, 256, nb, max_batch=4096)
+    m.set_params(fr.flat_params(init_params([3 * nb, 256, 256, nb], seed=7)))
+    rng = np.random.default_rng(0)
+    Yb = torch.empty((4096, nb), dtype=torch.float32, device="cuda")
+    first = last = None
+    for it in range(400):
+        idx = torch.from_numpy(rng.integers(0, n, 4096)).cuda()
+        xb, tb = Xc[idx].contiguous(), Tc[idx].contiguous()
+        m.forward(xb, Yb)
+        loss = m.backward(xb, tb)
+        m.adam(1e-3)
+        first = loss if first is None else first
+        last = loss
+    assert last < 0.5 * first
+    # evaluation on a held-out vortex
+    v = S.Vortex(x0=1.3, alpha=4.7)
+    U0 = v.state(X0, Y0)
+    U = torch.from_numpy(U0).cuda()
+    st0 = fr.step_row(ctx, 2, 0.05, U.clone())
+    fr.fr_attach_guess_model(ctx, m)
+    st1 = fr.step_row(ctx, 2, 0.05, U)
+    fr.fr_attach_guess_model(ctx, None)
+    assert st1.converged
+    assert st1.gmres_iters <= st0.gmres_iters
+    Uo, _ = o_row(Problem(Mesh(xe, ye), p), ROW[2](), 0.05, U0, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
+    assert np.linalg.norm(U.cpu().numpy() - Uo) / np.linalg.norm(Uo) < 1e-9
