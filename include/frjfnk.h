@@ -87,6 +87,12 @@ typedef struct fr_opts {
                             re-invert shift*I - J_ee when dtau changes (default);
                             1 = form the blocks again at every pseudo iterate.
                             The paper does not say; ROW forms them once per step */
+  int guess;             /* initial guess of ROW stage solves: 0 = zero (the
+                            paper's); 1 = the same stage's solution at the previous
+                            step (zero on a first step); 2 = learned (an attached
+                            fr_mlp fed [b, previous-step stage solution, previous
+                            stage solution]; falls back to 1 without a model).
+                            GMRES stops at tol_lin * ||b|| whatever the guess */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with
@@ -197,8 +203,9 @@ int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
               const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
 
 /* ---- learned initial guess (no counterpart in the paper) ---------------
- * A per-element MLP, features [b_e/s, Y_prev,e/s, U_e/rms(U)] -> Y_e/s with
- * s = ||b||_2/sqrt(ndof), network 3nb -> hidden -> hidden -> nb with ReLU,
+ * A per-element MLP for ROW stage i of step n, features
+ * [b_e/s, Y_i^{n-1}_e/s, Y_{i-1}^n_e/s] -> Y_i^n_e/s with s = ||b||_2/sqrt(ndof)
+ * (absent states are zero), network 3nb -> hidden -> hidden -> nb with ReLU,
  * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
  * (gradients checkable against an FP64 reference); inference runs BF16
  * operands on the tensor cores with FP32 accumulation.  GMRES judges the
@@ -223,8 +230,8 @@ int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf16, void* s
 int fr_mlp_backward(fr_mlp* m, const float* X, const float* T, int M, double* loss_host, void* stream);
 /* One Adam step (with bias correction) on the FP32 weights; refreshes the BF16 copy. */
 int fr_mlp_adam(fr_mlp* m, float lr, float beta1, float beta2, float eps, void* stream);
-/* Use the model for the initial guess of every ROW stage solve of ctx
- * (NULL detaches; x0 = 0 then).  Allocates the feature buffers once. */
+/* Model for fr_opts.guess = 2 (NULL detaches).  Allocates the feature
+ * buffers once. */
 int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model);
 /* Record training pairs from step_row: after each stage solve, features and
  * targets Y_e/s of every elem_stride-th element (offset rotating per stage)
@@ -232,8 +239,9 @@ int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model);
  * X = T = NULL stops.  fr_stage_capture_count gives the samples recorded. */
 int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long max_samples, int elem_stride);
 long long fr_stage_capture_count(const fr_ctx* ctx);
-/* Features of every element for (b, Y_prev (may be NULL), U) into X [ne][3nb]. */
-int fr_stage_features(fr_ctx* ctx, const double* b, const double* yprev, const double* U, float* X,
+/* Features of every element for (b, a1, a2) into X [ne][3nb]; a1 = the
+ * stage's previous-step solution, a2 = the previous stage's (NULL = zero). */
+int fr_stage_features(fr_ctx* ctx, const double* b, const double* a1, const double* a2, float* X,
                       void* stream);
 
 /* ---- allocation-free variant (no counterpart in the paper) -------------

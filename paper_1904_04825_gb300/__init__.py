@@ -59,7 +59,8 @@ class fr_opts(ctypes.Structure):
                 ("tol_lin", ctypes.c_double), ("reorth_eta", ctypes.c_double),
                 ("mu", ctypes.c_double), ("prandtl", ctypes.c_double),
                 ("body_force_x", ctypes.c_double), ("wall_temperature", ctypes.c_double),
-                ("block_precision", ctypes.c_int), ("precond_refresh", ctypes.c_int)]
+                ("block_precision", ctypes.c_int), ("precond_refresh", ctypes.c_int),
+                ("guess", ctypes.c_int)]
 
 
 class fr_ptc_opts(ctypes.Structure):
@@ -424,5 +425,5 @@ def fr_stage_capture_count(ctx: Context) -> int:
     return int(lib.fr_stage_capture_count(ctx.handle))
 
 
-def fr_stage_features(ctx: Context, b, yprev, U, X, stream=None):
-    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(yprev), _ptr(U), _fptr(X), _stream(stream)))
+def fr_stage_features(ctx: Context, b, a1, a2, X, stream=None):
+    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(a1), _ptr(a2), _fptr(X), _stream(stream)))

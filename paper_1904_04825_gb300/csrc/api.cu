@@ -227,6 +227,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->body_force_x = 0.0;
   o->wall_temperature = 1.0;
   o->precond_refresh = 0;
+  o->guess = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -253,7 +254,8 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
       !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
-      (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1)
+      (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1 ||
+      o.guess < 0 || o.guess > 2)
     return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

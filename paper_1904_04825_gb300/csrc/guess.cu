@@ -1,9 +1,10 @@
 // Stage-solve features for the learned initial guess, the guess itself, and
 // capture of training pairs from the plain method's ROW stage solves.
 //
-// Features of element e for a stage with right-hand side b, previous stage
-// solution Y_prev and state U: [b_e / s, Y_prev,e / s, U_e / rms(U)] with
-// s = ||b||_2 / sqrt(N) (the stage scale); the guess is x0 = s * MLP(features).
+// Features of element e for ROW stage i of step n with right-hand side b:
+// [b_e / s, Y_i^{n-1}_e / s, Y_{i-1}^n_e / s] (the same stage's solution at
+// the previous step and the previous stage's solution at this step, zero
+// when absent) with s = ||b||_2 / sqrt(N); the guess is x0 = s * MLP(features).
 #include "device.cuh"
 
 struct fr_mlp;
@@ -12,17 +13,14 @@ extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf
 namespace frk {
 namespace {
 
-// X[e][0:nb) = b/s, [nb:2nb) = yprev/s (0 when null), [2nb:3nb) = U/su for the
-// elements e = e0 + stride * r, r < count; T[r][0:nb) = y/s when y != null.
-__global__ void k_features(const double* __restrict__ b, const double* __restrict__ yprev,
-                           const double* __restrict__ U, const double* __restrict__ y, int nb,
+// X[r][0:nb) = b/s, [nb:2nb) = a1/s, [2nb:3nb) = a2/s (zero for a null a1 / a2)
+// for the elements e = e0 + stride * r, r < count; T[r][0:nb) = y/s when y != null.
+__global__ void k_features(const double* __restrict__ b, const double* __restrict__ a1,
+                           const double* __restrict__ a2, const double* __restrict__ y, int nb,
                            long long e0, long long stride, long long count, const double* nb2,
-                           const double* nu2, long long ndof, float* __restrict__ X,
-                           float* __restrict__ T) {
+                           long long ndof, float* __restrict__ X, float* __restrict__ T) {
   const double s = sqrt(*nb2 / (double)ndof);
   const double is = s > 0.0 ? 1.0 / s : 1.0;
-  const double su = sqrt(*nu2 / (double)ndof);
-  const double isu = su > 0.0 ? 1.0 / su : 1.0;
   const long long n = count * nb;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const long long r = t / nb;
@@ -30,8 +28,8 @@ __global__ void k_features(const double* __restrict__ b, const double* __restric
     const long long g = (e0 + stride * r) * nb + c;
     float* xr = X + r * 3 * nb;
     xr[c] = (float)(b[g] * is);
-    xr[nb + c] = yprev ? (float)(yprev[g] * is) : 0.f;
-    xr[2 * nb + c] = (float)(U[g] * isu);
+    xr[nb + c] = a1 ? (float)(a1[g] * is) : 0.f;
+    xr[2 * nb + c] = a2 ? (float)(a2[g] * is) : 0.f;
     if (T) T[r * nb + c] = (float)(y[g] * is);
   }
 }
@@ -52,15 +50,15 @@ unsigned grid_of(long long n) {
 
 }  // namespace
 
-// Guess for one stage solve into x0 (device, ndof).
-int stage_guess(fr_ctx* ctx, const double* b, const double* yprev, const double* U, double* x0,
+// Learned guess for one stage solve into x0 (device, ndof); a1 = the same
+// stage's previous-step solution, a2 = the previous stage's solution (either
+// may be null).
+int stage_guess(fr_ctx* ctx, const double* b, const double* a1, const double* a2, double* x0,
                 cudaStream_t s) {
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
-  FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_GU2, s));
   count_launch();
-  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, yprev, U, nullptr, ctx->nb, 0, 1, ctx->ne,
-                                                      ctx->scal + S_GB2, ctx->scal + S_GU2, ctx->ndof,
-                                                      ctx->gfeat, nullptr);
+  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, a1, a2, nullptr, ctx->nb, 0, 1, ctx->ne,
+                                                      ctx->scal + S_GB2, ctx->ndof, ctx->gfeat, nullptr);
   FRK_LAUNCHED(ctx);
   const int rc = fr_mlp_forward(ctx->guess, ctx->gfeat, (int)ctx->ne, ctx->gout, 1, s);
   if (rc != FR_OK) return set_error(ctx, rc, "learned guess: MLP forward failed");
@@ -71,7 +69,7 @@ int stage_guess(fr_ctx* ctx, const double* b, const double* yprev, const double*
 }
 
 // Record (features, target) of the elements sampled from one finished stage.
-int stage_capture(fr_ctx* ctx, const double* b, const double* yprev, const double* U, const double* y,
+int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* a2, const double* y,
                   cudaStream_t s) {
   StageCapture& C = ctx->cap;
   if (!C.X || C.count >= C.max) return FR_OK;
@@ -81,10 +79,9 @@ int stage_capture(fr_ctx* ctx, const double* b, const double* yprev, const doubl
   if (avail > C.max - C.count) avail = C.max - C.count;
   if (avail <= 0) return FR_OK;
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
-  FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_GU2, s));
   count_launch();
-  k_features<<<grid_of(avail * ctx->nb), 256, 0, s>>>(b, yprev, U, y, ctx->nb, e0, stride, avail,
-                                                    ctx->scal + S_GB2, ctx->scal + S_GU2, ctx->ndof,
+  k_features<<<grid_of(avail * ctx->nb), 256, 0, s>>>(b, a1, a2, y, ctx->nb, e0, stride, avail,
+                                                    ctx->scal + S_GB2, ctx->ndof,
                                                     C.X + C.count * 3 * ctx->nb, C.T + C.count * ctx->nb);
   FRK_LAUNCHED(ctx);
   C.count += avail;
@@ -121,16 +118,14 @@ extern "C" int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long m
 
 extern "C" long long fr_stage_capture_count(const fr_ctx* ctx) { return ctx ? ctx->cap.count : 0; }
 
-extern "C" int fr_stage_features(fr_ctx* ctx, const double* b, const double* yprev, const double* U,
+extern "C" int fr_stage_features(fr_ctx* ctx, const double* b, const double* a1, const double* a2,
                                  float* X, void* stream) {
-  if (!ctx || !b || !U || !X) return FR_ERR_INVALID_ARG;
+  if (!ctx || !b || !X) return FR_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
-  FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_GU2, s));
   count_launch();
-  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, yprev, U, nullptr, ctx->nb, 0, 1, ctx->ne,
-                                                      ctx->scal + S_GB2, ctx->scal + S_GU2, ctx->ndof, X,
-                                                      nullptr);
+  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, a1, a2, nullptr, ctx->nb, 0, 1, ctx->ne,
+                                                      ctx->scal + S_GB2, ctx->ndof, X, nullptr);
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }

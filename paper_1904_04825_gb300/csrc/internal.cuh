@@ -114,6 +114,7 @@ struct fr_ctx {
   double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
+  int hist_row = 0;          // ROW order of the last step if its stage solutions are intact
   fr_mlp* guess = nullptr;   // learned initial-guess model (ROW stages), or null
   float* gfeat = nullptr;    // [ne][3 nb] features for the guess
   float* gout = nullptr;     // [ne][nb] model output
@@ -219,9 +220,9 @@ int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
 int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s);
 // guess.cu
-int stage_guess(fr_ctx* ctx, const double* b, const double* yprev, const double* U, double* x0,
+int stage_guess(fr_ctx* ctx, const double* b, const double* a1, const double* a2, double* x0,
                 cudaStream_t s);
-int stage_capture(fr_ctx* ctx, const double* b, const double* yprev, const double* U, const double* y,
+int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* a2, const double* y,
                   cudaStream_t s);
 
 }  // namespace frk

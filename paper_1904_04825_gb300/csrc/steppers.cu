@@ -260,6 +260,8 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
   const RowTab t = row_tableau(scheme);
   fr_step_stats st{};
   st.converged = 1;
+  const bool hist = ctx->hist_row == scheme;  // stage solutions of the last step still in place
+  ctx->hist_row = 0;
   const double shift = 1.0 / (t.gamma * dt);
   double* R0 = ctx->buf[B_R0];
   FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R0, 0.0, nullptr, nullptr, s));
@@ -294,20 +296,31 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
       b = ctx->buf[B_RHS];
     }
     fr_gmres_info info{};
+    // previous stage of this step, and this stage's solution at the previous
+    // step (still in Yi when the last step was a ROW step of this scheme)
     const double* yprev = i > 0 ? ctx->buf[B_Y0 + i - 1] : nullptr;
-    if (ctx->guess) {
-      // learned initial guess; GMRES still stops at tol_lin * ||b||
-      FRK_TRY(stage_guess(ctx, b, yprev, U, Yi, s));
+    const double* ylast = nullptr;
+    if (hist && (ctx->cap.X || ctx->guess)) {
+      FRK_TRY(launch_copy(ctx, ctx->buf[B_STAGE], Yi, s));  // B_STAGE is free after R(U_i)
+      ylast = ctx->buf[B_STAGE];
+    }
+    int mode = ctx->opts.guess;
+    if (mode == 2 && !ctx->guess) mode = 1;
+    if (mode == 1 && !hist) mode = 0;
+    if (mode == 0) {
+      FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
+    } else {
+      // nonzero initial guess: the previous step's solution (mode 1) or the
+      // learned one (mode 2); GMRES still stops at tol_lin * ||b||
+      if (mode == 2) FRK_TRY(stage_guess(ctx, b, ylast, yprev, Yi, s));
       const int rc = gmres_impl(ctx, U, R0, shift, b, Yi, ctx->opts.gmres_m, ctx->opts.tol_lin,
                                 ctx->opts.gmres_max_restarts, false, &info, s);
       st.gmres_iters += info.iters;
       st.gmres_calls += 1;
       if (rc == FR_ERR_NOT_CONVERGED) st.converged = 0;
       else FRK_TRY(rc);
-    } else {
-      FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
     }
-    FRK_TRY(stage_capture(ctx, b, yprev, U, Yi, s));
+    FRK_TRY(stage_capture(ctx, b, ylast, yprev, Yi, s));
   }
 
   // q^{n+1} = q^n + sum m_j Y_j, checked before it overwrites U
@@ -322,6 +335,7 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
   if (!std::isfinite(nn)) return set_error(ctx, FR_ERR_NONFINITE, "step_row: new state not finite");
   FRK_TRY(launch_copy(ctx, U, ctx->buf[B_NEW], s));
   FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->hist_row = scheme;
   if (!st.converged) return set_error(ctx, FR_ERR_NOT_CONVERGED, "step_row: a stage solve did not converge");
   return FR_OK;
 }
@@ -337,6 +351,7 @@ extern "C" int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const 
   cudaStream_t s = as_stream(stream);
   const EsdirkTab t = esdirk_tableau(scheme);
   const double omega = t.A[1][1];
+  ctx->hist_row = 0;
   fr_step_stats st{};
   st.converged = 1;
   // stage residuals R(q_j) in B_Y0 + j
@@ -383,6 +398,7 @@ extern "C" int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int 
   cudaStream_t s = as_stream(stream);
   fr_step_stats st{};
   st.converged = 1;
+  ctx->hist_row = 0;
   double omega, a1, a2;
   if (first_step) { omega = 1.0; a1 = 1.0; a2 = 0.0; }
   else { omega = 2.0 / 3.0; a1 = 4.0 / 3.0; a2 = -1.0 / 3.0; }

@@ -102,51 +102,70 @@ def test_bf16_tensor_core_inference(fr):
 
 
 def test_learned_guess_in_row_stages(fr):
-    """Train on stage solves captured from plain ROW2 steps of a 20 x 20,
-    p = 2 vortex; then solve new steps from the learned guess.  GMRES still
-    meets tol_lin = 1e-12 * ||b||, so the end state matches the oracle's
-    zero-guess run to 1e-9; the initial guess cuts iterations."""
+    """Train on stage solves captured from plain ROW2 steps (zero guess) of
+    20 x 20, p = 2 vortices; then run a held-out vortex with the zero guess,
+    the previous-step guess and the learned guess at tol_lin = 1e-8.  GMRES
+    judges every guess (same absolute target tol * ||b||), so the states
+    agree at the tolerance level; the guesses cut iterations.  At
+    tol_lin = 1e-12 the learned-guess run matches the oracle to 1e-9."""
     import torch
     p = 2
     xe, ye = S.uniform_mesh(20)
     X0, Y0 = S.point_coords(xe, ye, p)
-    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=60))
     nb = 36
-    maxs = 40000
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-8, gmres_max_restarts=60))
+    maxs = 60000
     Xc = torch.empty((maxs, 3 * nb), dtype=torch.float32, device="cuda")
     Tc = torch.empty((maxs, nb), dtype=torch.float32, device="cuda")
-    fr.fr_set_stage_capture(ctx, Xc, Tc, maxs, 4)
+    fr.fr_set_stage_capture(ctx, Xc, Tc, maxs, 1)
+    rng = np.random.default_rng(11)
     for seed in range(4):
-        v = S.Vortex(x0=float(np.random.default_rng(seed).uniform(-2, 2)), alpha=4.0 + seed * 0.5)
+        v = S.Vortex(x0=float(rng.uniform(-2, 2)), y0=float(rng.uniform(-2, 2)), alpha=float(rng.uniform(3, 6)))
         U = torch.from_numpy(v.state(X0, Y0)).cuda()
-        for _ in range(3):
+        for _ in range(4):
             fr.step_row(ctx, 2, 0.05, U)
     n = fr.fr_stage_capture_count(ctx)
-    assert n > 10000
+    assert n == 4 * 4 * 3 * 400          # vortices x steps x stages x elements
     fr.fr_set_stage_capture(ctx, None, None, 0, 1)
     m = fr.MLP(3 * nb, 256, nb, max_batch=4096)
     m.set_params(fr.flat_params(init_params([3 * nb, 256, 256, nb], seed=7)))
-    rng = np.random.default_rng(0)
     Yb = torch.empty((4096, nb), dtype=torch.float32, device="cuda")
-    first = last = None
-    for it in range(400):
+    losses = []
+    for it in range(600):
         idx = torch.from_numpy(rng.integers(0, n, 4096)).cuda()
         xb, tb = Xc[idx].contiguous(), Tc[idx].contiguous()
         m.forward(xb, Yb)
-        loss = m.backward(xb, tb)
-        m.adam(1e-3)
-        first = loss if first is None else first
-        last = loss
-    assert last < 0.5 * first
-    # evaluation on a held-out vortex
-    v = S.Vortex(x0=1.3, alpha=4.7)
+        losses.append(m.backward(xb, tb))
+        m.adam(1e-3 if it < 400 else 3e-4)
+    assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:5])
+
+    v = S.Vortex(x0=1.3, y0=-0.7, alpha=4.7)
     U0 = v.state(X0, Y0)
+    iters, finals = {}, {}
+    for mode in (0, 1, 2):
+        c = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-8, gmres_max_restarts=60, guess=mode))
+        if mode == 2:
+            fr.fr_attach_guess_model(c, m)
+        U = torch.from_numpy(U0).cuda()
+        total = 0
+        for k in range(4):
+            st = fr.step_row(c, 2, 0.05, U)
+            assert st.converged
+            total += st.gmres_iters if k > 0 else 0   # first step has no history
+        iters[mode] = total
+        finals[mode] = U.cpu().numpy()
+    assert iters[1] < iters[0]
+    assert iters[2] < iters[0]
+    for mode in (1, 2):
+        assert np.linalg.norm(finals[mode] - finals[0]) / np.linalg.norm(finals[0]) < 1e-7
+
+    c = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=60, guess=2))
+    fr.fr_attach_guess_model(c, m)
     U = torch.from_numpy(U0).cuda()
-    st0 = fr.step_row(ctx, 2, 0.05, U.clone())
-    fr.fr_attach_guess_model(ctx, m)
-    st1 = fr.step_row(ctx, 2, 0.05, U)
-    fr.fr_attach_guess_model(ctx, None)
-    assert st1.converged
-    assert st1.gmres_iters <= st0.gmres_iters
-    Uo, _ = o_row(Problem(Mesh(xe, ye), p), ROW[2](), 0.05, U0, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
+    Uo = U0.copy()
+    prob = Problem(Mesh(xe, ye), p)
+    for _ in range(2):
+        fr.step_row(c, 2, 0.05, U)
+        Uo, _ = o_row(prob, ROW[2](), 0.05, Uo, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
     assert np.linalg.norm(U.cpu().numpy() - Uo) / np.linalg.norm(Uo) < 1e-9
+    print("GMRES iterations over steps 2-4 (zero / previous-step / learned):", iters)
