@@ -204,8 +204,9 @@ int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
 
 /* ---- learned initial guess (no counterpart in the paper) ---------------
  * A per-element MLP for ROW stage i of step n, features
- * [b_e/s, Y_i^{n-1}_e/s, Y_{i-1}^n_e/s] -> Y_i^n_e/s with s = ||b||_2/sqrt(ndof)
- * (absent states are zero), network 3nb -> hidden -> hidden -> nb with ReLU,
+ * [b_e/s, Y_i^{n-1}_e/s, Y_{i-1}^n_e/s] -> (Y_i^n - Y_i^{n-1})_e/s with
+ * s = ||b||_2/sqrt(ndof) (absent states are zero); the guess is
+ * Y_i^{n-1} + s MLP(features).  Network 3nb -> hidden -> hidden -> nb, ReLU,
  * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
  * (gradients checkable against an FP64 reference); inference runs BF16
  * operands on the tensor cores with FP32 accumulation.  GMRES judges the
@@ -234,7 +235,7 @@ int fr_mlp_adam(fr_mlp* m, float lr, float beta1, float beta2, float eps, void* 
  * buffers once. */
 int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model);
 /* Record training pairs from step_row: after each stage solve, features and
- * targets Y_e/s of every elem_stride-th element (offset rotating per stage)
+ * targets (Y_i^n - Y_i^{n-1})_e/s of every elem_stride-th element (offset rotating per stage)
  * into the device arrays X [max][3nb] and T [max][nb] until max samples.
  * X = T = NULL stops.  fr_stage_capture_count gives the samples recorded. */
 int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long max_samples, int elem_stride);

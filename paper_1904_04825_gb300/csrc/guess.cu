@@ -4,7 +4,10 @@
 // Features of element e for ROW stage i of step n with right-hand side b:
 // [b_e / s, Y_i^{n-1}_e / s, Y_{i-1}^n_e / s] (the same stage's solution at
 // the previous step and the previous stage's solution at this step, zero
-// when absent) with s = ||b||_2 / sqrt(N); the guess is x0 = s * MLP(features).
+// when absent) with s = ||b||_2 / sqrt(N).  The model predicts the change
+// from the previous-step solution: x0 = Y_i^{n-1} + s * MLP(features), target
+// (Y_i^n - Y_i^{n-1}) / s, so an imperfect model still starts GMRES near the
+// previous-step guess.
 #include "device.cuh"
 
 struct fr_mlp;
@@ -14,7 +17,7 @@ namespace frk {
 namespace {
 
 // X[r][0:nb) = b/s, [nb:2nb) = a1/s, [2nb:3nb) = a2/s (zero for a null a1 / a2)
-// for the elements e = e0 + stride * r, r < count; T[r][0:nb) = y/s when y != null.
+// for the elements e = e0 + stride * r, r < count; T[r][0:nb) = (y - a1)/s when y != null.
 __global__ void k_features(const double* __restrict__ b, const double* __restrict__ a1,
                            const double* __restrict__ a2, const double* __restrict__ y, int nb,
                            long long e0, long long stride, long long count, const double* nb2,
@@ -30,16 +33,16 @@ __global__ void k_features(const double* __restrict__ b, const double* __restric
     xr[c] = (float)(b[g] * is);
     xr[nb + c] = a1 ? (float)(a1[g] * is) : 0.f;
     xr[2 * nb + c] = a2 ? (float)(a2[g] * is) : 0.f;
-    if (T) T[r * nb + c] = (float)(y[g] * is);
+    if (T) T[r * nb + c] = (float)((a1 ? y[g] - a1[g] : y[g]) * is);
   }
 }
 
-// x0 = s * out
-__global__ void k_unscale(const float* __restrict__ out, const double* nb2, long long ndof,
-                          double* __restrict__ x0) {
+// x0 = a1 + s * out (a1 may be null)
+__global__ void k_unscale(const float* __restrict__ out, const double* __restrict__ a1, const double* nb2,
+                          long long ndof, double* __restrict__ x0) {
   const double s = sqrt(*nb2 / (double)ndof);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += (long long)gridDim.x * blockDim.x)
-    x0[i] = s * (double)out[i];
+    x0[i] = fma(s, (double)out[i], a1 ? a1[i] : 0.0);
 }
 
 unsigned grid_of(long long n) {
@@ -63,7 +66,7 @@ int stage_guess(fr_ctx* ctx, const double* b, const double* a1, const double* a2
   const int rc = fr_mlp_forward(ctx->guess, ctx->gfeat, (int)ctx->ne, ctx->gout, 1, s);
   if (rc != FR_OK) return set_error(ctx, rc, "learned guess: MLP forward failed");
   count_launch();
-  k_unscale<<<grid_of(ctx->ndof), 256, 0, s>>>(ctx->gout, ctx->scal + S_GB2, ctx->ndof, x0);
+  k_unscale<<<grid_of(ctx->ndof), 256, 0, s>>>(ctx->gout, a1, ctx->scal + S_GB2, ctx->ndof, x0);
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
