@@ -204,9 +204,11 @@ int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
 
 /* ---- learned initial guess (no counterpart in the paper) ---------------
  * A per-element MLP for ROW stage i of step n, features
- * [b_e/s, Y_i^{n-1}_e/s, Y_{i-1}^n_e/s] -> (Y_i^n - Y_i^{n-1})_e/s with
- * s = ||b||_2/sqrt(ndof) (absent states are zero); the guess is
- * Y_i^{n-1} + s MLP(features).  Network 3nb -> hidden -> hidden -> nb, ReLU,
+ * [b_e/s, (b - b^{n-1})_e/s, Y_i^{n-1}_e/s] -> (Y_i^n - Y_i^{n-1})_e/s with
+ * s = ||b||_2/sqrt(ndof) (the stage's right-hand side and solution at the
+ * previous step; zero when absent); the guess is Y_i^{n-1} + s MLP(features),
+ * kept only when its residual ||b - A x0|| is below that of Y_i^{n-1}.
+ * Network 3nb -> hidden -> hidden -> nb, ReLU,
  * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
  * (gradients checkable against an FP64 reference); inference runs BF16
  * operands on the tensor cores with FP32 accumulation.  GMRES judges the
@@ -240,10 +242,15 @@ int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model);
  * X = T = NULL stops.  fr_stage_capture_count gives the samples recorded. */
 int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long max_samples, int elem_stride);
 long long fr_stage_capture_count(const fr_ctx* ctx);
-/* Features of every element for (b, a1, a2) into X [ne][3nb]; a1 = the
- * stage's previous-step solution, a2 = the previous stage's (NULL = zero). */
-int fr_stage_features(fr_ctx* ctx, const double* b, const double* a1, const double* a2, float* X,
+/* Features of every element for (b, bl, yl) into X [ne][3nb]; bl / yl = the
+ * stage's previous-step right-hand side / solution (NULL = zero). */
+int fr_stage_features(fr_ctx* ctx, const double* b, const double* bl, const double* yl, float* X,
                       void* stream);
+/* Forget the stage solutions of the last step (call when U is replaced by an
+ * unrelated state); the next ROW step then starts from zero guesses. */
+int fr_reset_history(fr_ctx* ctx);
+/* Stage solves where a learned guess was formed, and where it was kept. */
+int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
 
 /* ---- allocation-free variant (no counterpart in the paper) -------------
  * y = shift*z - (R(U + eps z) - R0)/eps exactly as fr_jv computes it, but

@@ -122,6 +122,8 @@ def _load():
         "fr_set_stage_capture": (I, [P, P, P, ctypes.c_longlong, I]),
         "fr_stage_capture_count": (ctypes.c_longlong, [P]),
         "fr_stage_features": (I, [P, P, P, P, P, V]),
+        "fr_reset_history": (I, [P]),
+        "fr_guess_stats": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "fr_profile_begin": (I, [P, ctypes.c_uint]),
         "fr_profile_end": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -425,5 +427,19 @@ def fr_stage_capture_count(ctx: Context) -> int:
     return int(lib.fr_stage_capture_count(ctx.handle))
 
 
-def fr_stage_features(ctx: Context, b, a1, a2, X, stream=None):
-    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(a1), _ptr(a2), _fptr(X), _stream(stream)))
+def fr_stage_features(ctx: Context, b, bl, yl, X, stream=None):
+    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(bl), _ptr(yl), _fptr(X), _stream(stream)))
+
+
+def fr_reset_history(ctx: Context):
+    return ctx.check(lib.fr_reset_history(ctx.handle))
+
+
+def fr_guess_stats(ctx: Context):
+    t, u = ctx_ll(), ctx_ll()
+    ctx.check(lib.fr_guess_stats(ctx.handle, ctypes.byref(t), ctypes.byref(u)))
+    return int(t.value), int(u.value)
+
+
+def ctx_ll():
+    return ctypes.c_longlong()

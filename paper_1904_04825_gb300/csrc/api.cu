@@ -31,6 +31,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->mst);
   cudaFree(c->rloc);
   cudaFree(c->gfeat);
+  for (double* p : c->bhist) cudaFree(p);
   cudaFree(c->gout);
   cudaFree(c->V);
   cudaFree(c->z);

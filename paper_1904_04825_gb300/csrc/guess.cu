@@ -2,12 +2,12 @@
 // capture of training pairs from the plain method's ROW stage solves.
 //
 // Features of element e for ROW stage i of step n with right-hand side b:
-// [b_e / s, Y_i^{n-1}_e / s, Y_{i-1}^n_e / s] (the same stage's solution at
-// the previous step and the previous stage's solution at this step, zero
-// when absent) with s = ||b||_2 / sqrt(N).  The model predicts the change
-// from the previous-step solution: x0 = Y_i^{n-1} + s * MLP(features), target
-// (Y_i^n - Y_i^{n-1}) / s, so an imperfect model still starts GMRES near the
-// previous-step guess.
+// [b_e / s, (b_e - b^{n-1}_e) / s, Y_i^{n-1}_e / s] (this stage's right-hand
+// side and solution at the previous step, zero when absent) with
+// s = ||b||_2 / sqrt(N).  The model predicts the change from the previous-step
+// solution: x0 = Y_i^{n-1} + s * MLP(features), target (Y_i^n - Y_i^{n-1}) / s.
+// The learned guess is kept only when ||b - A x0|| is below the residual of
+// the previous-step guess (two extra FD products per stage).
 #include "device.cuh"
 
 struct fr_mlp;
@@ -16,10 +16,11 @@ extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf
 namespace frk {
 namespace {
 
-// X[r][0:nb) = b/s, [nb:2nb) = a1/s, [2nb:3nb) = a2/s (zero for a null a1 / a2)
-// for the elements e = e0 + stride * r, r < count; T[r][0:nb) = (y - a1)/s when y != null.
-__global__ void k_features(const double* __restrict__ b, const double* __restrict__ a1,
-                           const double* __restrict__ a2, const double* __restrict__ y, int nb,
+// X[r][0:nb) = b/s, [nb:2nb) = (b - bl)/s, [2nb:3nb) = yl/s (zero for a null
+// bl / yl) for the elements e = e0 + stride * r, r < count; T[r][0:nb) =
+// (y - yl)/s when y != null.
+__global__ void k_features(const double* __restrict__ b, const double* __restrict__ bl,
+                           const double* __restrict__ yl, const double* __restrict__ y, int nb,
                            long long e0, long long stride, long long count, const double* nb2,
                            long long ndof, float* __restrict__ X, float* __restrict__ T) {
   const double s = sqrt(*nb2 / (double)ndof);
@@ -31,9 +32,9 @@ __global__ void k_features(const double* __restrict__ b, const double* __restric
     const long long g = (e0 + stride * r) * nb + c;
     float* xr = X + r * 3 * nb;
     xr[c] = (float)(b[g] * is);
-    xr[nb + c] = a1 ? (float)(a1[g] * is) : 0.f;
-    xr[2 * nb + c] = a2 ? (float)(a2[g] * is) : 0.f;
-    if (T) T[r * nb + c] = (float)((a1 ? y[g] - a1[g] : y[g]) * is);
+    xr[nb + c] = bl ? (float)((b[g] - bl[g]) * is) : 0.f;
+    xr[2 * nb + c] = yl ? (float)(yl[g] * is) : 0.f;
+    if (T) T[r * nb + c] = (float)((yl ? y[g] - yl[g] : y[g]) * is);
   }
 }
 
@@ -53,26 +54,42 @@ unsigned grid_of(long long n) {
 
 }  // namespace
 
-// Learned guess for one stage solve into x0 (device, ndof); a1 = the same
-// stage's previous-step solution, a2 = the previous stage's solution (either
-// may be null).
-int stage_guess(fr_ctx* ctx, const double* b, const double* a1, const double* a2, double* x0,
-                cudaStream_t s) {
+int alloc_guess_buffers(fr_ctx* ctx);
+
+// Learned guess for one stage solve into x0 (device, ndof) from (b, bl, yl)
+// (bl / yl: previous-step right-hand side / solution of the stage).
+int stage_guess(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                const double* bl, const double* yl, double* x0, cudaStream_t s) {
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
   count_launch();
-  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, a1, a2, nullptr, ctx->nb, 0, 1, ctx->ne,
+  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, bl, yl, nullptr, ctx->nb, 0, 1, ctx->ne,
                                                       ctx->scal + S_GB2, ctx->ndof, ctx->gfeat, nullptr);
   FRK_LAUNCHED(ctx);
   const int rc = fr_mlp_forward(ctx->guess, ctx->gfeat, (int)ctx->ne, ctx->gout, 1, s);
   if (rc != FR_OK) return set_error(ctx, rc, "learned guess: MLP forward failed");
   count_launch();
-  k_unscale<<<grid_of(ctx->ndof), 256, 0, s>>>(ctx->gout, a1, ctx->scal + S_GB2, ctx->ndof, x0);
+  k_unscale<<<grid_of(ctx->ndof), 256, 0, s>>>(ctx->gout, yl, ctx->scal + S_GB2, ctx->ndof, x0);
   FRK_LAUNCHED(ctx);
+  if (!yl) return FR_OK;
+  // safeguard: residuals of the learned and of the previous-step guess
+  double* r = ctx->buf[B_GUESS_R];
+  FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_NU2, s));
+  FRK_TRY(launch_sumsq(ctx, x0, ctx->scal + S_NZ2, s, true));
+  FRK_TRY(launch_residual(ctx, 2, U, x0, R0, b, r, shift, ctx->scal + S_EPS, nullptr, s));
+  FRK_TRY(launch_sumsq(ctx, r, ctx->scal + S_GR1, s));
+  FRK_TRY(launch_sumsq(ctx, yl, ctx->scal + S_NZ2, s, true));
+  FRK_TRY(launch_residual(ctx, 2, U, yl, R0, b, r, shift, ctx->scal + S_EPS, nullptr, s));
+  FRK_TRY(launch_sumsq(ctx, r, ctx->scal + S_GR2, s));
+  FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 4, ctx->scal + S_GR1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->guess_used += ctx->h_scal[4] < ctx->h_scal[5] ? 1 : 0;
+  ctx->guess_tried += 1;
+  if (!(ctx->h_scal[4] < ctx->h_scal[5])) FRK_TRY(launch_copy(ctx, x0, yl, s));
   return FR_OK;
 }
 
 // Record (features, target) of the elements sampled from one finished stage.
-int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* a2, const double* y,
+int stage_capture(fr_ctx* ctx, const double* b, const double* bl, const double* yl, const double* y,
                   cudaStream_t s) {
   StageCapture& C = ctx->cap;
   if (!C.X || C.count >= C.max) return FR_OK;
@@ -83,7 +100,7 @@ int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* 
   if (avail <= 0) return FR_OK;
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
   count_launch();
-  k_features<<<grid_of(avail * ctx->nb), 256, 0, s>>>(b, a1, a2, y, ctx->nb, e0, stride, avail,
+  k_features<<<grid_of(avail * ctx->nb), 256, 0, s>>>(b, bl, yl, y, ctx->nb, e0, stride, avail,
                                                     ctx->scal + S_GB2, ctx->ndof,
                                                     C.X + C.count * 3 * ctx->nb, C.T + C.count * ctx->nb);
   FRK_LAUNCHED(ctx);
@@ -96,13 +113,36 @@ int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* 
 
 using namespace frk;
 
-extern "C" int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model) {
-  if (!ctx) return FR_ERR_INVALID_ARG;
-  ctx->guess = model;
-  if (model && !ctx->gfeat) {
+int alloc_guess_buffers(fr_ctx* ctx) {
+  if (!ctx->gfeat) {
     FRK_CUDA(ctx, cudaMalloc(reinterpret_cast<void**>(&ctx->gfeat), (size_t)ctx->ne * 3 * ctx->nb * sizeof(float)));
     FRK_CUDA(ctx, cudaMalloc(reinterpret_cast<void**>(&ctx->gout), (size_t)ctx->ne * ctx->nb * sizeof(float)));
   }
+  for (double*& p : ctx->bhist)
+    if (!p) {
+      FRK_CUDA(ctx, cudaMalloc(reinterpret_cast<void**>(&p), (size_t)ctx->ndof * sizeof(double)));
+      FRK_CUDA(ctx, cudaMemset(p, 0, (size_t)ctx->ndof * sizeof(double)));
+    }
+  return FR_OK;
+}
+
+extern "C" int fr_attach_guess_model(fr_ctx* ctx, fr_mlp* model) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->guess = model;
+  if (model) FRK_TRY(alloc_guess_buffers(ctx));
+  return FR_OK;
+}
+
+extern "C" int fr_reset_history(fr_ctx* ctx) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->hist_row = 0;
+  return FR_OK;
+}
+
+extern "C" int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (tried) *tried = ctx->guess_tried;
+  if (used) *used = ctx->guess_used;
   return FR_OK;
 }
 
@@ -110,6 +150,7 @@ extern "C" int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long m
   if (!ctx) return FR_ERR_INVALID_ARG;
   if ((X == nullptr) != (T == nullptr) || max_samples < 0 || elem_stride < 1)
     return set_error(ctx, FR_ERR_INVALID_ARG, "fr_set_stage_capture: bad arguments");
+  if (X) FRK_TRY(alloc_guess_buffers(ctx));
   ctx->cap.X = X;
   ctx->cap.T = T;
   ctx->cap.max = max_samples;
@@ -121,13 +162,13 @@ extern "C" int fr_set_stage_capture(fr_ctx* ctx, float* X, float* T, long long m
 
 extern "C" long long fr_stage_capture_count(const fr_ctx* ctx) { return ctx ? ctx->cap.count : 0; }
 
-extern "C" int fr_stage_features(fr_ctx* ctx, const double* b, const double* a1, const double* a2,
+extern "C" int fr_stage_features(fr_ctx* ctx, const double* b, const double* bl, const double* yl,
                                  float* X, void* stream) {
   if (!ctx || !b || !X) return FR_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   FRK_TRY(launch_sumsq(ctx, b, ctx->scal + S_GB2, s));
   count_launch();
-  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, a1, a2, nullptr, ctx->nb, 0, 1, ctx->ne,
+  k_features<<<grid_of(ctx->ne * ctx->nb), 256, 0, s>>>(b, bl, yl, nullptr, ctx->nb, 0, 1, ctx->ne,
                                                       ctx->scal + S_GB2, ctx->ndof, X, nullptr);
   FRK_LAUNCHED(ctx);
   return FR_OK;

@@ -60,7 +60,7 @@ struct GmresDev {
 };
 
 // Device scalars (sums of squares) used by the FD step and GMRES.
-enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_COUNT };
+enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_GR1, S_GR2, S_COUNT };
 
 // FD step eps = eps_rel (1 + ||U||) / ||z|| (or eps_fixed), written once per
 // product as (eps, 1/eps) by the kernel that finishes ||z||^2.
@@ -118,6 +118,8 @@ struct fr_ctx {
   fr_mlp* guess = nullptr;   // learned initial-guess model (ROW stages), or null
   float* gfeat = nullptr;    // [ne][3 nb] features for the guess
   float* gout = nullptr;     // [ne][nb] model output
+  double* bhist[6] = {};     // right-hand sides of the last ROW step's stages (guess features)
+  long long guess_tried = 0, guess_used = 0;
   frk::StageCapture cap;
   double* blocks = nullptr;  // [ne][nb][nb] inverse blocks, column-major per element
   int blocks_valid = 0;
@@ -219,10 +221,11 @@ int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
 int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s);
-// guess.cu
-int stage_guess(fr_ctx* ctx, const double* b, const double* a1, const double* a2, double* x0,
-                cudaStream_t s);
-int stage_capture(fr_ctx* ctx, const double* b, const double* a1, const double* a2, const double* y,
+// guess.cu (B_GUESS_R: stepper buffer free while a stage solve starts)
+constexpr int B_GUESS_R = 3;
+int stage_guess(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                const double* bl, const double* yl, double* x0, cudaStream_t s);
+int stage_capture(fr_ctx* ctx, const double* b, const double* bl, const double* yl, const double* y,
                   cudaStream_t s);
 
 }  // namespace frk

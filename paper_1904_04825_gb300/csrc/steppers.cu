@@ -141,6 +141,7 @@ enum {
   B_R0 = 0, B_RHS, B_STAGE, B_RSTAGE, B_CONST, B_F, B_DQ, B_Q, B_RQ, B_NEW,
   B_Y0 = 10  // 6 stage vectors B_Y0 .. B_Y0+5
 };
+static_assert(B_GUESS_R == B_RSTAGE, "guess residual buffer");
 
 int read_scalar(fr_ctx* ctx, const double* dev, double* host, cudaStream_t s) {
   FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 3, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -296,23 +297,26 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
       b = ctx->buf[B_RHS];
     }
     fr_gmres_info info{};
-    // previous stage of this step, and this stage's solution at the previous
-    // step (still in Yi when the last step was a ROW step of this scheme)
-    const double* yprev = i > 0 ? ctx->buf[B_Y0 + i - 1] : nullptr;
+    // this stage's solution and right-hand side at the previous step (still in
+    // place when the last step was a ROW step of this scheme on this state)
+    const bool learn = ctx->cap.X || (ctx->guess && ctx->opts.guess == 2);
     const double* ylast = nullptr;
-    if (hist && (ctx->cap.X || ctx->guess)) {
+    const double* blast = nullptr;
+    if (hist && learn) {
       FRK_TRY(launch_copy(ctx, ctx->buf[B_STAGE], Yi, s));  // B_STAGE is free after R(U_i)
       ylast = ctx->buf[B_STAGE];
+      blast = ctx->bhist[i];
     }
     int mode = ctx->opts.guess;
     if (mode == 2 && !ctx->guess) mode = 1;
-    if (mode == 1 && !hist) mode = 0;
+    if (mode != 0 && !hist) mode = 0;
     if (mode == 0) {
       FRK_TRY(solve(ctx, U, R0, shift, b, Yi, ctx->opts.tol_lin, &st, &info, s));
     } else {
       // nonzero initial guess: the previous step's solution (mode 1) or the
-      // learned one (mode 2); GMRES still stops at tol_lin * ||b||
-      if (mode == 2) FRK_TRY(stage_guess(ctx, b, ylast, yprev, Yi, s));
+      // learned one, kept only when its residual is below the previous-step
+      // guess's (mode 2); GMRES still stops at tol_lin * ||b||
+      if (mode == 2) FRK_TRY(stage_guess(ctx, U, R0, shift, b, blast, ylast, Yi, s));
       const int rc = gmres_impl(ctx, U, R0, shift, b, Yi, ctx->opts.gmres_m, ctx->opts.tol_lin,
                                 ctx->opts.gmres_max_restarts, false, &info, s);
       st.gmres_iters += info.iters;
@@ -320,7 +324,8 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
       if (rc == FR_ERR_NOT_CONVERGED) st.converged = 0;
       else FRK_TRY(rc);
     }
-    FRK_TRY(stage_capture(ctx, b, ylast, yprev, Yi, s));
+    FRK_TRY(stage_capture(ctx, b, blast, ylast, Yi, s));
+    if (learn) FRK_TRY(launch_copy(ctx, ctx->bhist[i], b, s));
   }
 
   // q^{n+1} = q^n + sum m_j Y_j, checked before it overwrites U

@@ -122,6 +122,7 @@ def test_learned_guess_in_row_stages(fr):
     for seed in range(4):
         v = S.Vortex(x0=float(rng.uniform(-2, 2)), y0=float(rng.uniform(-2, 2)), alpha=float(rng.uniform(3, 6)))
         U = torch.from_numpy(v.state(X0, Y0)).cuda()
+        fr.fr_reset_history(ctx)
         for _ in range(4):
             fr.step_row(ctx, 2, 0.05, U)
     n = fr.fr_stage_capture_count(ctx)
@@ -142,6 +143,7 @@ def test_learned_guess_in_row_stages(fr):
     v = S.Vortex(x0=1.3, y0=-0.7, alpha=4.7)
     U0 = v.state(X0, Y0)
     iters, finals = {}, {}
+    c = None
     for mode in (0, 1, 2):
         c = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-8, gmres_max_restarts=60, guess=mode))
         if mode == 2:
@@ -154,8 +156,14 @@ def test_learned_guess_in_row_stages(fr):
             total += st.gmres_iters if k > 0 else 0   # first step has no history
         iters[mode] = total
         finals[mode] = U.cpu().numpy()
+        if mode < 2:
+            c.close()
+    tried, used = fr.fr_guess_stats(c)
+    print("GMRES iterations over steps 2-4 (zero / previous-step / learned):", iters,
+          "learned guess kept in", used, "of", tried, "stage solves")
     assert iters[1] < iters[0]
     assert iters[2] < iters[0]
+    assert iters[2] <= iters[1] + 3
     for mode in (1, 2):
         assert np.linalg.norm(finals[mode] - finals[0]) / np.linalg.norm(finals[0]) < 1e-7
 
@@ -168,4 +176,3 @@ def test_learned_guess_in_row_stages(fr):
         fr.step_row(c, 2, 0.05, U)
         Uo, _ = o_row(prob, ROW[2](), 0.05, Uo, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
     assert np.linalg.norm(U.cpu().numpy() - Uo) / np.linalg.norm(Uo) < 1e-9
-    print("GMRES iterations over steps 2-4 (zero / previous-step / learned):", iters)
