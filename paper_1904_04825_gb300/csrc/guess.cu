@@ -113,7 +113,7 @@ int stage_capture(fr_ctx* ctx, const double* b, const double* bl, const double* 
 
 using namespace frk;
 
-int alloc_guess_buffers(fr_ctx* ctx) {
+int frk::alloc_guess_buffers(fr_ctx* ctx) {
   if (!ctx->gfeat) {
     FRK_CUDA(ctx, cudaMalloc(reinterpret_cast<void**>(&ctx->gfeat), (size_t)ctx->ne * 3 * ctx->nb * sizeof(float)));
     FRK_CUDA(ctx, cudaMalloc(reinterpret_cast<void**>(&ctx->gout), (size_t)ctx->ne * ctx->nb * sizeof(float)));
