@@ -274,6 +274,61 @@ int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
 int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opts, const double* U,
                   const double* R0, const double* z, double shift, double* y, void* stream);
 
+/* ---- batches of independent instances (no counterpart in the paper) ----
+ * Many small problems (uneven meshes and degrees, one fr_opts for all)
+ * advanced with one call per time step.  Each instance keeps its own
+ * context and kernels; they run concurrently on one CUDA stream per
+ * instance, and every restart cycle of the stage GMRES of all instances is
+ * replayed as one CUDA graph: one graph launch and one host wait per cycle
+ * for the whole batch instead of one host round trip per chunk of Arnoldi
+ * steps per instance.  Instances that converged skip the cycle's work on
+ * the device (the GMRES kernels test a device flag). */
+typedef struct fr_batch fr_batch;
+
+/* Create `count` instances: meshes[k] (host edges, copied), degrees[k] in
+ * {2,3,4}, opts shared (NULL = defaults; opts->guess must be 0, else
+ * FR_ERR_UNSUPPORTED).  *out = NULL on failure. */
+int fr_batch_create(int count, const fr_mesh_desc* meshes, const int* degrees, const fr_opts* opts,
+                    fr_batch** out);
+int fr_batch_destroy(fr_batch* batch);
+const char* fr_batch_last_error(const fr_batch* batch);
+/* Context of instance k (owned by the batch; NULL when out of range), for
+ * fr_residual, fr_set_launch_config, fr_autotune and friends. */
+fr_ctx* fr_batch_member(fr_batch* batch, int k);
+
+/* One ROW step (scheme as fr_step_row: 2, 3 or 4) of size dt on every
+ * instance: U[k] (device, ndof(k) doubles) is replaced by its new state;
+ * stats[k] (host, may be NULL) as fr_step_row reports them.  The stage
+ * solves are restarted GMRES(gmres_m) from a zero guess with the stopping
+ * test of fr_gmres_solve (Givens residual <= tol_lin * ||b||), so each
+ * instance takes the same iterations as fr_step_row with guess 0 on its
+ * own; per-instance results agree to round-off (reduction grids may differ).
+ * The cycle graphs are captured on the first call and replayed while the
+ * U pointers, dt, scheme and launch configurations stay the same.  Ordered
+ * after the work queued on `stream` and blocks the host until the step is
+ * done.  Errors: FR_ERR_NOT_CONVERGED when an instance's stage solve
+ * reached gmres_max_restarts (states still advanced), FR_ERR_NONFINITE
+ * (states untouched), FR_ERR_CUDA. */
+int fr_batch_step_row(fr_batch* batch, int scheme, double dt, double* const* U, fr_step_stats* stats,
+                      void* stream);
+
+/* ---- launch configuration (no counterpart in the paper) ----------------
+ * vec_blocks: grid of the streaming Krylov-vector kernels (dots, updates,
+ * norms, block apply), 1..4096 CTAs; tile_variant: element-tile shape of
+ * the Euler residual kernel (0 or 1; results are identical, only the
+ * speed differs).  Reductions are deterministic for a fixed vec_blocks;
+ * another vec_blocks changes their rounding order. */
+int fr_set_launch_config(fr_ctx* ctx, int vec_blocks, int tile_variant);
+int fr_get_launch_config(const fr_ctx* ctx, int* vec_blocks, int* tile_variant);
+/* Time full GMRES(gmres_m) cycles of A = shift I - dR/dU at U (device) for
+ * vec_blocks in {152, 304, 456, 608, 912, 1216} x both tile variants and
+ * keep the fastest; ms_best / ms_default (host, may be NULL) = time of one
+ * cycle with the chosen / the configuration found on entry.  Overwrites the
+ * element blocks (formed at `shift`) and the internal work vectors;
+ * synchronises `stream`. */
+int fr_autotune(fr_ctx* ctx, const double* U, double shift, int reps, double* ms_best, double* ms_default,
+                void* stream);
+
 /* ---- measurement hooks (no counterpart in the paper) -------------------
  * Kernel families for fr_profile_*: */
 enum {

@@ -124,6 +124,15 @@ def _load():
         "fr_stage_features": (I, [P, P, P, P, P, V]),
         "fr_reset_history": (I, [P]),
         "fr_guess_stats": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "fr_batch_create": (I, [I, ctypes.POINTER(fr_mesh_desc), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(fr_opts), ctypes.POINTER(ctypes.c_void_p)]),
+        "fr_batch_destroy": (I, [P]),
+        "fr_batch_last_error": (ctypes.c_char_p, [P]),
+        "fr_batch_member": (P, [P, I]),
+        "fr_batch_step_row": (I, [P, I, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fr_step_stats), V]),
+        "fr_set_launch_config": (I, [P, I, I]),
+        "fr_get_launch_config": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "fr_autotune": (I, [P, P, D, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
         "fr_profile_begin": (I, [P, ctypes.c_uint]),
         "fr_profile_end": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -192,10 +201,21 @@ class Context:
         self.ndof = int(lib.fr_ndof(h))
         self.shape = (self.ne, 4, self.np)
 
+    @classmethod
+    def _view(cls, handle, nx, ny, p, opts):
+        """A non-owning Context over a context that a Batch owns."""
+        c = cls.__new__(cls)
+        c.handle, c.p, c.nx, c.ny, c.opts = handle, p, nx, ny, opts
+        c.ne, c.np = nx * ny, (p + 1) ** 2
+        c.ndof = int(lib.fr_ndof(handle))
+        c.shape = (c.ne, 4, c.np)
+        c._owner = False
+        return c
+
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "_owner", True):
             lib.fr_ctx_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -443,3 +463,79 @@ def fr_guess_stats(ctx: Context):
 
 def ctx_ll():
     return ctypes.c_longlong()
+
+
+def set_launch_config(ctx: Context, vec_blocks: int, tile_variant: int):
+    ctx.check(lib.fr_set_launch_config(ctx.handle, int(vec_blocks), int(tile_variant)))
+
+
+def get_launch_config(ctx: Context):
+    vb, tv = ctypes.c_int(), ctypes.c_int()
+    ctx.check(lib.fr_get_launch_config(ctx.handle, ctypes.byref(vb), ctypes.byref(tv)))
+    return int(vb.value), int(tv.value)
+
+
+def autotune(ctx: Context, U, shift: float, reps: int = 2, stream=None):
+    """Pick the fastest launch configuration for GMRES cycles at U; returns
+    (vec_blocks, tile_variant, ms per cycle chosen, ms per cycle on entry)."""
+    best, dflt = ctypes.c_double(), ctypes.c_double()
+    ctx.check(lib.fr_autotune(ctx.handle, _ptr(U), float(shift), int(reps), ctypes.byref(best),
+                              ctypes.byref(dflt), _stream(stream)))
+    vb, tv = get_launch_config(ctx)
+    return vb, tv, best.value, dflt.value
+
+
+class Batch:
+    """Independent instances (own mesh and degree, shared options) stepped
+    together; the stage GMRES cycles of all of them run as one CUDA graph."""
+
+    def __init__(self, meshes, degrees, opts: fr_opts | None = None):
+        if len(meshes) != len(degrees) or not meshes:
+            raise ValueError("one degree per mesh, at least one instance")
+        self.opts = opts if opts is not None else default_opts()
+        self._edges = []
+        descs = (fr_mesh_desc * len(meshes))()
+        for k, (xe, ye) in enumerate(meshes):
+            xe = np.ascontiguousarray(xe, dtype=np.float64)
+            ye = np.ascontiguousarray(ye, dtype=np.float64)
+            self._edges.append((xe, ye))
+            descs[k] = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
+                                    xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+        degs = (ctypes.c_int * len(degrees))(*[int(d) for d in degrees])
+        h = ctypes.c_void_p()
+        rc = lib.fr_batch_create(len(meshes), descs, degs, ctypes.byref(self.opts), ctypes.byref(h))
+        if rc != FR_OK:
+            raise FrError(rc, "fr_batch_create failed")
+        self.handle = h
+        self.members = [Context._view(lib.fr_batch_member(h, k), len(xe) - 1, len(ye) - 1, int(d), self.opts)
+                        for k, ((xe, ye), d) in enumerate(zip(self._edges, degrees))]
+
+    def __len__(self):
+        return len(self.members)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.handle = None
+            lib.fr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step_row(self, scheme: int, dt: float, Us, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+        if len(Us) != len(self.members):
+            raise ValueError("one state per instance")
+        for U, m in zip(Us, self.members):
+            if U.numel() != m.ndof:
+                raise ValueError("state shape does not match its instance")
+        ptrs = (ctypes.c_void_p * len(Us))(*[_ptr(U).value for U in Us])
+        st = (fr_step_stats * len(Us))()
+        rc = lib.fr_batch_step_row(self.handle, int(scheme), float(dt), ptrs, st, _stream(stream))
+        if rc != FR_OK and rc not in allow:
+            raise FrError(rc, lib.fr_batch_last_error(self.handle).decode())
+        return [_stats(st[k], rc) for k in range(len(Us))]

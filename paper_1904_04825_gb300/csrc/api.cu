@@ -159,6 +159,7 @@ void prof_harvest(fr_ctx* c, int f) {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_static_error(const char* msg) {
   std::strncpy(g_static_err, msg, sizeof(g_static_err) - 1);

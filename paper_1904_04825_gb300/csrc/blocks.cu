@@ -502,9 +502,9 @@ int solupdate_nb(fr_ctx* ctx, double* x, cudaStream_t s) {
   }
 }
 
-unsigned vec_grid(long long n) {
+unsigned vec_grid(const fr_ctx* ctx, long long n) {
   long long g = (n + kThreads - 1) / kThreads;
-  if (g > kVecBlocks) g = kVecBlocks;
+  if (g > ctx->vec_blocks) g = ctx->vec_blocks;
   return (unsigned)(g < 1 ? 1 : g);
 }
 
@@ -564,7 +564,7 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
                        const int* done, cudaStream_t s, bool with_eps) {
   if (!ctx->opts.precond) {
-    { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
+    { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx, ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
                                                           done, eps_args(ctx, with_eps)); }
     FRK_LAUNCHED(ctx);
     return FR_OK;
@@ -579,7 +579,7 @@ int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, d
 
 int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
   if (!ctx->opts.precond) {
-    { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate_plain<<<vec_grid(ctx->ndof), kThreads, 0, s>>>(ctx->V, ctx->ndof, ctx->gd.y,
+    { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate_plain<<<vec_grid(ctx, ctx->ndof), kThreads, 0, s>>>(ctx->V, ctx->ndof, ctx->gd.y,
                                                                ctx->gd.k, x, ctx->ndof); }
     FRK_LAUNCHED(ctx);
     return FR_OK;

@@ -14,7 +14,7 @@ namespace frk {
 constexpr int kMaxN = 5;          // p <= 4
 constexpr int kThreads = 256;     // default block size of the vector kernels
 constexpr int kMaxVec = 32;       // largest Krylov basis slice handled per call (m_max + 1)
-constexpr int kVecBlocks = 456;   // 3 x 152 SMs: grid of the streaming vector kernels
+constexpr int kVecBlocks = 456;   // default grid of the streaming vector kernels (3 x 152 SMs)
 constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
 
 // 1D tables of Sec. 3 on Gauss-Legendre points, passed to kernels by value.
@@ -60,7 +60,7 @@ struct GmresDev {
 };
 
 // Device scalars (sums of squares) used by the FD step and GMRES.
-enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_GR1, S_GR2, S_COUNT };
+enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_GR1, S_GR2, S_ST0, S_ST1, S_ST2, S_ST3, S_COUNT };  // S_ST*: one GMRES cycle status
 
 // FD step eps = eps_rel (1 + ||U||) / ||z|| (or eps_fixed), written once per
 // product as (eps, 1/eps) by the kernel that finishes ||z||^2.
@@ -127,6 +127,8 @@ struct fr_ctx {
   double* z = nullptr;       // preconditioned basis vector
   double* buf[16] = {};      // stepper buffers, ndof each
   double* scal = nullptr;    // frk::S_COUNT device scalars
+  int vec_blocks = frk::kVecBlocks;  // grid of the streaming vector kernels (autotuned)
+  int tile_variant = 0;      // element-tile shape of the Euler residual kernel (autotuned)
   frk::Reduce red{};
   frk::GmresDev gd{};
   int* h_stat = nullptr;     // pinned host mirror: done, k
@@ -168,6 +170,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // Launch accounting: every kernel launch goes through prof_begin / prof_end.
 void count_launch();
+void count_launches(long long n);
 void prof_begin(fr_ctx* ctx, int family, cudaStream_t s);
 void prof_end(fr_ctx* ctx, int family, cudaStream_t s);
 
@@ -210,6 +213,8 @@ int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s);
 int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
                double* x, int m, double rtol, int max_restarts, bool x_is_zero,
                fr_gmres_info* info, cudaStream_t s);
+int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                        double* x, int m, double rtol, double* status, cudaStream_t s);
 // tables.cu
 void build_tables(int p, Tables* t);
 // ns.cu (viscous path): mode 0 R, 1 A z, 2 b - A z; block formation + inversion

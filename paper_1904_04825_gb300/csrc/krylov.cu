@@ -14,9 +14,9 @@
 namespace frk {
 namespace {
 
-unsigned vgrid(long long n) {
+unsigned vgrid(const fr_ctx* ctx, long long n) {
   long long g = (n + kThreads - 1) / kThreads;
-  if (g > kVecBlocks) g = kVecBlocks;
+  if (g > ctx->vec_blocks) g = ctx->vec_blocks;
   return (unsigned)(g < 1 ? 1 : g);
 }
 
@@ -253,6 +253,15 @@ __global__ void k_backsub(GmresDev gd) {
   }
 }
 
+// cycle status for the host: [k, |g_k|, rtol ||b||, ||b||]
+__global__ void k_status(GmresDev gd, const double* nb2, double* out) {
+  if (threadIdx.x != 0) return;
+  out[0] = (double)*gd.k;
+  out[1] = *gd.res;
+  out[2] = *gd.target;
+  out[3] = sqrt(*nb2);
+}
+
 __global__ void k_copy(double* dst, const double* src, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -273,7 +282,7 @@ EpsArgs eps_args(fr_ctx* ctx, bool on) {
 }
 
 int launch_sumsq(fr_ctx* ctx, const double* x, double* out, cudaStream_t s, bool with_eps) {
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_sumsq<<<vgrid(ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red, eps_args(ctx, with_eps)); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_sumsq<<<vgrid(ctx, ctx->ndof), kThreads, 0, s>>>(x, ctx->ndof, out, ctx->red, eps_args(ctx, with_eps)); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -287,19 +296,58 @@ int launch_lincomb(fr_ctx* ctx, double* out, int nterms, const double* const* xs
     lc.x[t] = xs[t];
     lc.c[t] = coefs[t];
   }
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_lincomb<<<vgrid(ctx->ndof), kThreads, 0, s>>>(out, ctx->ndof, lc, sumsq, ctx->red); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_lincomb<<<vgrid(ctx, ctx->ndof), kThreads, 0, s>>>(out, ctx->ndof, lc, sumsq, ctx->red); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 int launch_copy(fr_ctx* ctx, double* dst, const double* src, cudaStream_t s) {
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_copy<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, src, ctx->ndof); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_copy<<<vgrid(ctx, ctx->ndof), kThreads, 0, s>>>(dst, src, ctx->ndof); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s) {
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_fill<<<vgrid(ctx->ndof), kThreads, 0, s>>>(dst, v, ctx->ndof); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_fill<<<vgrid(ctx, ctx->ndof), kThreads, 0, s>>>(dst, v, ctx->ndof); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+// One whole GMRES cycle enqueued without any host synchronisation (for CUDA
+// graph capture): r = b - A x (exactly b for x = 0), m Arnoldi iterations
+// that stop on the device, the solution update, and the status
+// [k, |g_k|, target, ||b||] written to status (device, 4 doubles).
+int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                        double* x, int m, double rtol, double* status, cudaStream_t s) {
+  const long long n = ctx->ndof;
+  double* sc = ctx->scal;
+  GmresDev& gd = ctx->gd;
+  double* V = ctx->V;
+  FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
+  FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
+  FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
+  FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, nullptr, s));
+  FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m); }
+  FRK_LAUNCHED(ctx);
+  for (int j = 0; j < m; ++j) {
+    double* vj = V + (size_t)j * n;
+    double* w = V + (size_t)(j + 1) * n;
+    FRK_TRY(launch_block_apply(ctx, vj, gd.invh + j, ctx->z, sc + S_NZ2, gd.done, s, true));
+    FRK_TRY(launch_residual(ctx, 1, U, ctx->z, R0, nullptr, w, shift, sc + S_EPS, gd.done, s));
+    const Reorth none{nullptr, 0.0, nullptr, nullptr};
+    const Reorth first{gd.h1 + (j + 1), ctx->opts.reorth_eta * ctx->opts.reorth_eta, gd.rflag + j, gd.h2};
+    { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(ctx, n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, 1, ctx->red, gd.done, nullptr); }
+    { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(ctx, n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, sc + S_NW2, ctx->red, gd.done, nullptr, first); }
+    { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(ctx, n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, 0, ctx->red, gd.done, gd.rflag + j); }
+    { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(ctx, n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done, gd.rflag + j, none); }
+    { ProfScope ps_(ctx, FR_KF_OTHER, s); k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2); }
+    FRK_LAUNCHED(ctx);
+  }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
+  FRK_LAUNCHED(ctx);
+  FRK_TRY(launch_solution_update(ctx, x, s));
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -360,10 +408,10 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
         // first shrank ||w|| below reorth_eta ||w|| (decided on the device)
         const Reorth none{nullptr, 0.0, nullptr, nullptr};
         const Reorth first{gd.h1 + (j + 1), ctx->opts.reorth_eta * ctx->opts.reorth_eta, gd.rflag + j, gd.h2};
-        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, 1, ctx->red, gd.done, nullptr); }
-        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, sc + S_NW2, ctx->red, gd.done, nullptr, first); }
-        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, 0, ctx->red, gd.done, gd.rflag + j); }
-        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done, gd.rflag + j, none); }
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(ctx, n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h1, 1, ctx->red, gd.done, nullptr); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(ctx, n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h1, n, sc + S_NW2, ctx->red, gd.done, nullptr, first); }
+        { ProfScope ps_(ctx, FR_KF_DOTS, s); k_dots<<<vgrid(ctx, n), kThreads, 0, s>>>(V, n, j + 1, w, n, gd.h2, 0, ctx->red, gd.done, gd.rflag + j); }
+        { ProfScope ps_(ctx, FR_KF_UPDATE, s); k_update<<<vgrid(ctx, n), kThreads, 0, s>>>(w, V, n, j + 1, gd.h2, n, sc + S_NW2, ctx->red, gd.done, gd.rflag + j, none); }
         { ProfScope ps_(ctx, FR_KF_OTHER, s); k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2); }
         FRK_LAUNCHED(ctx);
       }

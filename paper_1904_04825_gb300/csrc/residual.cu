@@ -58,16 +58,20 @@ __device__ __forceinline__ double trace_global(const double* __restrict__ U,
   return s;
 }
 
-// Element tile handled by one CTA (TX x TY elements, one thread per point).
-template <int P> struct Tile;
-template <> struct Tile<2> { static constexpr int TX = 5, TY = 5; };
-template <> struct Tile<3> { static constexpr int TX = 4, TY = 4; };
-template <> struct Tile<4> { static constexpr int TX = 3, TY = 3; };
+// Element tile handled by one CTA (TX x TY elements, one thread per point);
+// two shapes per degree, picked at run time by the autotuner.
+template <int P, int V> struct Tile;
+template <> struct Tile<2, 0> { static constexpr int TX = 5, TY = 5; };
+template <> struct Tile<2, 1> { static constexpr int TX = 7, TY = 4; };
+template <> struct Tile<3, 0> { static constexpr int TX = 4, TY = 4; };
+template <> struct Tile<3, 1> { static constexpr int TX = 8, TY = 2; };
+template <> struct Tile<4, 0> { static constexpr int TX = 3, TY = 3; };
+template <> struct Tile<4, 1> { static constexpr int TX = 5, TY = 2; };
 
-template <int P, int MODE>
+template <int P, int MODE, int TV>
 __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   constexpr int N = P + 1, NP = N * N;
-  constexpr int TX = Tile<P>::TX, TY = Tile<P>::TY, NE = TX * TY;
+  constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
   constexpr int NXF = (TX + 1) * TY * N;  // points on the tile's x-faces (normal +x)
   constexpr int NYF = (TY + 1) * TX * N;  // points on the tile's y-faces (normal +y)
   constexpr bool PERTURB = MODE > 0;
@@ -218,9 +222,9 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   }
 }
 
-template <int P>
-int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
-  constexpr int NP = (P + 1) * (P + 1), TX = Tile<P>::TX, TY = Tile<P>::TY;
+template <int P, int TV>
+int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
+  constexpr int NP = (P + 1) * (P + 1), TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY;
   const long long grid = (long long)((ctx->nx + TX - 1) / TX) * ((ctx->ny + TY - 1) / TY);
   const dim3 blk(TX * TY * NP);
   // algorithmic work: R reads U and writes R (16 B/DOF); A z also reads z and
@@ -230,11 +234,16 @@ int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   const bool in_cycle = a.done != nullptr;
   const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
   const double wf = in_cycle ? 0.0 : (mode == 0 ? fl : fl + 6.0 * nd);
-  if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2><<<(unsigned)grid, blk, 0, s>>>(a); }
+  if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+template <int P>
+int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
+  return ctx->tile_variant == 1 ? launch_pv<P, 1>(ctx, mode, a, s) : launch_pv<P, 0>(ctx, mode, a, s);
 }
 
 }  // namespace

@@ -3,6 +3,9 @@
 // on the caller's stream; the host reads back only the scalars the method
 // branches on (GMRES cycle status, ||F|| of each pseudo step).
 #include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -247,6 +250,58 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
   return FR_OK;
 }
 
+
+// ROW prologue: R0 = R(q^n) and the element blocks at shift 1/(gamma dt).
+int row_prologue(fr_ctx* ctx, const RowTab& t, double dt, const double* U, fr_step_stats* st,
+                 cudaStream_t s) {
+  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, ctx->buf[B_R0], 0.0, nullptr, nullptr, s));
+  st->residual_evals += 1;
+  if (ctx->opts.precond) {
+    FRK_TRY(launch_block_factor(ctx, U, 1.0 / (t.gamma * dt), s));
+    ctx->blocks_valid = 1;
+  }
+  return FR_OK;
+}
+
+// Right-hand side of ROW stage i: R(q^n + sum a_ij Y_j) + (1/dt) sum c_ij Y_j.
+int row_stage_rhs(fr_ctx* ctx, const RowTab& t, int i, double dt, const double* U, fr_step_stats* st,
+                  const double** b_out, cudaStream_t s) {
+  const double* Ri = ctx->buf[B_R0];
+  bool any_a = false;
+  for (int j = 0; j < i; ++j) any_a |= t.a[i][j] != 0.0;
+  if (i > 0 && any_a) {
+    const double* xs[7];
+    double cs[7];
+    xs[0] = U; cs[0] = 1.0;
+    for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.a[i][j]; }
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_STAGE], i + 1, xs, cs, nullptr, s));
+    FRK_TRY(launch_residual(ctx, 0, ctx->buf[B_STAGE], nullptr, nullptr, nullptr, ctx->buf[B_RSTAGE],
+                            0.0, nullptr, nullptr, s));
+    st->residual_evals += 1;
+    Ri = ctx->buf[B_RSTAGE];
+  }
+  const double* b = Ri;
+  if (i > 0) {
+    const double* xs[7];
+    double cs[7];
+    xs[0] = Ri; cs[0] = 1.0;
+    for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.c[i][j] / dt; }
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_RHS], i + 1, xs, cs, nullptr, s));
+    b = ctx->buf[B_RHS];
+  }
+  *b_out = b;
+  return FR_OK;
+}
+
+// q^{n+1} = q^n + sum m_j Y_j into B_NEW, its squared norm into S_NX2.
+int row_combine(fr_ctx* ctx, const RowTab& t, const double* U, cudaStream_t s) {
+  const double* xs[7];
+  double cs[7];
+  xs[0] = U; cs[0] = 1.0;
+  for (int j = 0; j < t.s; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.m[j]; }
+  return launch_lincomb(ctx, ctx->buf[B_NEW], t.s + 1, xs, cs, ctx->scal + S_NX2, s);
+}
+
 }  // namespace
 }  // namespace frk
 
@@ -265,37 +320,11 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
   ctx->hist_row = 0;
   const double shift = 1.0 / (t.gamma * dt);
   double* R0 = ctx->buf[B_R0];
-  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, R0, 0.0, nullptr, nullptr, s));
-  st.residual_evals += 1;
-  if (ctx->opts.precond) {
-    FRK_TRY(launch_block_factor(ctx, U, shift, s));
-    ctx->blocks_valid = 1;
-  }
+  FRK_TRY(row_prologue(ctx, t, dt, U, &st, s));
   for (int i = 0; i < t.s; ++i) {
     double* Yi = ctx->buf[B_Y0 + i];
-    const double* Ri = R0;
-    bool any_a = false;
-    for (int j = 0; j < i; ++j) any_a |= t.a[i][j] != 0.0;
-    if (i > 0 && any_a) {
-      const double* xs[7];
-      double cs[7];
-      xs[0] = U; cs[0] = 1.0;
-      for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.a[i][j]; }
-      FRK_TRY(launch_lincomb(ctx, ctx->buf[B_STAGE], i + 1, xs, cs, nullptr, s));
-      FRK_TRY(launch_residual(ctx, 0, ctx->buf[B_STAGE], nullptr, nullptr, nullptr, ctx->buf[B_RSTAGE],
-                              0.0, nullptr, nullptr, s));
-      st.residual_evals += 1;
-      Ri = ctx->buf[B_RSTAGE];
-    }
-    const double* b = Ri;
-    if (i > 0) {
-      const double* xs[7];
-      double cs[7];
-      xs[0] = Ri; cs[0] = 1.0;
-      for (int j = 0; j < i; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.c[i][j] / dt; }
-      FRK_TRY(launch_lincomb(ctx, ctx->buf[B_RHS], i + 1, xs, cs, nullptr, s));
-      b = ctx->buf[B_RHS];
-    }
+    const double* b = nullptr;
+    FRK_TRY(row_stage_rhs(ctx, t, i, dt, U, &st, &b, s));
     fr_gmres_info info{};
     // this stage's solution and right-hand side at the previous step (still in
     // place when the last step was a ROW step of this scheme on this state)
@@ -329,11 +358,7 @@ extern "C" int step_row(fr_ctx* ctx, int scheme, double dt, double* U, fr_step_s
   }
 
   // q^{n+1} = q^n + sum m_j Y_j, checked before it overwrites U
-  const double* xs[7];
-  double cs[7];
-  xs[0] = U; cs[0] = 1.0;
-  for (int j = 0; j < t.s; ++j) { xs[j + 1] = ctx->buf[B_Y0 + j]; cs[j + 1] = t.m[j]; }
-  FRK_TRY(launch_lincomb(ctx, ctx->buf[B_NEW], t.s + 1, xs, cs, ctx->scal + S_NX2, s));
+  FRK_TRY(row_combine(ctx, t, U, s));
   double nn;
   FRK_TRY(read_scalar(ctx, ctx->scal + S_NX2, &nn, s));
   if (stats) *stats = st;
@@ -425,5 +450,364 @@ extern "C" int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int 
   FRK_TRY(launch_copy(ctx, U, q, s));
   FRK_CUDA(ctx, cudaStreamSynchronize(s));
   if (rc != FR_OK || !st.converged) return set_error(ctx, FR_ERR_NOT_CONVERGED, "step_bdf2: PTC did not converge");
+  return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent instances (uneven meshes and degrees) advanced
+// together: the per-instance kernels of each phase run concurrently on one
+// stream per instance, and every GMRES cycle of all instances is one CUDA
+// graph launch (captured once per stage, replayed every step).
+
+struct fr_batch {
+  std::vector<fr_ctx*> m;
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> st;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  double* status_dev = nullptr;   // [count][4] GMRES cycle status
+  double* status_host = nullptr;  // pinned mirror
+  cudaGraphExec_t exec[6] = {};
+  long long nodes[6] = {};
+  std::vector<const double*> keyU;
+  std::vector<int> keyCfg;  // vec_blocks, tile_variant of every instance
+  double key_dt = 0.0;
+  int key_scheme = 0;
+  char err[256] = {0};
+};
+
+namespace frk {
+namespace {
+
+int batch_err(fr_batch* B, int code, const char* msg) {
+  if (B) {
+    std::strncpy(B->err, msg, sizeof(B->err) - 1);
+    B->err[sizeof(B->err) - 1] = 0;
+  }
+  return code;
+}
+
+#define BATCH_CUDA(B, call)                                                        \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return batch_err((B), FR_ERR_CUDA, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define BATCH_TRY(B, k, expr)                                                       \
+  do {                                                                             \
+    int r_ = (expr);                                                               \
+    if (r_ != FR_OK) return batch_err((B), r_, fr_last_error((B)->m[k]));          \
+  } while (0)
+
+void free_batch(fr_batch* B) {
+  if (!B) return;
+  for (auto& e : B->exec)
+    if (e) cudaGraphExecDestroy(e);
+  for (fr_ctx* c : B->m) fr_ctx_destroy(c);
+  for (cudaStream_t s : B->st) cudaStreamDestroy(s);
+  for (cudaEvent_t e : B->join) cudaEventDestroy(e);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->main) cudaStreamDestroy(B->main);
+  cudaFree(B->status_dev);
+  cudaFreeHost(B->status_host);
+  delete B;
+}
+
+// fork every instance stream off the main stream / join them back
+int fork_all(fr_batch* B) {
+  BATCH_CUDA(B, cudaEventRecord(B->fork, B->main));
+  for (cudaStream_t s : B->st) BATCH_CUDA(B, cudaStreamWaitEvent(s, B->fork, 0));
+  return FR_OK;
+}
+int join_all(fr_batch* B) {
+  for (size_t k = 0; k < B->st.size(); ++k) {
+    BATCH_CUDA(B, cudaEventRecord(B->join[k], B->st[k]));
+    BATCH_CUDA(B, cudaStreamWaitEvent(B->main, B->join[k], 0));
+  }
+  return FR_OK;
+}
+
+// capture the graph of one GMRES cycle of stage i for all instances
+int capture_cycle(fr_batch* B, int i, const RowTab& t, double dt, double* const* U) {
+  const double shift = 1.0 / (t.gamma * dt);
+  cudaGraph_t g = nullptr;
+  // launches enqueued while capturing run only when the graph is replayed;
+  // per-family event timing does not apply inside a graph
+  const long long launches0 = fr_kernel_launches();
+  std::vector<unsigned> masks(B->m.size());
+  for (size_t k = 0; k < B->m.size(); ++k) {
+    masks[k] = B->m[k]->prof.mask;
+    B->m[k]->prof.mask = 0;
+  }
+  BATCH_CUDA(B, cudaStreamBeginCapture(B->main, cudaStreamCaptureModeRelaxed));
+  int rc = fork_all(B);
+  for (size_t k = 0; k < B->m.size() && rc == FR_OK; ++k) {
+    fr_ctx* c = B->m[k];
+    const double* b = (i == 0) ? c->buf[B_R0] : (i > 0 ? c->buf[B_RHS] : nullptr);
+    rc = gmres_cycle_enqueue(c, U[k], c->buf[B_R0], shift, b, c->buf[B_Y0 + i], c->opts.gmres_m,
+                             c->opts.tol_lin, B->status_dev + 4 * k, B->st[k]);
+    if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
+  }
+  if (rc == FR_OK) rc = join_all(B);
+  if (rc == FR_OK && cudaMemcpyAsync(B->status_host, B->status_dev, B->m.size() * 4 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, B->main) != cudaSuccess)
+    rc = batch_err(B, FR_ERR_CUDA, "status copy capture failed");
+  const cudaError_t ee = cudaStreamEndCapture(B->main, &g);
+  for (size_t k = 0; k < B->m.size(); ++k) B->m[k]->prof.mask = masks[k];
+  count_launches(launches0 - fr_kernel_launches());
+  if (rc != FR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  BATCH_CUDA(B, ee);
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  long long kernels = 0;
+  if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+    for (size_t q = 0; q < nn; ++q) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
+  if (B->exec[i]) cudaGraphExecDestroy(B->exec[i]);
+  B->exec[i] = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&B->exec[i], g, 0);
+  cudaGraphDestroy(g);
+  BATCH_CUDA(B, ei);
+  B->nodes[i] = kernels;
+  return FR_OK;
+}
+
+}  // namespace
+}  // namespace frk
+
+extern "C" int fr_batch_create(int count, const fr_mesh_desc* meshes, const int* degrees, const fr_opts* opts,
+                               fr_batch** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !meshes || !degrees) return FR_ERR_INVALID_ARG;
+  if (opts && opts->guess != 0) return FR_ERR_UNSUPPORTED;  // batch stage solves start from zero
+  fr_batch* B = new (std::nothrow) fr_batch();
+  if (!B) return FR_ERR_CUDA;
+  int rc = FR_OK;
+  for (int k = 0; k < count && rc == FR_OK; ++k) {
+    fr_ctx* c = nullptr;
+    rc = fr_ctx_create(&meshes[k], degrees[k], opts, &c);
+    if (rc == FR_OK) B->m.push_back(c);
+  }
+  if (rc == FR_OK && cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking) != cudaSuccess) rc = FR_ERR_CUDA;
+  if (rc == FR_OK && cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) rc = FR_ERR_CUDA;
+  for (int k = 0; k < count && rc == FR_OK; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FR_ERR_CUDA;
+    else B->st.push_back(s);
+    if (rc == FR_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = FR_ERR_CUDA;
+    else if (rc == FR_OK) B->join.push_back(e);
+  }
+  if (rc == FR_OK && cudaMalloc(&B->status_dev, (size_t)count * 4 * sizeof(double)) != cudaSuccess) rc = FR_ERR_CUDA;
+  if (rc == FR_OK && cudaMallocHost(&B->status_host, (size_t)count * 4 * sizeof(double)) != cudaSuccess) rc = FR_ERR_CUDA;
+  if (rc != FR_OK) {
+    free_batch(B);
+    return rc;
+  }
+  *out = B;
+  return FR_OK;
+}
+
+extern "C" int fr_batch_destroy(fr_batch* B) {
+  free_batch(B);
+  return FR_OK;
+}
+
+extern "C" const char* fr_batch_last_error(const fr_batch* B) { return B ? B->err : "invalid batch"; }
+
+extern "C" fr_ctx* fr_batch_member(fr_batch* B, int k) {
+  if (!B || k < 0 || k >= (int)B->m.size()) return nullptr;
+  return B->m[k];
+}
+
+extern "C" int fr_batch_step_row(fr_batch* B, int scheme, double dt, double* const* U, fr_step_stats* stats,
+                                 void* stream) {
+  if (!B || !U) return FR_ERR_INVALID_ARG;
+  if (scheme < 2 || scheme > 4 || !(dt > 0.0)) return batch_err(B, FR_ERR_INVALID_ARG, "bad scheme or dt");
+  const int K = (int)B->m.size();
+  for (int k = 0; k < K; ++k)
+    if (!U[k]) return batch_err(B, FR_ERR_INVALID_ARG, "null state");
+  const RowTab t = row_tableau(scheme);
+  std::vector<fr_step_stats> st(K);
+  for (auto& s : st) s.converged = 1;
+  // order the batch after the caller's stream
+  cudaStream_t caller = as_stream(stream);
+  BATCH_CUDA(B, cudaEventRecord(B->fork, caller));
+  BATCH_CUDA(B, cudaStreamWaitEvent(B->main, B->fork, 0));
+  // (re)capture the cycle graphs when the states, dt or scheme changed
+  std::vector<int> cfg(2 * K);
+  for (int k = 0; k < K; ++k) {
+    cfg[2 * k] = B->m[k]->vec_blocks;
+    cfg[2 * k + 1] = B->m[k]->tile_variant;
+  }
+  bool same = B->key_scheme == scheme && B->key_dt == dt && (int)B->keyU.size() == K && B->keyCfg == cfg;
+  for (int k = 0; same && k < K; ++k) same = B->keyU[k] == U[k];
+  if (!same) {
+    B->keyCfg = cfg;
+    for (auto& e : B->exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    B->keyU.assign(U, U + K);
+    B->key_dt = dt;
+    B->key_scheme = scheme;
+  }
+  FRK_TRY(fork_all(B));
+  for (int k = 0; k < K; ++k) {
+    B->m[k]->hist_row = 0;
+    BATCH_TRY(B, k, row_prologue(B->m[k], t, dt, U[k], &st[k], B->st[k]));
+  }
+  for (int i = 0; i < t.s; ++i) {
+    for (int k = 0; k < K; ++k) {
+      const double* b = nullptr;
+      BATCH_TRY(B, k, row_stage_rhs(B->m[k], t, i, dt, U[k], &st[k], &b, B->st[k]));
+      BATCH_TRY(B, k, launch_fill(B->m[k], B->m[k]->buf[B_Y0 + i], 0.0, B->st[k]));
+    }
+    FRK_TRY(join_all(B));
+    if (!B->exec[i]) FRK_TRY(capture_cycle(B, i, t, dt, U));
+    std::vector<int> conv(K, 0), cycles(K, 0);
+    const int max_restarts = B->m[0]->opts.gmres_max_restarts;
+    for (int cyc = 0; cyc <= max_restarts; ++cyc) {
+      BATCH_CUDA(B, cudaGraphLaunch(B->exec[i], B->main));
+      count_launches(B->nodes[i]);
+      BATCH_CUDA(B, cudaStreamSynchronize(B->main));
+      bool all = true;
+      for (int k = 0; k < K; ++k) {
+        const double* q = B->status_host + 4 * k;
+        if (!std::isfinite(q[1])) return batch_err(B, FR_ERR_NONFINITE, "batch GMRES residual not finite");
+        if (conv[k]) continue;
+        st[k].gmres_iters += (int)q[0];
+        if (q[0] > 0) cycles[k] += 1;
+        if (q[1] <= q[2]) conv[k] = 1;
+        all = all && conv[k];
+      }
+      if (all) break;
+    }
+    for (int k = 0; k < K; ++k) {
+      st[k].gmres_calls += 1;
+      if (!conv[k]) st[k].converged = 0;
+    }
+    FRK_TRY(fork_all(B));
+  }
+  for (int k = 0; k < K; ++k) BATCH_TRY(B, k, row_combine(B->m[k], t, U[k], B->st[k]));
+  FRK_TRY(join_all(B));
+  for (int k = 0; k < K; ++k)
+    BATCH_CUDA(B, cudaMemcpyAsync(B->status_host + 4 * k, B->m[k]->scal + S_NX2, sizeof(double),
+                                  cudaMemcpyDeviceToHost, B->main));
+  BATCH_CUDA(B, cudaStreamSynchronize(B->main));
+  for (int k = 0; k < K; ++k)
+    if (!std::isfinite(B->status_host[4 * k]))
+      return batch_err(B, FR_ERR_NONFINITE, "batch: a new state is not finite");
+  FRK_TRY(fork_all(B));
+  for (int k = 0; k < K; ++k) BATCH_TRY(B, k, launch_copy(B->m[k], U[k], B->m[k]->buf[B_NEW], B->st[k]));
+  FRK_TRY(join_all(B));
+  BATCH_CUDA(B, cudaEventRecord(B->fork, B->main));
+  BATCH_CUDA(B, cudaStreamWaitEvent(caller, B->fork, 0));
+  BATCH_CUDA(B, cudaStreamSynchronize(B->main));
+  bool ok = true;
+  for (int k = 0; k < K; ++k) {
+    if (stats) stats[k] = st[k];
+    ok = ok && st[k].converged;
+  }
+  if (!ok) return batch_err(B, FR_ERR_NOT_CONVERGED, "batch: a stage solve did not converge");
+  return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration: grid of the streaming vector kernels and the element
+// tile of the Euler residual kernel, set by hand or measured.
+
+extern "C" int fr_set_launch_config(fr_ctx* ctx, int vec_blocks, int tile_variant) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (vec_blocks < 1 || vec_blocks > kRedBlocks || tile_variant < 0 || tile_variant > 1)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "launch config: vec_blocks in [1, 4096], tile_variant 0 or 1");
+  ctx->vec_blocks = vec_blocks;
+  ctx->tile_variant = tile_variant;
+  return FR_OK;
+}
+
+extern "C" int fr_get_launch_config(const fr_ctx* ctx, int* vec_blocks, int* tile_variant) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (vec_blocks) *vec_blocks = ctx->vec_blocks;
+  if (tile_variant) *tile_variant = ctx->tile_variant;
+  return FR_OK;
+}
+
+namespace frk {
+namespace {
+// candidate grids: 1..8 CTAs per SM on the 152 SMs
+constexpr int kTuneGrids[] = {152, 304, 456, 608, 912, 1216};
+
+int time_cycles(fr_ctx* ctx, const double* U, double shift, int reps, cudaEvent_t e0, cudaEvent_t e1,
+                float* ms, cudaStream_t s) {
+  double* b = ctx->buf[B_R0];
+  double* x = ctx->buf[B_Y0];
+  const int m = ctx->opts.gmres_m;
+  // one warm-up cycle, then `reps` timed ones, each from x = 0
+  for (int r = 0; r <= reps; ++r) {
+    FRK_TRY(launch_fill(ctx, x, 0.0, s));
+    if (r == 1) FRK_CUDA(ctx, cudaEventRecord(e0, s));
+    FRK_TRY(gmres_cycle_enqueue(ctx, U, b, shift, b, x, m, 0.0, ctx->scal + S_ST0, s));
+  }
+  FRK_CUDA(ctx, cudaEventRecord(e1, s));
+  FRK_CUDA(ctx, cudaEventSynchronize(e1));
+  FRK_CUDA(ctx, cudaEventElapsedTime(ms, e0, e1));
+  *ms /= (float)reps;
+  return FR_OK;
+}
+}  // namespace
+}  // namespace frk
+
+extern "C" int fr_autotune(fr_ctx* ctx, const double* U, double shift, int reps, double* ms_best,
+                           double* ms_default, void* stream) {
+  if (!ctx || !U) return FR_ERR_INVALID_ARG;
+  if (reps < 1) reps = 1;
+  if (!(shift >= 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "autotune: shift must be >= 0");
+  cudaStream_t s = as_stream(stream);
+  const unsigned mask = ctx->prof.mask;
+  ctx->prof.mask = 0;
+  const int vb0 = ctx->vec_blocks, tv0 = ctx->tile_variant;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = FR_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = set_error(ctx, FR_ERR_CUDA, "autotune: event creation failed");
+  // the cycle's operator: R(U) and the element blocks at this shift
+  if (rc == FR_OK)
+    rc = launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, ctx->buf[B_R0], 0.0, nullptr, nullptr, s);
+  if (rc == FR_OK && ctx->opts.precond) {
+    rc = launch_block_factor(ctx, U, shift, s);
+    if (rc == FR_OK) ctx->blocks_valid = 1;
+  }
+  float best = 0.f, dflt = 0.f;
+  int best_vb = vb0, best_tv = tv0;
+  if (rc == FR_OK) rc = time_cycles(ctx, U, shift, reps, e0, e1, &dflt, s);
+  best = dflt;
+  const int ntv = ctx->viscous ? 1 : 2;  // the viscous residual has one tile shape
+  for (int tv = 0; tv < ntv && rc == FR_OK; ++tv)
+    for (int vb : kTuneGrids) {
+      ctx->vec_blocks = vb;
+      ctx->tile_variant = tv;
+      float ms = 0.f;
+      rc = time_cycles(ctx, U, shift, reps, e0, e1, &ms, s);
+      if (rc != FR_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_vb = vb;
+        best_tv = tv;
+      }
+    }
+  ctx->vec_blocks = rc == FR_OK ? best_vb : vb0;
+  ctx->tile_variant = rc == FR_OK ? best_tv : tv0;
+  ctx->prof.mask = mask;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != FR_OK) return rc;
+  if (ms_best) *ms_best = best;
+  if (ms_default) *ms_default = dflt;
   return FR_OK;
 }
