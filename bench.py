@@ -466,6 +466,152 @@ def kernel_arm(args):
     return 0
 
 
+BATCH_MESHES = (16, 24, 32, 48, 64)
+BATCH_DEGREES = (2, 3, 4)
+
+
+def batch_arm(args):
+    """Many small independent problems: 64 vortex instances of uneven size
+    (meshes 16^2..64^2 of [-5,5]^2, p = 2, 3, 4, vortex centres spread over
+    the box), one ROW step of dt for all per call.  Timed twice on the same
+    instances and states: through the batch API (graph-replayed GMRES cycles
+    of all instances) and instance after instance through step_row."""
+    import numpy as np
+    import torch
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    count = args.count
+    kind, order = args.scheme[:-1], int(args.scheme[-1])
+    if kind != "row":
+        raise SystemExit("--workload batch: ROW schemes only")
+    dt = args.dt or DT
+    rng = np.random.default_rng(7)
+    meshes, degrees, U0 = [], [], []
+    for k in range(count):
+        n = BATCH_MESHES[k % len(BATCH_MESHES)]
+        p = BATCH_DEGREES[(k // len(BATCH_MESHES)) % len(BATCH_DEGREES)]
+        xe, ye = S.uniform_mesh(n)
+        X, Y = S.point_coords(xe, ye, p)
+        v = S.Vortex(x0=float(rng.uniform(-4, 4)), y0=float(rng.uniform(-4, 4)))
+        meshes.append((xe, ye))
+        degrees.append(p)
+        U0.append(v.state(X, Y))
+    opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20)
+    B = fr.Batch(meshes, degrees, opts)
+    Ub = [torch.from_numpy(u).to(dev) for u in U0]
+    singles = [fr.Context(xe, ye, p, opts) for (xe, ye), p in zip(meshes, degrees)]
+    Us = [torch.from_numpy(u).to(dev) for u in U0]
+    ndofs = [m.ndof for m in B.members]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        units = 0.0
+        e0.record(stream)
+        for _ in range(steps):
+            units += fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), units
+
+    def batch_step(Ulist=Ub):
+        st = B.step_row(order, dt, Ulist)
+        return float(sum(n * s.gmres_iters for n, s in zip(ndofs, st)))
+
+    def seq_step():
+        return float(sum(n * fr.step_row(c, order, dt, U).gmres_iters for n, c, U in zip(ndofs, singles, Us)))
+
+    t_cap = time.perf_counter()
+    batch_step()  # captures the cycle graphs
+    capture_s = time.perf_counter() - t_cap
+    for _ in range(args.warmup - 1):
+        batch_step()
+    for _ in range(args.warmup):
+        seq_step()
+    launches0 = fr.fr_kernel_launches()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms, units = timed(batch_step, args.steps)
+    clk = clocks.stop()
+    launches = fr.fr_kernel_launches() - launches0
+    ms_seq, units_seq = timed(seq_step, args.steps)
+
+    # end to end: every state from pinned host memory and back, each step
+    host_in = [torch.from_numpy(u.cpu().numpy()).pin_memory() for u in Ub]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    Ud = [h.to(dev) for h in host_in]
+    batch_step(Ud)  # new state buffers: capture outside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_units = 0.0
+    for _ in range(args.steps):
+        for d, h in zip(Ud, host_in):
+            d.copy_(h, non_blocking=True)
+        e2e_units += batch_step(Ud)
+        for d, h in zip(Ud, host_out):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        host_in, host_out = host_out, host_in
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([ms, e2e_s, ms_seq], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units, e2e_units, units_seq], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, e2e_s, ms_seq = (float(x) for x in t)
+        units, e2e_units, units_seq = (float(x) for x in u)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    total = int(sum(ndofs))
+    wl = f"batch{count}-vortex-mesh16..64-p2..4-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
+    line = {
+        "metric": f"DOF*GMRES-iters/s ({wl})", "value": units / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl, "instances": count, "total_ndof": total,
+                   "meshes": list(BATCH_MESHES), "degrees": list(BATCH_DEGREES),
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set below L2 for most instances; no flush (launch-bound regime)",
+                   "graph_capture_s": capture_s},
+        "sequential": {"value": units_seq / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps,
+                       "note": "same instances, one step_row call after another"},
+        "speedup_vs_sequential": (units / ms) / (units_seq / ms_seq),
+        "gpu_launches": launches, "clocks": clk,
+        "roofline": None,
+        "roofline_note": "kernels run inside CUDA graphs; per-kernel event timing does not apply",
+        "cpu_baseline": None,
+        "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * total,
+                "d2h_bytes_per_step": 8 * total},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", choices=["residual", "jv", "factor", "apply"], default=None,
@@ -477,7 +623,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
-    ap.add_argument("--workload", choices=["vortex", "channel"], default="vortex")
+    ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
+    ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default="row3",
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2"])
     ap.add_argument("--dt", type=float, default=None)
@@ -498,6 +645,8 @@ def main():
         return kernel_arm(args)
     if args.t_end:
         return t_end_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
     return our_arm(args)
 
 

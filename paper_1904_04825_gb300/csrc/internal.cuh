@@ -213,8 +213,10 @@ int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s);
 int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
                double* x, int m, double rtol, int max_restarts, bool x_is_zero,
                fr_gmres_info* info, cudaStream_t s);
+// fin (device int, may be NULL): set by the cycle once the solve met its
+// tolerance; a cycle that finds it set does no work (for replayed graphs).
 int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
-                        double* x, int m, double rtol, double* status, cudaStream_t s);
+                        double* x, int m, double rtol, double* status, int* fin, cudaStream_t s);
 // tables.cu
 void build_tables(int p, Tables* t);
 // ns.cu (viscous path): mode 0 R, 1 A z, 2 b - A z; block formation + inversion

@@ -199,8 +199,14 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
 }
 
 // start of a cycle: beta = ||r||, g = beta e_1, done if beta <= rtol ||b||
-__global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, double rtol, int m) {
+__global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, double rtol, int m,
+                             const int* fin) {
   if (threadIdx.x != 0) return;
+  if (fin && *fin) {  // solve already finished: the whole cycle is skipped
+    *gd.k = 0;
+    *gd.done = 1;
+    return;
+  }
   const double beta = sqrt(*nr2);
   const double target = rtol * sqrt(*nb2);
   for (int i = 0; i <= m; ++i) gd.g[i] = 0.0;
@@ -253,9 +259,17 @@ __global__ void k_backsub(GmresDev gd) {
   }
 }
 
-// cycle status for the host: [k, |g_k|, rtol ||b||, ||b||]
-__global__ void k_status(GmresDev gd, const double* nb2, double* out) {
+// cycle status for the host: [k, |g_k|, rtol ||b||, ||b||]; marks the
+// solve finished once the residual met the target
+__global__ void k_status(GmresDev gd, const double* nb2, double* out, int* fin) {
   if (threadIdx.x != 0) return;
+  if (fin) {
+    if (*fin) {
+      out[0] = 0.0;
+      return;
+    }
+    if (*gd.res <= *gd.target) *fin = 1;
+  }
   out[0] = (double)*gd.k;
   out[1] = *gd.res;
   out[2] = *gd.target;
@@ -318,7 +332,7 @@ int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s) {
 // that stop on the device, the solution update, and the status
 // [k, |g_k|, target, ||b||] written to status (device, 4 doubles).
 int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
-                        double* x, int m, double rtol, double* status, cudaStream_t s) {
+                        double* x, int m, double rtol, double* status, int* fin, cudaStream_t s) {
   const long long n = ctx->ndof;
   double* sc = ctx->scal;
   GmresDev& gd = ctx->gd;
@@ -326,9 +340,9 @@ int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double s
   FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
   FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
   FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
-  FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, nullptr, s));
+  FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, fin, s));
   FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m, fin); }
   FRK_LAUNCHED(ctx);
   for (int j = 0; j < m; ++j) {
     double* vj = V + (size_t)j * n;
@@ -347,7 +361,7 @@ int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double s
   { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
   FRK_LAUNCHED(ctx);
   FRK_TRY(launch_solution_update(ctx, x, s));
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status, fin); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -388,7 +402,7 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
       FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, nullptr, s));
     }
     FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
-    { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m); }
+    { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m, nullptr); }
     FRK_LAUNCHED(ctx);
     // Launch the cycle in chunks of kChunk iterations; after launching chunk
     // c, wait for the finished-flag copied after chunk c-1, so the device

@@ -467,6 +467,7 @@ struct fr_batch {
   std::vector<cudaEvent_t> join;
   double* status_dev = nullptr;   // [count][4] GMRES cycle status
   double* status_host = nullptr;  // pinned mirror
+  int* fin_dev = nullptr;         // [count] stage solve finished (reset per stage)
   cudaGraphExec_t exec[6] = {};
   long long nodes[6] = {};
   std::vector<const double*> keyU;
@@ -509,6 +510,7 @@ void free_batch(fr_batch* B) {
   if (B->fork) cudaEventDestroy(B->fork);
   if (B->main) cudaStreamDestroy(B->main);
   cudaFree(B->status_dev);
+  cudaFree(B->fin_dev);
   cudaFreeHost(B->status_host);
   delete B;
 }
@@ -545,7 +547,7 @@ int capture_cycle(fr_batch* B, int i, const RowTab& t, double dt, double* const*
     fr_ctx* c = B->m[k];
     const double* b = (i == 0) ? c->buf[B_R0] : (i > 0 ? c->buf[B_RHS] : nullptr);
     rc = gmres_cycle_enqueue(c, U[k], c->buf[B_R0], shift, b, c->buf[B_Y0 + i], c->opts.gmres_m,
-                             c->opts.tol_lin, B->status_dev + 4 * k, B->st[k]);
+                             c->opts.tol_lin, B->status_dev + 4 * k, B->fin_dev + k, B->st[k]);
     if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
   }
   if (rc == FR_OK) rc = join_all(B);
@@ -607,6 +609,7 @@ extern "C" int fr_batch_create(int count, const fr_mesh_desc* meshes, const int*
   }
   if (rc == FR_OK && cudaMalloc(&B->status_dev, (size_t)count * 4 * sizeof(double)) != cudaSuccess) rc = FR_ERR_CUDA;
   if (rc == FR_OK && cudaMallocHost(&B->status_host, (size_t)count * 4 * sizeof(double)) != cudaSuccess) rc = FR_ERR_CUDA;
+  if (rc == FR_OK && cudaMalloc(&B->fin_dev, (size_t)count * sizeof(int)) != cudaSuccess) rc = FR_ERR_CUDA;
   if (rc != FR_OK) {
     free_batch(B);
     return rc;
@@ -669,6 +672,7 @@ extern "C" int fr_batch_step_row(fr_batch* B, int scheme, double dt, double* con
       BATCH_TRY(B, k, launch_fill(B->m[k], B->m[k]->buf[B_Y0 + i], 0.0, B->st[k]));
     }
     FRK_TRY(join_all(B));
+    BATCH_CUDA(B, cudaMemsetAsync(B->fin_dev, 0, (size_t)K * sizeof(int), B->main));
     if (!B->exec[i]) FRK_TRY(capture_cycle(B, i, t, dt, U));
     std::vector<int> conv(K, 0), cycles(K, 0);
     const int max_restarts = B->m[0]->opts.gmres_max_restarts;
@@ -752,7 +756,7 @@ int time_cycles(fr_ctx* ctx, const double* U, double shift, int reps, cudaEvent_
   for (int r = 0; r <= reps; ++r) {
     FRK_TRY(launch_fill(ctx, x, 0.0, s));
     if (r == 1) FRK_CUDA(ctx, cudaEventRecord(e0, s));
-    FRK_TRY(gmres_cycle_enqueue(ctx, U, b, shift, b, x, m, 0.0, ctx->scal + S_ST0, s));
+    FRK_TRY(gmres_cycle_enqueue(ctx, U, b, shift, b, x, m, 0.0, ctx->scal + S_ST0, nullptr, s));
   }
   FRK_CUDA(ctx, cudaEventRecord(e1, s));
   FRK_CUDA(ctx, cudaEventSynchronize(e1));
