@@ -466,16 +466,13 @@ def kernel_arm(args):
     return 0
 
 
-BATCH_MESHES = (16, 24, 32, 48, 64)
-BATCH_DEGREES = (2, 3, 4)
-
-
 def batch_arm(args):
-    """Many small independent problems: 64 vortex instances of uneven size
-    (meshes 16^2..64^2 of [-5,5]^2, p = 2, 3, 4, vortex centres spread over
-    the box), one ROW step of dt for all per call.  Timed twice on the same
-    instances and states: through the batch API (graph-replayed GMRES cycles
-    of all instances) and instance after instance through step_row."""
+    """Many independent problems: 64 vortex instances of uneven size (seeded
+    centres, strengths and flow angles; meshes 32^2..128^2 of [-5,5]^2;
+    p = 2, 3, 4), one step of dt for all per call (ROW4 by default).  Timed
+    twice on the same instances: through the batch API (graph-replayed GMRES
+    cycles for ROW, a host thread pool over instance streams for ESDIRK and
+    BDF2) and instance after instance through the single-instance calls."""
     import numpy as np
     import torch
     import paper_1904_04825_gb300 as fr
@@ -493,28 +490,27 @@ def batch_arm(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     count = args.count
-    kind, order = args.scheme[:-1], int(args.scheme[-1])
-    if kind != "row":
-        raise SystemExit("--workload batch: ROW schemes only")
+    scheme = args.scheme or "row4"
+    kind, order = scheme[:-1], int(scheme[-1])
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
     dt = args.dt or DT
-    rng = np.random.default_rng(7)
-    meshes, degrees, U0 = [], [], []
-    for k in range(count):
-        n = BATCH_MESHES[k % len(BATCH_MESHES)]
-        p = BATCH_DEGREES[(k // len(BATCH_MESHES)) % len(BATCH_DEGREES)]
-        xe, ye = S.uniform_mesh(n)
-        X, Y = S.point_coords(xe, ye, p)
-        v = S.Vortex(x0=float(rng.uniform(-4, 4)), y0=float(rng.uniform(-4, 4)))
-        meshes.append((xe, ye))
-        degrees.append(p)
-        U0.append(v.state(X, Y))
-    opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20)
+    inst = S.batch_instances(count, seed=0)
+    meshes = [i.mesh() for i in inst]
+    degrees = [i.p for i in inst]
+    U0 = [i.state() for i in inst]
+    tol = TOL_LIN if kind == "row" else 1e-1
+    opts = fr.default_opts(tol_lin=tol, gmres_m=30, gmres_max_restarts=20, block_precision=prec)
+    ptc = fr.default_ptc_opts(tol_nl=1e-6, tol_lin=1e-1)
     B = fr.Batch(meshes, degrees, opts)
     Ub = [torch.from_numpy(u).to(dev) for u in U0]
+    Pb = [torch.empty_like(u) for u in Ub]
     singles = [fr.Context(xe, ye, p, opts) for (xe, ye), p in zip(meshes, degrees)]
     Us = [torch.from_numpy(u).to(dev) for u in U0]
+    Ps = [torch.empty_like(u) for u in Us]
     ndofs = [m.ndof for m in B.members]
     stream = torch.cuda.current_stream()
+    nb = [0]
+    ns = [0]
 
     def timed(fn, steps):
         torch.cuda.synchronize()
@@ -534,15 +530,30 @@ def batch_arm(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), units
 
-    def batch_step(Ulist=Ub):
-        st = B.step_row(order, dt, Ulist)
+    def batch_step(Ulist=Ub, Plist=Pb):
+        if kind == "row":
+            st = B.step_row(order, dt, Ulist)
+        elif kind == "esdirk":
+            st = B.step_esdirk(order, dt, Ulist, ptc)
+        else:
+            st = B.step_bdf2(dt, Ulist, Plist, nb[0] == 0, ptc)
+        nb[0] += 1
         return float(sum(n * s.gmres_iters for n, s in zip(ndofs, st)))
 
+    def seq_one(c, U, P):
+        if kind == "row":
+            return fr.step_row(c, order, dt, U)
+        if kind == "esdirk":
+            return fr.step_esdirk(c, order, dt, U, ptc)
+        return fr.step_bdf2(c, dt, U, P, ns[0] == 0, ptc)
+
     def seq_step():
-        return float(sum(n * fr.step_row(c, order, dt, U).gmres_iters for n, c, U in zip(ndofs, singles, Us)))
+        u = float(sum(n * seq_one(c, U, P).gmres_iters for n, c, U, P in zip(ndofs, singles, Us, Ps)))
+        ns[0] += 1
+        return u
 
     t_cap = time.perf_counter()
-    batch_step()  # captures the cycle graphs
+    batch_step()  # captures the cycle graphs (ROW)
     capture_s = time.perf_counter() - t_cap
     for _ in range(args.warmup - 1):
         batch_step()
@@ -560,14 +571,16 @@ def batch_arm(args):
     host_in = [torch.from_numpy(u.cpu().numpy()).pin_memory() for u in Ub]
     host_out = [torch.empty_like(h).pin_memory() for h in host_in]
     Ud = [h.to(dev) for h in host_in]
-    batch_step(Ud)  # new state buffers: capture outside the timed region
+    Pd = [torch.empty_like(u) for u in Ud]
+    nb[0] = 0
+    batch_step(Ud, Pd)  # new state buffers: capture outside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_units = 0.0
     for _ in range(args.steps):
         for d, h in zip(Ud, host_in):
             d.copy_(h, non_blocking=True)
-        e2e_units += batch_step(Ud)
+        e2e_units += batch_step(Ud, Pd)
         for d, h in zip(Ud, host_out):
             h.copy_(d, non_blocking=True)
         torch.cuda.synchronize()
@@ -585,19 +598,22 @@ def batch_arm(args):
             dist.destroy_process_group()
         return 0
     total = int(sum(ndofs))
-    wl = f"batch{count}-vortex-mesh16..64-p2..4-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
+    wl = (f"batch{count}-vortex-mesh32..128-p2..4-{scheme.upper()}-dt{dt:g}-gmres30-tol{tol:g}"
+          + (f"-{args.block_precision}blocks" if prec else ""))
     line = {
         "metric": f"DOF*GMRES-iters/s ({wl})", "value": units / (ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl, "instances": count, "total_ndof": total,
-                   "meshes": list(BATCH_MESHES), "degrees": list(BATCH_DEGREES),
+                   "meshes": list(S.BATCH_MESHES), "degrees": list(S.BATCH_DEGREES),
+                   "instances_recipe": "PCG64 seed 0: centre U([-2.5,2.5]^2), alpha U[3,6], theta U[0,2pi), "
+                                       "mesh and p uniform",
                    "parallelism": f"replicas x{world}",
-                   "l2": "working set below L2 for most instances; no flush (launch-bound regime)",
+                   "l2": "working set of all instances ~10x the L2; no flush",
                    "graph_capture_s": capture_s},
         "sequential": {"value": units_seq / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps,
-                       "note": "same instances, one step_row call after another"},
+                       "note": "same instances, one single-instance step call after another"},
         "speedup_vs_sequential": (units / ms) / (units_seq / ms_seq),
         "gpu_launches": launches, "clocks": clk,
         "roofline": None,
@@ -625,7 +641,7 @@ def main():
                     help="element-Jacobi block precision (fp64 = the plain method)")
     ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
-    ap.add_argument("--scheme", default="row3",
+    ap.add_argument("--scheme", default=None,
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2"])
     ap.add_argument("--dt", type=float, default=None)
     ap.add_argument("--t-end", type=float, default=None,
@@ -637,6 +653,8 @@ def main():
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     args = ap.parse_args()
+    if args.scheme is None and args.workload != "batch":
+        args.scheme = "row3"
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

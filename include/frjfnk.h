@@ -312,6 +312,23 @@ fr_ctx* fr_batch_member(fr_batch* batch, int k);
 int fr_batch_step_row(fr_batch* batch, int scheme, double dt, double* const* U, fr_step_stats* stats,
                       void* stream);
 
+/* One ESDIRK step (scheme 2, 3 or 4, as step_esdirk) / one BDF2 step (as
+ * step_bdf2; U_prev[k] in/out) of every instance.  Each pseudo-transient
+ * iteration decides on the host from its own residual norms, so instances
+ * run their own control loops: `threads` host threads (0 = one per host
+ * core, at most one per instance) take instances in turn and step each on
+ * the instance's stream, so the kernels of different instances overlap on
+ * the device.  Blocks until every instance finished.  stats[k] as for the
+ * single-instance calls.  Returns FR_OK, or the most severe instance status
+ * (FR_ERR_CUDA / FR_ERR_NONFINITE / FR_ERR_INVALID_ARG before
+ * FR_ERR_NOT_CONVERGED / FR_ERR_PTC_STALLED); fr_batch_last_error names the
+ * instance.  Each instance's U (and U_prev) follows that instance's status
+ * as the single-instance calls document it. */
+int fr_batch_step_esdirk(fr_batch* batch, int scheme, double dt, double* const* U, const fr_ptc_opts* ptc,
+                         int threads, fr_step_stats* stats, void* stream);
+int fr_batch_step_bdf2(fr_batch* batch, double dt, double* const* U, double* const* U_prev, int first_step,
+                       const fr_ptc_opts* ptc, int threads, fr_step_stats* stats, void* stream);
+
 /* ---- launch configuration (no counterpart in the paper) ----------------
  * vec_blocks: grid of the streaming Krylov-vector kernels (dots, updates,
  * norms, block apply), 1..4096 CTAs; tile_variant: element-tile shape of

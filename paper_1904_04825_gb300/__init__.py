@@ -130,6 +130,10 @@ def _load():
         "fr_batch_last_error": (ctypes.c_char_p, [P]),
         "fr_batch_member": (P, [P, I]),
         "fr_batch_step_row": (I, [P, I, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fr_step_stats), V]),
+        "fr_batch_step_esdirk": (I, [P, I, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fr_ptc_opts), I,
+                                     ctypes.POINTER(fr_step_stats), V]),
+        "fr_batch_step_bdf2": (I, [P, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), I,
+                                   ctypes.POINTER(fr_ptc_opts), I, ctypes.POINTER(fr_step_stats), V]),
         "fr_set_launch_config": (I, [P, I, I]),
         "fr_get_launch_config": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "fr_autotune": (I, [P, P, D, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
@@ -527,15 +531,40 @@ class Batch:
         except Exception:
             pass
 
-    def step_row(self, scheme: int, dt: float, Us, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+    def _states(self, Us):
         if len(Us) != len(self.members):
             raise ValueError("one state per instance")
         for U, m in zip(Us, self.members):
             if U.numel() != m.ndof:
                 raise ValueError("state shape does not match its instance")
-        ptrs = (ctypes.c_void_p * len(Us))(*[_ptr(U).value for U in Us])
-        st = (fr_step_stats * len(Us))()
-        rc = lib.fr_batch_step_row(self.handle, int(scheme), float(dt), ptrs, st, _stream(stream))
+        return (ctypes.c_void_p * len(Us))(*[_ptr(U).value for U in Us])
+
+    def _finish(self, rc, st, allow):
         if rc != FR_OK and rc not in allow:
             raise FrError(rc, lib.fr_batch_last_error(self.handle).decode())
-        return [_stats(st[k], rc) for k in range(len(Us))]
+        return [_stats(st[k], rc) for k in range(len(self.members))]
+
+    def step_row(self, scheme: int, dt: float, Us, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+        ptrs = self._states(Us)
+        st = (fr_step_stats * len(Us))()
+        rc = lib.fr_batch_step_row(self.handle, int(scheme), float(dt), ptrs, st, _stream(stream))
+        return self._finish(rc, st, allow)
+
+    def step_esdirk(self, scheme: int, dt: float, Us, ptc: fr_ptc_opts | None = None, threads: int = 0,
+                    stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+        ptrs = self._states(Us)
+        st = (fr_step_stats * len(Us))()
+        rc = lib.fr_batch_step_esdirk(self.handle, int(scheme), float(dt), ptrs,
+                                      ctypes.byref(ptc) if ptc is not None else None, int(threads), st,
+                                      _stream(stream))
+        return self._finish(rc, st, allow)
+
+    def step_bdf2(self, dt: float, Us, Uprevs, first_step: bool, ptc: fr_ptc_opts | None = None,
+                  threads: int = 0, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
+        ptrs = self._states(Us)
+        prev = self._states(Uprevs)
+        st = (fr_step_stats * len(Us))()
+        rc = lib.fr_batch_step_bdf2(self.handle, float(dt), ptrs, prev, int(bool(first_step)),
+                                    ctypes.byref(ptc) if ptc is not None else None, int(threads), st,
+                                    _stream(stream))
+        return self._finish(rc, st, allow)

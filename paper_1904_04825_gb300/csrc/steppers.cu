@@ -3,8 +3,12 @@
 // on the caller's stream; the host reads back only the scalars the method
 // branches on (GMRES cycle status, ||F|| of each pseudo step).
 #include <cmath>
+#include <atomic>
+#include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -720,6 +724,87 @@ extern "C" int fr_batch_step_row(fr_batch* B, int scheme, double dt, double* con
   }
   if (!ok) return batch_err(B, FR_ERR_NOT_CONVERGED, "batch: a stage solve did not converge");
   return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched ESDIRK / BDF2: every pseudo-transient iteration of an instance
+// takes host decisions (acceptance, SER, rejection) on its own residual
+// norms, so the instances cannot share one graph.  Instead a pool of host
+// threads takes instances from a shared counter and runs each instance's
+// step on that instance's stream; the kernels of different instances
+// overlap on the device and their host waits overlap on the CPU.
+
+namespace frk {
+namespace {
+
+int run_members(fr_batch* B, void* stream, int threads, const std::function<int(int)>& fn) {
+  const int K = (int)B->m.size();
+  cudaStream_t caller = as_stream(stream);
+  BATCH_CUDA(B, cudaEventRecord(B->fork, caller));
+  for (cudaStream_t s : B->st) BATCH_CUDA(B, cudaStreamWaitEvent(s, B->fork, 0));
+  std::vector<int> rc(K, FR_OK);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int k = next.fetch_add(1); k < K; k = next.fetch_add(1)) rc[k] = fn(k);
+  };
+  int T = threads > 0 ? threads : (int)std::thread::hardware_concurrency();
+  if (T < 1) T = 1;
+  if (T > K) T = K;
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  for (size_t k = 0; k < B->st.size(); ++k) {
+    BATCH_CUDA(B, cudaEventRecord(B->join[k], B->st[k]));
+    BATCH_CUDA(B, cudaStreamWaitEvent(caller, B->join[k], 0));
+  }
+  // most severe status first: hard errors, then non-convergence
+  int worst = FR_OK;
+  for (int k = 0; k < K; ++k) {
+    if (rc[k] == FR_OK) continue;
+    const bool soft = rc[k] == FR_ERR_NOT_CONVERGED || rc[k] == FR_ERR_PTC_STALLED;
+    const bool worst_soft = worst == FR_OK || worst == FR_ERR_NOT_CONVERGED || worst == FR_ERR_PTC_STALLED;
+    if (worst == FR_OK || (worst_soft && !soft)) {
+      worst = rc[k];
+      char msg[256];
+      std::snprintf(msg, sizeof(msg), "instance %d: %s", k, fr_last_error(B->m[k]));
+      batch_err(B, rc[k], msg);
+    }
+  }
+  return worst;
+}
+
+}  // namespace
+}  // namespace frk
+
+extern "C" int fr_batch_step_esdirk(fr_batch* B, int scheme, double dt, double* const* U, const fr_ptc_opts* ptc,
+                                    int threads, fr_step_stats* stats, void* stream) {
+  if (!B || !U) return FR_ERR_INVALID_ARG;
+  if (scheme < 2 || scheme > 4 || !(dt > 0.0)) return batch_err(B, FR_ERR_INVALID_ARG, "bad scheme or dt");
+  const int K = (int)B->m.size();
+  for (int k = 0; k < K; ++k)
+    if (!U[k]) return batch_err(B, FR_ERR_INVALID_ARG, "null state");
+  return run_members(B, stream, threads, [&](int k) {
+    fr_step_stats st{};
+    const int r = step_esdirk(B->m[k], scheme, dt, U[k], ptc, &st, B->st[k]);
+    if (stats) stats[k] = st;
+    return r;
+  });
+}
+
+extern "C" int fr_batch_step_bdf2(fr_batch* B, double dt, double* const* U, double* const* U_prev, int first_step,
+                                  const fr_ptc_opts* ptc, int threads, fr_step_stats* stats, void* stream) {
+  if (!B || !U || !U_prev) return FR_ERR_INVALID_ARG;
+  if (!(dt > 0.0)) return batch_err(B, FR_ERR_INVALID_ARG, "bad dt");
+  const int K = (int)B->m.size();
+  for (int k = 0; k < K; ++k)
+    if (!U[k] || !U_prev[k]) return batch_err(B, FR_ERR_INVALID_ARG, "null state");
+  return run_members(B, stream, threads, [&](int k) {
+    fr_step_stats st{};
+    const int r = step_bdf2(B->m[k], dt, U[k], U_prev[k], first_step, ptc, &st, B->st[k]);
+    if (stats) stats[k] = st;
+    return r;
+  });
 }
 
 // ---------------------------------------------------------------------------

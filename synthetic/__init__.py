@@ -254,3 +254,43 @@ class Channel:
         v = scale * vp
         T = self.temperature
         return conserved(np.ones_like(X), u, v, T * np.ones_like(X), self.gamma)
+
+
+@dataclass
+class Instance:
+    """One member of a batch of independent vortex problems."""
+    n: int          # n x n uniform quads of [-5,5]^2
+    p: int          # polynomial degree
+    vortex: Vortex
+
+    def mesh(self):
+        return uniform_mesh(self.n)
+
+    def state(self) -> np.ndarray:
+        xe, ye = self.mesh()
+        X, Y = point_coords(xe, ye, self.p)
+        return self.vortex.state(X, Y)
+
+
+BATCH_MESHES = (32, 48, 64, 96, 128)
+BATCH_DEGREES = (2, 3, 4)
+
+
+def batch_instances(count: int = 64, seed: int = 0, meshes=BATCH_MESHES, degrees=BATCH_DEGREES):
+    """Independent vortex instances of uneven size and degree.
+
+    One PCG64 stream (``seed``); per instance, in this order: centre
+    (x0, y0) ~ U([-2.5, 2.5]^2), strength alpha ~ U[3, 6], flow angle
+    theta ~ U[0, 2 pi), mesh n uniform over ``meshes``, degree p uniform
+    over ``degrees``.  Mach 0.5 on the free-stream speed sqrt(2), phi = 1/2.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        x0, y0 = rng.uniform(-2.5, 2.5, 2)
+        alpha = rng.uniform(3.0, 6.0)
+        theta = rng.uniform(0.0, 2.0 * math.pi)
+        n = int(meshes[rng.integers(len(meshes))])
+        p = int(degrees[rng.integers(len(degrees))])
+        out.append(Instance(n, p, Vortex(alpha=float(alpha), theta=float(theta), x0=float(x0), y0=float(y0))))
+    return out
