@@ -432,10 +432,13 @@ def kernel_arm(args):
     import synthetic as S
 
     torch.cuda.set_device(0)
+    if args.kernel in ("mlp", "mlp_train"):
+        return mlp_kernel_arm(args)
     xe, ye = S.uniform_mesh(NX)
     X, Y = S.point_coords(xe, ye, P)
     U = torch.from_numpy(S.Vortex().state(X, Y)).cuda()
-    ctx = fr.Context(xe, ye, P)
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
+    ctx = fr.Context(xe, ye, P, fr.default_opts(block_precision=prec))
     R = ctx.empty()
     fr.fr_residual(ctx, U, R)
     z = torch.from_numpy(S.random_vector(ctx.shape, 1)).cuda()
@@ -458,7 +461,8 @@ def kernel_arm(args):
     torch.cuda.synchronize()
     pr = fr.fr_profile_end(ctx)[args.kernel]
     us = pr["ms"] / max(pr["launches"], 1) * 1e3
-    print(json.dumps({"kernel": args.kernel, "launches": pr["launches"], "avg_us": us,
+    print(json.dumps({"kernel": args.kernel, "block_precision": args.block_precision,
+                      "launches": pr["launches"], "avg_us": us,
                       "tflops": pr["flops"] / pr["launches"] / (us * 1e-6) / 1e12,
                       "gbs": pr["bytes"] / pr["launches"] / (us * 1e-6) / 1e9,
                       "bytes_per_launch": pr["bytes"] / pr["launches"],
@@ -628,9 +632,64 @@ def batch_arm(args):
     return 0
 
 
+def mlp_kernel_arm(args):
+    """The per-element guess MLP at the size of its largest workload: one
+    inference (BF16 tensor cores, FP32 accumulate) or one training step
+    (FP32 forward + backward + Adam) over the 73,728 elements of a 384x192
+    p=4 mesh; features 3 x 100, two hidden layers of 256, 100 outputs."""
+    import numpy as np
+    import torch
+    import paper_1904_04825_gb300 as fr
+
+    n_in, n_h, n_out, M = 300, 256, 100, 384 * 192
+    net = fr.MLP(n_in, n_h, n_out, M)
+    rng = np.random.default_rng(0)
+    flat = np.concatenate([rng.standard_normal(n).astype(np.float32) * 0.05 for n in [net.nparam]])
+    net.set_params(flat)
+    X = torch.from_numpy(rng.standard_normal((M, n_in)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.standard_normal((M, n_out)).astype(np.float32)).cuda()
+    Yo = torch.empty((M, n_out), dtype=torch.float32, device="cuda")
+    gemm_flops = 2.0 * M * (n_in * n_h + n_h * n_h + n_h * n_out)
+    if args.kernel == "mlp":
+        run = lambda: net.forward(X, Yo, bf16=True)
+        flops = gemm_flops
+    else:
+        def run():
+            net.forward(X, Yo, bf16=False)
+            net.backward(X, T)
+            net.adam()
+        # forward, weight gradients of all layers, input gradients of layers 2 and 3
+        flops = 2.0 * gemm_flops + 2.0 * M * (n_h * n_h + n_h * n_out)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    out = {"kernel": args.kernel, "elements": M, "layers": [n_in, n_h, n_h, n_out], "ms": ms,
+           "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12}
+    if args.kernel == "mlp":
+        pk = peaks.get("bf16_tflops")
+        out["bf16_peak_tflops"] = pk
+        out["frac_of_measured_bf16"] = (out["tflops"] / pk) if pk else None
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["residual", "jv", "factor", "apply"], default=None,
+    ap.add_argument("--kernel", choices=["residual", "jv", "factor", "apply", "mlp", "mlp_train"], default=None,
                     help="time one kernel family alone on the full-size inputs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
