@@ -164,7 +164,11 @@ int ejacobi_factor(fr_ctx* ctx, const double* U, const double* R0, double shift,
 
 /* z_e = M_e^{-1} r_e for every element with the blocks of the last
  * ejacobi_factor call (FR_ERR_INVALID_ARG if there was none).  r, z: device,
- * ndof doubles, must not alias. */
+ * ndof doubles, must not alias; r 16-byte aligned (FR_ERR_INVALID_ARG
+ * otherwise: element blocks and rows of r are streamed into shared memory
+ * by bulk copies).  A copy that never completes (bounded wait) sets the
+ * context's error flag; the next GMRES cycle then returns FR_ERR_TIMEOUT
+ * and the context should be destroyed. */
 int ejacobi_apply(fr_ctx* ctx, const double* r, double* z, void* stream);
 
 /* Solve A x = b, A z = shift*z - (R(U+eps z) - R0)/eps, with restarted

@@ -48,6 +48,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->gd.h2);
   cudaFree(c->gd.invh);
   cudaFree(c->gd.done);
+  cudaFree(c->kerr);
   cudaFree(c->gd.rflag);
   cudaFree(c->gd.k);
   cudaFree(c->gd.res);
@@ -126,6 +127,8 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   FRK_TRY(dalloc(c, &c->gd.k, 1));
   FRK_TRY(dalloc(c, &c->gd.res, 1));
   FRK_TRY(dalloc(c, &c->gd.target, 1));
+  FRK_TRY(dalloc(c, &c->kerr, 1));
+  FRK_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), (4 + kMaxVec) * sizeof(int)));
   FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 8 * sizeof(double)));
   for (cudaEvent_t& e : c->chunk_ev) FRK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

@@ -307,45 +307,119 @@ __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, 
 // z = Minv r (optionally r scaled by *scale first and written back), optional
 // sum of squares of z.  EPC elements per CTA, one thread per block row.
 // S: block storage type; A: accumulation type (FP64 for FP64 blocks, FP32 otherwise).
+// Shape of the staged apply per block size and storage type: KS threads
+// share one row's dot product (threads = KS nb), NS elements in flight per
+// CTA (element block + its r, one bulk copy each, in a ring of stages).
+template <int NB, typename S> struct ApplyShape;
+template <> struct ApplyShape<36, double> { static constexpr int KS = 4, NS = 6; };
+template <> struct ApplyShape<64, double> { static constexpr int KS = 2, NS = 3; };
+template <> struct ApplyShape<100, double> { static constexpr int KS = 2, NS = 2; };
+template <> struct ApplyShape<36, float> { static constexpr int KS = 4, NS = 8; };
+template <> struct ApplyShape<64, float> { static constexpr int KS = 2, NS = 4; };
+template <> struct ApplyShape<100, float> { static constexpr int KS = 2, NS = 3; };
+template <> struct ApplyShape<36, __nv_bfloat16> { static constexpr int KS = 4, NS = 8; };
+template <> struct ApplyShape<64, __nv_bfloat16> { static constexpr int KS = 2, NS = 6; };
+template <> struct ApplyShape<100, __nv_bfloat16> { static constexpr int KS = 2, NS = 4; };
+
 template <int NB, typename S, typename A>
-__global__ void __launch_bounds__(256) k_apply(const S* __restrict__ Minv, double* r,
-                                               const double* scale, double* __restrict__ z,
-                                               long long ne, double* sumsq, Reduce red,
-                                               const int* done, EpsArgs ea) {
-  constexpr int EPC = 256 / NB;
-  __shared__ A rs[EPC][NB];
-  __shared__ double sh[32];
+struct ApplyLayout {
+  static constexpr int KS = ApplyShape<NB, S>::KS, NS = ApplyShape<NB, S>::NS;
+  static constexpr int WORKERS = KS * NB;                   // threads with a (row, k-range)
+  static constexpr int THREADS = (WORKERS + 31) / 32 * 32;  // whole warps (the reductions shuffle)
+  static constexpr unsigned MB = (unsigned)(NB * NB * sizeof(S));  // one block (multiple of 16)
+  static constexpr unsigned RB = (unsigned)(NB * sizeof(double));  // its r (multiple of 16)
+  static constexpr unsigned STAGE = (MB + RB + 127) / 128 * 128;
+  static constexpr size_t BYTES = (size_t)NS * STAGE + (size_t)(1 + KS) * NB * sizeof(A) + 32 * sizeof(double) +
+                                  NS * sizeof(unsigned long long);
+};
+
+// z_e = M_e^-1 (s r_e) per element (optionally r_e *= s written back), and the
+// sum of squares of z.  Persistent CTAs walk the elements e = blockIdx.x +
+// t gridDim.x; thread 0 keeps NS elements' block and r in flight with bulk
+// copies (TMA engine) completing on per-stage mbarriers, so the block bytes
+// stream from HBM while the previous elements are multiplied out of shared
+// memory (column-major blocks: thread i reads consecutive addresses).  Each
+// row's dot product is split over KS threads and summed in a fixed order.
+// A wait that gives up sets *kerr, waits (bounded) for the copies it issued
+// and leaves.
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
+    k_apply(const S* __restrict__ Minv, double* r, const double* scale, double* __restrict__ z, long long ne,
+            double* sumsq, Reduce red, const int* done, EpsArgs ea, int* kerr) {
+  using L = ApplyLayout<NB, S, A>;
+  constexpr int KS = L::KS, NS = L::NS, KP = NB / KS;
+  extern __shared__ __align__(128) double smem_d[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(smem_d);
+  A* rs = reinterpret_cast<A*>(smem + (size_t)NS * L::STAGE);
+  A* part = rs + NB;
+  double* sh = reinterpret_cast<double*>(part + KS * NB);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sh + 32);
   if (done && *done) return;
-  const int el = threadIdx.x / NB, i = threadIdx.x % NB;
-  const double s = scale ? *scale : 1.0;
+  const int tid = threadIdx.x, i = tid % NB, ks = tid / NB;  // ks == KS: padding thread
+  const long long G = gridDim.x;
+  const long long nloc = ne > (long long)blockIdx.x ? (ne - 1 - blockIdx.x) / G + 1 : 0;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long t) {
+    const int q = (int)(t % NS);
+    const long long e = blockIdx.x + t * G;
+    unsigned char* st = smem + (size_t)q * L::STAGE;
+    mbar_arrive_expect_tx(&bar[q], L::MB + L::RB);
+    bulk_g2s(st, Minv + e * NB * NB, L::MB, &bar[q]);
+    bulk_g2s(st + L::MB, r + e * NB, L::RB, &bar[q]);
+  };
+  if (tid == 0)
+    for (long long t = 0; t < NS && t < nloc; ++t) issue(t);
+  const double sc = scale ? *scale : 1.0;
   double ss = 0.0;
-  for (long long e0 = (long long)blockIdx.x * EPC; e0 < ne; e0 += (long long)gridDim.x * EPC) {
-    const long long e = e0 + el;
-    const bool act = el < EPC && e < ne;
-    __syncthreads();
-    if (act) {
-      double v = r[e * NB + i];
+  long long t = 0;
+  for (; t < nloc; ++t) {
+    const int q = (int)(t % NS);
+    const bool ok = mbar_wait(&bar[q], (unsigned)((t / NS) & 1), kWaitPolls);
+    if (!__syncthreads_and(ok)) break;
+    const long long e = blockIdx.x + t * G;
+    const S* Ms = reinterpret_cast<const S*>(smem + (size_t)q * L::STAGE);
+    const double* rsrc = reinterpret_cast<const double*>(smem + (size_t)q * L::STAGE + L::MB);
+    if (ks == 0) {
+      double v = rsrc[i];
       if (scale) {
-        v *= s;
+        v *= sc;
         r[e * NB + i] = v;
       }
-      rs[el][i] = (A)v;
+      rs[i] = (A)v;
     }
     __syncthreads();
-    if (act) {
-      const S* Me = Minv + e * (long long)NB * NB;
+    if (ks < KS) {
+      const S* Mk = Ms + (size_t)(ks * KP) * NB + i;
+      const A* rk = rs + ks * KP;
       A acc0 = 0, acc1 = 0;
-#pragma unroll 8
-      for (int k = 0; k < NB; k += 2) {
-        acc0 = fma(load_acc(Me + k * NB + i), rs[el][k], acc0);
-        if (k + 1 < NB) acc1 = fma(load_acc(Me + (k + 1) * NB + i), rs[el][k + 1], acc1);
+#pragma unroll
+      for (int k = 0; k < KP; k += 2) {
+        acc0 = fma(load_acc(Mk + k * NB), rk[k], acc0);
+        if (k + 1 < KP) acc1 = fma(load_acc(Mk + (k + 1) * NB), rk[k + 1], acc1);
       }
-      const double zi = (double)(acc0 + acc1);
+      part[ks * NB + i] = acc0 + acc1;
+    }
+    __syncthreads();  // stage q consumed, partial sums visible
+    if (tid == 0 && t + NS < nloc) issue(t + NS);
+    if (ks == 0) {
+      A zz = part[i];
+#pragma unroll
+      for (int u = 1; u < KS; ++u) zz += part[u * NB + i];
+      const double zi = (double)zz;
       z[e * NB + i] = zi;
       ss = fma(zi, zi, ss);
     }
   }
-  if (sumsq) {
+  if (t < nloc && tid == 0) {  // a copy never completed: flag it and drain what was issued
+    atomicExch(kerr, 1);
+    for (long long u = t; u < nloc && u < t + NS; ++u)
+      (void)mbar_wait(&bar[u % NS], (unsigned)((u / NS) & 1), kWaitPolls);
+  }
+  if (sumsq) {  // every CTA takes part, so the reduction's counter stays consistent
     const double bs = block_sum(ss, sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
     if (last_block(red.counter)) {
@@ -469,8 +543,20 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
   const double nd = (double)ctx->ndof;
   const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
-  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB, S, A><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
-                                                                  sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
+  using L = ApplyLayout<NB, S, A>;
+  static int per_sm = 0;  // resident CTAs per SM (function attribute set once per process)
+  if (per_sm == 0) {
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    int occ = 0;
+    FRK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<NB, S, A>, L::THREADS, L::BYTES));
+    per_sm = occ > 0 ? occ : 1;
+  }
+  long long grid = (long long)per_sm * ctx->num_sms;
+  if (grid > ctx->ne) grid = ctx->ne;
+  if (grid > kRedBlocks) grid = kRedBlocks;
+  if (grid < 1) grid = 1;
+  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB, S, A><<<(unsigned)grid, L::THREADS, L::BYTES, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
+                                                                  sumsq, ctx->red, done, eps_args(ctx, with_eps), ctx->kerr); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -563,6 +649,9 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
 
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
                        const int* done, cudaStream_t s, bool with_eps) {
+  // the staged apply copies r with the bulk-copy engine: 16-byte aligned rows
+  if (reinterpret_cast<uintptr_t>(r) % 16 != 0)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply: r must be 16-byte aligned");
   if (!ctx->opts.precond) {
     { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx, ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
                                                           done, eps_args(ctx, with_eps)); }

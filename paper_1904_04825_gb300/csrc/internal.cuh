@@ -127,6 +127,8 @@ struct fr_ctx {
   double* z = nullptr;       // preconditioned basis vector
   double* buf[16] = {};      // stepper buffers, ndof each
   double* scal = nullptr;    // frk::S_COUNT device scalars
+  int num_sms = 1;           // SMs of the device (persistent grids)
+  int* kerr = nullptr;       // device flag: a kernel's bounded wait gave up
   int vec_blocks = frk::kVecBlocks;  // grid of the streaming vector kernels (autotuned)
   int tile_variant = 0;      // element-tile shape of the Euler residual kernel (autotuned)
   frk::Reduce red{};

@@ -261,8 +261,12 @@ __global__ void k_backsub(GmresDev gd) {
 
 // cycle status for the host: [k, |g_k|, rtol ||b||, ||b||]; marks the
 // solve finished once the residual met the target
-__global__ void k_status(GmresDev gd, const double* nb2, double* out, int* fin) {
+__global__ void k_status(GmresDev gd, const double* nb2, double* out, int* fin, const int* kerr) {
   if (threadIdx.x != 0) return;
+  if (*kerr) {  // a bounded wait gave up in this cycle
+    out[0] = -1.0;
+    return;
+  }
   if (fin) {
     if (*fin) {
       out[0] = 0.0;
@@ -361,7 +365,7 @@ int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double s
   { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
   FRK_LAUNCHED(ctx);
   FRK_TRY(launch_solution_update(ctx, x, s));
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status, fin); }
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status, fin, ctx->kerr); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -448,7 +452,9 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, gd.res, sizeof(double), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 1, gd.target, sizeof(double), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal + 2, sc + S_NB2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_stat + 1, ctx->kerr, sizeof(int), cudaMemcpyDeviceToHost, s));
     FRK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_stat[1]) return set_error(ctx, FR_ERR_TIMEOUT, "a kernel's bounded wait for its copies gave up");
     const int k = ctx->h_stat[0];
     const double res = ctx->h_scal[0], target = ctx->h_scal[1], bn = std::sqrt(ctx->h_scal[2]);
     {  // launches of this cycle that found it finished (for per-launch timing),

@@ -687,6 +687,7 @@ extern "C" int fr_batch_step_row(fr_batch* B, int scheme, double dt, double* con
       bool all = true;
       for (int k = 0; k < K; ++k) {
         const double* q = B->status_host + 4 * k;
+        if (q[0] < 0.0) return batch_err(B, FR_ERR_TIMEOUT, "a kernel's bounded wait for its copies gave up");
         if (!std::isfinite(q[1])) return batch_err(B, FR_ERR_NONFINITE, "batch GMRES residual not finite");
         if (conv[k]) continue;
         st[k].gmres_iters += (int)q[0];
