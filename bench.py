@@ -222,6 +222,13 @@ def our_arm(args):
     ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
     U = torch.from_numpy(U0).to(dev)
     Uprev = torch.empty_like(U)
+    tuned = None
+    if not args.no_autotune:
+        # launch configuration (vector-kernel grid, residual tile) measured on
+        # full GMRES cycles at this step's shift, before any timing
+        gam = {"row": {2: 0.43586652150845900, 3: 0.435866521508459, 4: 0.25}}.get(kind, {}).get(order, 0.5)
+        vb, tv, ms_best, ms_def = fr.autotune(ctx, U, 1.0 / (gam * dt), reps=2)
+        tuned = {"vec_blocks": vb, "tile_variant": tv, "cycle_ms": ms_best, "cycle_ms_default": ms_def}
     stream = torch.cuda.current_stream()
     ptc = fr.default_ptc_opts(tol_nl=1e-6, tol_lin=1e-1)
     nstep = [0]
@@ -352,7 +359,7 @@ def our_arm(args):
         "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
                            "block_precision": args.block_precision, "workload": wl,
                            "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
-                           "mesh": f"{ctx.nx}x{ctx.ny}",
+                           "mesh": f"{ctx.nx}x{ctx.ny}", "launch_config": tuned,
                            "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / dt) if args.workload == "vortex" else None}),
         "gpu_launches": launches,
         "clocks": clk,
@@ -393,7 +400,10 @@ def t_end_arm(args):
     dt = args.t_end / nsteps
     tol = args.tol
     ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else 1e-1, gmres_m=30,
-                                                gmres_max_restarts=20, block_precision=prec))
+                                                gmres_max_restarts=20, block_precision=prec,
+                                                guess=args.guess))
+    if not args.no_autotune:
+        fr.autotune(ctx, U, 1.0 / (0.5 * dt), reps=1)
     ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=args.tol_lin)
     iters = 0
     bad = 0
@@ -418,7 +428,7 @@ def t_end_arm(args):
     print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
-                      "block_precision": args.block_precision, "t_end": args.t_end,
+                      "block_precision": args.block_precision, "guess": args.guess, "t_end": args.t_end,
                       "time_to_t_end_s": wall, "E_rho": err, "gmres_iters": iters,
                       "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
     return 0
@@ -696,6 +706,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
     ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
@@ -709,6 +720,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6,
                     help="--t-end: tol_rel,linear for ROW, tol_rel,nonlinear for ESDIRK/BDF2")
     ap.add_argument("--tol-lin", type=float, default=1e-1, help="--t-end: ESDIRK/BDF2 GMRES tolerance")
+    ap.add_argument("--guess", type=int, default=0, choices=[0, 1],
+                    help="--t-end, ROW: stage-solve initial guess (0 zero, 1 previous step's)")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     args = ap.parse_args()

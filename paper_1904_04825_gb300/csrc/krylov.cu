@@ -122,10 +122,35 @@ __global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long
       case 7: dots_chunk<7>(ptr, w, n, acc); break;
       default: dots_chunk<8>(ptr, w, n, acc); break;
     }
-    for (int i = 0; i < nc; ++i) {
-      const double t = warp_sum(acc[i]);
-      if (lane == 0) sred[i][wid] = t;
+    // Warp sums of the (up to) 8 values by recursive halving: each exchange
+    // sends half of the values still held to the partner lane and keeps the
+    // other half, so lane l ends with the warp sum of value
+    // 4 b4 + 2 b3 + b2 (b = bits of l) after 9 additions instead of 8 x 5.
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i >= nc) acc[i] = 0.0;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double send = b4 ? acc[q] : acc[q + 4];
+      const double keep = b4 ? acc[q + 4] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double send = b3 ? acc[q] : acc[q + 2];
+      const double keep = b3 ? acc[q + 2] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+      const double send = b2 ? acc[0] : acc[1];
+      const double keep = b2 ? acc[1] : acc[0];
+      acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    const int vi = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+    if ((lane & 3) == 0 && vi < nc) sred[vi][wid] = acc[0];
     __syncthreads();
     if ((int)threadIdx.x < nc) {
       double t = 0.0;
