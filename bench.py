@@ -204,7 +204,8 @@ def our_arm(args):
         X, Y = S.point_coords(xe, ye, P)
         U0 = S.Vortex().state(X, Y)
         p, dt, wall = P, (args.dt or DT), False
-        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec)
+        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
+                               jv_precision=1 if args.jv_precision == "fp32" else 0)
         wl = f"vortex-160x160-p3-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
     else:
         ch = S.Channel()
@@ -219,6 +220,8 @@ def our_arm(args):
         wl = f"channel-256x128-p3-Re1000-M0.2-{args.scheme.upper()}-dt{dt:g}"
     if prec:
         wl += f"-{args.block_precision}blocks"
+    if args.jv_precision == "fp32":
+        wl += "-fp32linearjv"
     ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
     U = torch.from_numpy(U0).to(dev)
     Uprev = torch.empty_like(U)
@@ -350,14 +353,16 @@ def our_arm(args):
                          f"CFL 13.6 and tol 1e-6, {it} GMRES iterations, {secs:.1f} s), NumPy on 1 host thread"}
 
     line = {
-        "metric": METRIC if (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt)
+        "metric": METRIC if (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt
+                             and args.jv_precision == "fp64")
         else f"DOF*GMRES-iters/s ({wl})",
         "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
-                           "block_precision": args.block_precision, "workload": wl,
+                           "block_precision": args.block_precision, "jv_precision": args.jv_precision,
+                           "workload": wl,
                            "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
                            "mesh": f"{ctx.nx}x{ctx.ny}", "launch_config": tuned,
                            "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / dt) if args.workload == "vortex" else None}),
@@ -401,7 +406,8 @@ def t_end_arm(args):
     tol = args.tol
     ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else 1e-1, gmres_m=30,
                                                 gmres_max_restarts=20, block_precision=prec,
-                                                guess=args.guess))
+                                                guess=args.guess,
+                                                jv_precision=1 if args.jv_precision == "fp32" else 0))
     if not args.no_autotune:
         fr.autotune(ctx, U, 1.0 / (0.5 * dt), reps=1)
     ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=args.tol_lin)
@@ -428,7 +434,8 @@ def t_end_arm(args):
     print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
-                      "block_precision": args.block_precision, "guess": args.guess, "t_end": args.t_end,
+                      "block_precision": args.block_precision, "jv_precision": args.jv_precision,
+                      "guess": args.guess, "t_end": args.t_end,
                       "time_to_t_end_s": wall, "E_rho": err, "gmres_iters": iters,
                       "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
     return 0
@@ -448,7 +455,8 @@ def kernel_arm(args):
     X, Y = S.point_coords(xe, ye, P)
     U = torch.from_numpy(S.Vortex().state(X, Y)).cuda()
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
-    ctx = fr.Context(xe, ye, P, fr.default_opts(block_precision=prec))
+    ctx = fr.Context(xe, ye, P, fr.default_opts(block_precision=prec,
+                                                jv_precision=1 if args.jv_precision == "fp32" else 0))
     R = ctx.empty()
     fr.fr_residual(ctx, U, R)
     z = torch.from_numpy(S.random_vector(ctx.shape, 1)).cuda()
@@ -472,6 +480,7 @@ def kernel_arm(args):
     pr = fr.fr_profile_end(ctx)[args.kernel]
     us = pr["ms"] / max(pr["launches"], 1) * 1e3
     print(json.dumps({"kernel": args.kernel, "block_precision": args.block_precision,
+                      "jv_precision": args.jv_precision,
                       "launches": pr["launches"], "avg_us": us,
                       "tflops": pr["flops"] / pr["launches"] / (us * 1e-6) / 1e12,
                       "gbs": pr["bytes"] / pr["launches"] / (us * 1e-6) / 1e9,
@@ -709,6 +718,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
+    ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
+                    help="fp32: linear parts of the FD operator in FP32 (Euler only)")
     ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,

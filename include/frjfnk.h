@@ -93,6 +93,15 @@ typedef struct fr_opts {
                             fr_mlp fed [b, previous-step stage solution, previous
                             stage solution]; falls back to 1 without a model).
                             GMRES stops at tol_lin * ||b|| whatever the guess */
+  int jv_precision;      /* finite-difference operator A z (Euler residual only):
+                            0 = FP64 throughout (default, the paper's);
+                            1 = the linear parts of R(U+eps z) - R(U) -- solution and
+                            flux interpolation, derivative and correction -- in
+                            FP32 on eps z, the nonlinear pointwise and common
+                            fluxes and their differences from the cached
+                            F(U), f^num(U) in FP64.  A z then carries a relative
+                            error of ~1e-7, so use it only with tol_lin >= 1e-6
+                            (ROW at loose tolerances, ESDIRK/BDF2 inner solves) */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with
@@ -149,7 +158,9 @@ int fr_residual(fr_ctx* ctx, const double* U, double* R, void* stream);
  * Jacobian-vector product of Sec. 4.5 applied as A z with
  * A = D - dR/dq, D = shift*I (Eq. linear).  eps follows fr_opts; a zero z
  * gives y = 0.  R0 must equal R(U).  All device, ndof doubles; y must not
- * alias the inputs. */
+ * alias the inputs.  With fr_opts.jv_precision = 1 the product is formed
+ * from fluxes cached at U (recomputed by this call and at the start of every
+ * GMRES solve) instead of R0, with the linear parts in FP32. */
 int fr_jv(fr_ctx* ctx, const double* U, const double* R0, const double* z, double shift,
           double* y, void* stream);
 
@@ -215,7 +226,7 @@ int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
  * Network 3nb -> hidden -> hidden -> nb, ReLU,
  * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
  * (gradients checkable against an FP64 reference); inference runs BF16
- * operands on the tensor cores with FP32 accumulation.  GMRES judges the
+ * operands on the tcgen05 tensor cores with FP32 accumulation.  GMRES judges the
  * guess: a stage solved from it still stops at tol_lin * ||b||. */
 typedef struct fr_mlp fr_mlp;
 /* Create a model (device memory for up to max_batch samples). */
@@ -230,7 +241,10 @@ int fr_mlp_get_params(fr_mlp* m, float* host, void* stream);
 int fr_mlp_get_grads(fr_mlp* m, float* host, void* stream);
 /* Y[M][n_out] = MLP(X[M][n_in]) (device FP32 arrays, M <= max_batch);
  * bf16 = 0: FP32 training path (keeps the activations for fr_mlp_backward);
- * bf16 = 1: BF16 tensor-core inference. */
+ * bf16 = 1: BF16 inference on the 5th-generation tensor cores (tcgen05 MMA,
+ * FP32 accumulation in tensor memory; inputs and hidden activations rounded
+ * to BF16).  A GEMM whose bounded wait gave up sets a flag that the next
+ * fr_mlp_forward reports as FR_ERR_TIMEOUT. */
 int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf16, void* stream);
 /* Gradients of mean((Y - T)^2)/2 after an FP32 forward on the same X;
  * loss_host (may be NULL) receives the loss (synchronises). */

@@ -29,6 +29,9 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->blocks);
   cudaFree(c->tb);
   cudaFree(c->mst);
+  cudaFree(c->lin_fg);
+  cudaFree(c->lin_fx);
+  cudaFree(c->lin_fy);
   cudaFree(c->rloc);
   cudaFree(c->gfeat);
   for (double* p : c->bhist) cudaFree(p);
@@ -107,6 +110,11 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
     FRK_TRY(dalloc(c, &c->rloc, n));
   }
   FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
+  if (o->jv_precision == 1) {  // linearisation caches of the mixed-precision A z
+    FRK_TRY(dalloc(c, &c->lin_fg, (size_t)c->ne * 8 * c->np));
+    FRK_TRY(dalloc(c, &c->lin_fx, (size_t)c->ne * c->n1 * 12));
+    FRK_TRY(dalloc(c, &c->lin_fy, (size_t)c->ne * c->n1 * 12));
+  }
   FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
   FRK_TRY(dalloc(c, &c->z, n));
   for (double*& b : c->buf) FRK_TRY(dalloc(c, &b, n));
@@ -195,6 +203,24 @@ double residual_flops_per_element(int p) {
   return 22 * Np + 2 * 16 * N * N + 70 * 2 * N + 2 * 2 * 4 * Np * (N + 2) + 4 * Np;
 }
 
+// Navier-Stokes (BR2) residual per element, counted like the Euler one
+// (a fused multiply-add = 2): per kernel pass (trace and residual kernel
+// each) the state and its reference derivatives (8Np + 16 Np N) and the face
+// traces of (q, q_x, q_y) (96 N^2 + 32 N); per own face point (4N, each face
+// evaluated from both sides) averages and BR2 liftings (48), Rusanov (70),
+// the viscous flux (50) and the total (4); per point the corrected gradient
+// (56), the inviscid and viscous fluxes (80), the corrected divergence
+// (16 (N+2) + 4) and the body force (4).
+double ns_residual_flops_per_element(int p) {
+  const double N = p + 1, Np = N * N;
+  return 2 * (8 * Np + 16 * Np * N + 96 * N * N + 32 * N) + 4 * N * (48 + 70 + 50 + 4) +
+         Np * (56 + 80 + 4 * (16 * (N + 2) + 4) + 4);
+}
+
+double jv_flops_per_element(const fr_ctx* ctx) {
+  return ctx->viscous ? ns_residual_flops_per_element(ctx->p) : residual_flops_per_element(ctx->p);
+}
+
 // Element block: nb = 4 Np columns, each a local FD column (one pointwise
 // flux, four Rusanov fluxes, 2N x 4 entries of 3 multiply-adds) plus
 // Gauss-Jordan inversion, 2 nb^3.
@@ -233,6 +259,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->wall_temperature = 1.0;
   o->precond_refresh = 0;
   o->guess = 0;
+  o->jv_precision = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -260,8 +287,9 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
       (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1 ||
-      o.guess < 0 || o.guess > 2)
+      o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1)
     return FR_ERR_INVALID_ARG;
+  if (o.jv_precision == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->ny; ++i)
@@ -304,6 +332,7 @@ extern "C" int fr_jv(fr_ctx* ctx, const double* U, const double* R0, const doubl
   FRK_TRY(check_vec(ctx, y, "y"));
   if (y == U || y == R0 || y == z) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_jv: y aliases an input");
   cudaStream_t s = as_stream(stream);
+  FRK_TRY(launch_linearize(ctx, U, s));
   FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_NU2, s));
   FRK_TRY(launch_sumsq(ctx, z, ctx->scal + S_NZ2, s, true));
   return launch_residual(ctx, 1, U, z, R0, nullptr, y, shift, ctx->scal + S_EPS, nullptr, s);

@@ -73,6 +73,7 @@ int stage_guess(fr_ctx* ctx, const double* U, const double* R0, double shift, co
   if (!yl) return FR_OK;
   // safeguard: residuals of the learned and of the previous-step guess
   double* r = ctx->buf[B_GUESS_R];
+  FRK_TRY(launch_linearize(ctx, U, s));
   FRK_TRY(launch_sumsq(ctx, U, ctx->scal + S_NU2, s));
   FRK_TRY(launch_sumsq(ctx, x0, ctx->scal + S_NZ2, s, true));
   FRK_TRY(launch_residual(ctx, 2, U, x0, R0, b, r, shift, ctx->scal + S_EPS, nullptr, s));

@@ -127,6 +127,9 @@ struct fr_ctx {
   double* z = nullptr;       // preconditioned basis vector
   double* buf[16] = {};      // stepper buffers, ndof each
   double* scal = nullptr;    // frk::S_COUNT device scalars
+  double* lin_fg = nullptr;  // mixed A z: F(U), G(U) at the points [ne][8][np]
+  double* lin_fx = nullptr;  // mixed A z: per element's west face point (q-, q+, f^num) [ne][n1][12]
+  double* lin_fy = nullptr;  // mixed A z: per element's south face point, same layout
   int num_sms = 1;           // SMs of the device (persistent grids)
   int* kerr = nullptr;       // device flag: a kernel's bounded wait gave up
   int vec_blocks = frk::kVecBlocks;  // grid of the streaming vector kernels (autotuned)
@@ -192,11 +195,16 @@ struct ProfScope {
 
 // Algorithmic work per launch (counting rules; see the launch sites).
 double residual_flops_per_element(int p);
+double ns_residual_flops_per_element(int p);
+double jv_flops_per_element(const fr_ctx* ctx);  // Euler or Navier-Stokes
 double factor_flops_per_element(int p);
 
 // ---- launchers implemented in the .cu files --------------------------------
 // residual.cu: mode 0: out = R(U); mode 1: out = A z; mode 2: out = b - A z
 // eps2 points at the device pair (eps, 1/eps) of the product (modes 1, 2)
+// mixed-precision A z (jv_precision 1): cache F(U), G(U) and the face states
+// and common fluxes at U for the following modes 1 / 2; no-op otherwise
+int launch_linearize(fr_ctx* ctx, const double* U, cudaStream_t s);
 int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
                     const double* b, double* out, double shift, const double* eps2,
                     const int* done, cudaStream_t s);

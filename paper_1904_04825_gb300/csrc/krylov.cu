@@ -366,6 +366,7 @@ int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double s
   double* sc = ctx->scal;
   GmresDev& gd = ctx->gd;
   double* V = ctx->V;
+  FRK_TRY(launch_linearize(ctx, U, s));
   FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
   FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
   FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
@@ -403,6 +404,7 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
   GmresDev& gd = ctx->gd;
   double* V = ctx->V;
   fr_gmres_info loc{};
+  FRK_TRY(launch_linearize(ctx, U, s));
   // ||U|| for the FD step, ||b|| for the stopping test
   FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
   FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
@@ -498,7 +500,7 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
           prof_work(ctx, FR_KF_APPLY, 8.0 * (double)ctx->ne * ctx->nb * ctx->nb + 24.0 * nd, 2.0 * ctx->nb * nd);
         else
           prof_work(ctx, FR_KF_APPLY, 24.0 * nd, 3.0 * nd);
-        prof_work(ctx, FR_KF_JV, 32.0 * nd, residual_flops_per_element(ctx->p) * (double)ctx->ne + 6.0 * nd);
+        prof_work(ctx, FR_KF_JV, 32.0 * nd, jv_flops_per_element(ctx) * (double)ctx->ne + 6.0 * nd);
         // pass 1: dots of j+1 basis vectors and w with w; update reads them and w, writes w
         prof_work(ctx, FR_KF_DOTS, 8.0 * (kv + 1) * nd, 2.0 * (kv + 1) * nd);
         prof_work(ctx, FR_KF_UPDATE, 8.0 * (kv + 2) * nd, 2.0 * kv * nd + 2.0 * nd);

@@ -6,8 +6,9 @@
 //  * training path (forward with stored activations, backward, Adam): FP32
 //    tiled GEMMs on the CUDA cores, so the gradients can be checked against
 //    the FP64 oracle;
-//  * inference path: BF16 operands on the tensor cores (mma.sync m16n8k16,
-//    FP32 accumulation) with bias + ReLU fused into the epilogue.
+//  * inference path: BF16 operands on the 5th-generation tensor cores
+//    (tcgen05.mma, FP32 accumulator in tensor memory) with bias + ReLU fused
+//    into the epilogue that reads the accumulator back.
 // Loss: mean of (y - t)^2 / 2 over all outputs; Adam with bias correction.
 #include <cuda_bf16.h>
 
@@ -26,13 +27,16 @@ struct fr_mlp {
   float* G = nullptr;       // gradients (same layout)
   float* Mo = nullptr;      // Adam first moments
   float* Vo = nullptr;      // Adam second moments
-  __nv_bfloat16* P16 = nullptr;  // BF16 copy of the weights (biases stay FP32 in P)
   float* Z[3] = {};         // pre-activations [M x n[l+1]]
   float* A[2] = {};         // hidden activations [M x n[l+1]]
   float* D[3] = {};         // loss gradients w.r.t. Z
   float* part = nullptr;    // split-M partial weight gradients
-  __nv_bfloat16* X16 = nullptr;   // BF16 input / hidden activations for inference
-  __nv_bfloat16* H16[2] = {};
+  __nv_bfloat16* X16 = nullptr;   // BF16 input / hidden activations for inference,
+  __nv_bfloat16* H16[2] = {};     //   rows padded to kp[l] (16-byte rows, zero pad)
+  __nv_bfloat16* W16[3] = {};     // BF16 weights [n[l+1]][kp[l]], zero-padded columns
+  int kp[3] = {0, 0, 0};          // padded widths of the layer inputs
+  int* derr = nullptr;            // device flag: a bounded wait of the GEMM gave up
+  int* herr = nullptr;            // pinned host copy, refreshed after every inference
   double* loss = nullptr;   // device scalar
   int step = 0;
   char err[256] = {0};
@@ -103,70 +107,186 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
 }
 
 // ---- BF16 tensor-core GEMM for inference: Y = act(X W^T + b) ----
-// X [M x K] row-major BF16, W [N x K] row-major BF16, K % 16 == 0 handled by
-// zero padding in shared memory.  CTA 128 threads = 4 warps, tile 64 (rows) x
-// 64 (cols); each warp owns 16 rows x 64 cols = 8 m16n8k16 tiles.
+// 5th-generation tensor cores: one thread issues tcgen05.mma (kind::f16,
+// BF16 operands, FP32 accumulator in tensor memory), the CTA stages the
+// operands in shared memory, and the epilogue reads the accumulator back
+// with tcgen05.ld.
+//  * CTA tile 128 rows x BN (<= 256) columns, 128 threads (4 warps);
+//    K in 64-wide slices through a 2-stage shared-memory ring filled with
+//    16-byte cp.async copies (zero-filled outside the matrices), so padded
+//    rows/columns contribute exact zeros;
+//  * operands K-major without swizzle: 8-row x 16-byte core matrices, the
+//    two core matrices of one K=16 step 128 bytes apart (leading byte
+//    offset), consecutive 8-row groups 1024 bytes apart (stride byte offset);
+//  * one MMA group per slice is committed to that stage's mbarrier; a stage
+//    is refilled only after its MMAs completed; every wait is bounded and a
+//    wait that gives up sets *err, and the tensor memory is always freed.
+// X [M][kp] and W [N][kp] row-major BF16 with kp % 8 == 0 (16-byte rows).
+namespace umma {
+constexpr int BM = 128, BK = 64, STAGES = 2, MAXN = 256;
+constexpr unsigned A_BYTES = BM * BK * 2;        // 16 KB
+constexpr unsigned B_BYTES = MAXN * BK * 2;      // 32 KB
+constexpr unsigned STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 64;
+constexpr unsigned TMEM_COLS = 256;
+
+// shared-memory matrix descriptor, no swizzle, K-major
+__device__ __forceinline__ unsigned long long sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;  // descriptor version (fixed 0b001 at bits 46-48)
+  return d;         // base offset 0, absolute-offset mode off, layout 0 = no swizzle
+}
+// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr unsigned idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+__device__ __forceinline__ void cp16(unsigned dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+}  // namespace umma
+
 template <bool RELU, bool OUT_BF16>
-__global__ void __launch_bounds__(128) k_hgemm(int M, int N, int K, const __nv_bfloat16* __restrict__ X,
-                                               const __nv_bfloat16* __restrict__ W,
-                                               const float* __restrict__ bias, void* out) {
-  __shared__ __align__(16) __nv_bfloat16 Xs[64][16 + 8];
-  __shared__ __align__(16) __nv_bfloat16 Ws[64][16 + 8];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int g = lane / 4, tq = lane % 4;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  float acc[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int t = threadIdx.x; t < 64 * 16; t += 128) {
-      const int r = t / 16, kk = t % 16;
-      const int i = i0 + r, j = j0 + r, k = k0 + kk;
-      Xs[r][kk] = (i < M && k < K) ? X[(long long)i * K + k] : zero;
-      Ws[r][kk] = (j < N && k < K) ? W[(long long)j * K + k] : zero;
-    }
-    __syncthreads();
-    const int r = warp * 16;
-    unsigned a[4];
-    a[0] = *reinterpret_cast<const unsigned*>(&Xs[r + g][2 * tq]);
-    a[1] = *reinterpret_cast<const unsigned*>(&Xs[r + g + 8][2 * tq]);
-    a[2] = *reinterpret_cast<const unsigned*>(&Xs[r + g][2 * tq + 8]);
-    a[3] = *reinterpret_cast<const unsigned*>(&Xs[r + g + 8][2 * tq + 8]);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      unsigned b[2];
-      b[0] = *reinterpret_cast<const unsigned*>(&Ws[nt * 8 + g][2 * tq]);
-      b[1] = *reinterpret_cast<const unsigned*>(&Ws[nt * 8 + g][2 * tq + 8]);
-      asm volatile(
-          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-          "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-          : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(128) k_umma_gemm(int M, int N, int kp, const __nv_bfloat16* __restrict__ X,
+                                                   const __nv_bfloat16* __restrict__ W,
+                                                   const float* __restrict__ bias, void* out, int ldo,
+                                                   int* err) {
+  using namespace umma;
+  extern __shared__ __align__(1024) unsigned char usm[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(usm + STAGES * STAGE_BYTES);
+  unsigned* tslot = reinterpret_cast<unsigned*>(usm + STAGES * STAGE_BYTES + 32);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * MAXN;
+  const int ncol = min(MAXN, N - n0);           // output columns of this tile
+  const int bn = (ncol + 15) / 16 * 16;         // MMA N (multiple of 16)
+  const int nk = (kp + BK - 1) / BK;
+  const unsigned sbase = smem_u32(usm);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if (tid == 0) {
+    for (int q = 0; q < STAGES; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tslot;
+
+  // fill stage st with K slice kt: A rows m0.., B rows n0.. (16-byte chunks)
+  auto load = [&](int kt, int st) {
+    const unsigned a_s = sbase + st * STAGE_BYTES, b_s = a_s + A_BYTES;
+    const int k0 = kt * BK;
+    for (int c = tid; c < BM * (BK / 8); c += 128) {
+      const int row = c / (BK / 8), kc = c % (BK / 8);
+      const int gi = m0 + row, gk = k0 + kc * 8;
+      const bool ok = gi < M && gk < kp;
+      cp16(a_s + (row / 8) * 1024 + kc * 128 + (row % 8) * 16, ok ? (const void*)(X + (size_t)gi * kp + gk) : (const void*)X, ok);
+    }
+    for (int c = tid; c < bn * (BK / 8); c += 128) {
+      const int row = c / (BK / 8), kc = c % (BK / 8);
+      const int gj = n0 + row, gk = k0 + kc * 8;
+      const bool ok = gj < N && gk < kp;
+      cp16(b_s + (row / 8) * 1024 + kc * 128 + (row % 8) * 16, ok ? (const void*)(W + (size_t)gj * kp + gk) : (const void*)W, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  bool ok = true;
+  load(0, 0);
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int st = kt % STAGES;
+    if (kt + 1 < nk) {
+      const int nst = (kt + 1) % STAGES;
+      if (kt + 1 >= STAGES) {  // MMAs of slice kt+1-STAGES must be done with stage nst
+        const int u = (kt + 1 - STAGES) / STAGES;
+        ok = mbar_wait(&bar[nst], (unsigned)(u & 1), kWaitPolls);
+      }
+      if (!__syncthreads_and(ok)) break;
+      load(kt + 1, nst);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    // generic-proxy writes -> visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a_s = sbase + st * STAGE_BYTES, b_s = a_s + A_BYTES;
+      const unsigned id = idesc_bf16(BM, bn);
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const unsigned long long ad = sdesc(a_s + kk * 256, 128, 1024);
+        const unsigned long long bd = sdesc(b_s + kk * 256, 128, 1024);
+        const unsigned acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(id), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar[st]))
+                   : "memory");
+    }
+  }
+  // all MMAs done: the last commit tracks every MMA issued before it
+  if (ok && nk > 0) {
+    const int last = nk - 1;
+    ok = mbar_wait(&bar[last % STAGES], (unsigned)((last / STAGES) & 1), kWaitPolls);
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) {
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may land after the CTA leaves
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < bn; c0 += 16) {
+      unsigned v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = i0 + warp * 16 + g + (c >= 2 ? 8 : 0);
-      const int j = j0 + nt * 8 + 2 * tq + (c & 1);
-      if (i < M && j < N) {
-        float v = acc[nt][c] + bias[j];
-        if (RELU) v = fmaxf(v, 0.f);
-        if (OUT_BF16) reinterpret_cast<__nv_bfloat16*>(out)[(long long)i * N + j] = __float2bfloat16_rn(v);
-        else reinterpret_cast<float*>(out)[(long long)i * N + j] = v;
+        for (int q = 0; q < 16; ++q) {
+          const int j = n0 + c0 + q;
+          if (j - n0 >= bn || j >= ldo) continue;
+          float x = __uint_as_float(v[q]) + (j < N ? bias[j] : 0.f);
+          if (RELU) x = fmaxf(x, 0.f);
+          if (OUT_BF16) reinterpret_cast<__nv_bfloat16*>(out)[(size_t)row * ldo + j] = __float2bfloat16_rn(x);
+          else if (j < N) reinterpret_cast<float*>(out)[(size_t)row * ldo + j] = x;
+        }
       }
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-__global__ void k_f2bf(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16_rn(x[i]);
+// x [M][k] FP32 -> y [M][kp] BF16, zero in the padding columns
+__global__ void k_f2bf_pad(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long M, int k, int kp) {
+  const long long n = M * kp;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t / kp;
+    const int j = (int)(t % kp);
+    y[t] = j < k ? __float2bfloat16_rn(x[i * k + j]) : __float2bfloat16_rn(0.f);
+  }
 }
+
 
 // dZ_out = (y - t) / (M * n_out), loss partial sums (FP64)
 __global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ d,
@@ -244,11 +364,12 @@ unsigned grid_for(long long n) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// BF16 copies of the weights with rows padded to 16 bytes (biases stay FP32)
 int refresh_bf16(fr_mlp* m, cudaStream_t s) {
   for (int l = 0; l < 3; ++l) {
-    const long long n = (long long)m->n[l + 1] * m->n[l];
+    const long long n = (long long)m->n[l + 1] * m->kp[l];
     count_launch();
-    k_f2bf<<<grid_for(n), 256, 0, s>>>(m->P + off_W(m, l), m->P16 + off_W(m, l), n);
+    k_f2bf_pad<<<grid_for(n), 256, 0, s>>>(m->P + off_W(m, l), m->W16[l], m->n[l + 1], m->n[l], m->kp[l]);
   }
   MLP_CUDA(m, cudaGetLastError());
   return FR_OK;
@@ -256,7 +377,10 @@ int refresh_bf16(fr_mlp* m, cudaStream_t s) {
 
 void free_mlp(fr_mlp* m) {
   if (!m) return;
-  cudaFree(m->P); cudaFree(m->G); cudaFree(m->Mo); cudaFree(m->Vo); cudaFree(m->P16);
+  cudaFree(m->P); cudaFree(m->G); cudaFree(m->Mo); cudaFree(m->Vo);
+  for (auto* p : m->W16) cudaFree(p);
+  cudaFree(m->derr);
+  cudaFreeHost(m->herr);
   for (auto* p : m->Z) cudaFree(p);
   for (auto* p : m->A) cudaFree(p);
   for (auto* p : m->D) cudaFree(p);
@@ -294,20 +418,26 @@ extern "C" int fr_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, f
   if (e == cudaSuccess) e = cudaMalloc(&m->G, np * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->Mo, np * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->Vo, np * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&m->P16, np * sizeof(__nv_bfloat16));
+  for (int l = 0; l < 3; ++l) m->kp[l] = (m->n[l] + 7) / 8 * 8;
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l)
+    e = cudaMalloc(&m->W16[l], (size_t)m->n[l + 1] * m->kp[l] * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->derr, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&m->herr, sizeof(int));
+  if (e == cudaSuccess) *m->herr = 0;
   for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
     e = cudaMalloc(&m->Z[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->D[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
   }
   for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
     e = cudaMalloc(&m->A[l], (size_t)max_batch * m->n[l + 1] * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->H16[l], (size_t)max_batch * m->n[l + 1] * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&m->H16[l], (size_t)max_batch * m->kp[l + 1] * sizeof(__nv_bfloat16));
   }
   const int nparts = (max_batch + kSplitRows - 1) / kSplitRows;
   long long maxw = 0;
   for (int l = 0; l < 3; ++l) maxw = std::max(maxw, (long long)m->n[l + 1] * m->n[l]);
   if (e == cudaSuccess) e = cudaMalloc(&m->part, (size_t)nparts * maxw * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&m->X16, (size_t)max_batch * n_in * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->X16, (size_t)max_batch * m->kp[0] * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(m->Mo, 0, np * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->Vo, 0, np * sizeof(float));
@@ -363,6 +493,7 @@ extern "C" int fr_mlp_get_grads(fr_mlp* m, float* host, void* stream) {
 
 extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf16, void* stream) {
   if (!m || !X || !Y || M < 1 || M > m->max_batch) return mlp_err(m, FR_ERR_INVALID_ARG, "bad forward arguments");
+  if (*m->herr) return mlp_err(m, FR_ERR_TIMEOUT, "an earlier tensor-core GEMM gave up a bounded wait");
   cudaStream_t s = as_stream(stream);
   if (!bf16) {
     const float* in = X;
@@ -380,21 +511,33 @@ extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf
       in = C;
     }
   } else {
+    static bool attr = false;  // dynamic shared memory above 48 KB, set once per process
+    if (!attr) {
+      MLP_CUDA(m, cudaFuncSetAttribute(k_umma_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)umma::SMEM));
+      MLP_CUDA(m, cudaFuncSetAttribute(k_umma_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)umma::SMEM));
+      attr = true;
+    }
     count_launch();
-    k_f2bf<<<grid_for((long long)M * m->n[0]), 256, 0, s>>>(X, m->X16, (long long)M * m->n[0]);
+    k_f2bf_pad<<<grid_for((long long)M * m->kp[0]), 256, 0, s>>>(X, m->X16, M, m->n[0], m->kp[0]);
     const __nv_bfloat16* in = m->X16;
     for (int l = 0; l < 3; ++l) {
-      const int K = m->n[l], N = m->n[l + 1];
-      const dim3 grid((N + 63) / 64, (M + 63) / 64);
+      const int N = m->n[l + 1];
+      const dim3 grid((M + umma::BM - 1) / umma::BM, (N + umma::MAXN - 1) / umma::MAXN);
       count_launch();
       if (l < 2)
-        k_hgemm<true, true><<<grid, 128, 0, s>>>(M, N, K, in, m->P16 + off_W(m, l), m->P + off_b(m, l), m->H16[l]);
+        k_umma_gemm<true, true><<<grid, 128, umma::SMEM, s>>>(M, N, m->kp[l], in, m->W16[l], m->P + off_b(m, l),
+                                                              m->H16[l], m->kp[l + 1], m->derr);
       else
-        k_hgemm<false, false><<<grid, 128, 0, s>>>(M, N, K, in, m->P16 + off_W(m, l), m->P + off_b(m, l), Y);
+        k_umma_gemm<false, false><<<grid, 128, umma::SMEM, s>>>(M, N, m->kp[l], in, m->W16[l], m->P + off_b(m, l),
+                                                                Y, N, m->derr);
       in = l < 2 ? m->H16[l] : nullptr;
     }
   }
   MLP_CUDA(m, cudaGetLastError());
+  // the GEMMs' error flag reaches the host with the stream; the next call reports it
+  if (bf16) MLP_CUDA(m, cudaMemcpyAsync(m->herr, m->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
   return FR_OK;
 }
 

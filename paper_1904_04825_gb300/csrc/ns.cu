@@ -395,13 +395,11 @@ int ns_launch(fr_ctx* ctx, int mode, const NsArgs& a, bool perturb_trace, cudaSt
   const unsigned gt = (unsigned)((ctx->ne + E - 1) / E);
   const int fam = mode == 3 ? FR_KF_FACTOR : (mode == 0 ? FR_KF_RESIDUAL : FR_KF_JV);
   {
-    ProfScope ps_(ctx, fam, s);
+    ProfScope ps_(ctx, fam, s, wb, wf);  // one timed record for the trace + residual pair
     if (perturb_trace) k_ns_trace<P, true><<<gt, E * NP, 0, s>>>(a);
     else k_ns_trace<P, false><<<gt, E * NP, 0, s>>>(a);
-  }
-  FRK_LAUNCHED(ctx);
-  {
-    ProfScope ps_(ctx, fam, s, wb, wf);
+    FRK_LAUNCHED(ctx);
+    count_launch();  // the scope counted the trace kernel
     if (mode == 0) k_ns_res<P, 0><<<gt, E * NP, 0, s>>>(a);
     else if (mode == 1) k_ns_res<P, 1><<<gt, E * NP, 0, s>>>(a);
     else if (mode == 2) k_ns_res<P, 2><<<gt, E * NP, 0, s>>>(a);
@@ -439,7 +437,8 @@ int launch_ns_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
   const double nd = (double)ctx->ndof;
   const bool in_cycle = done != nullptr;
   const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
-  return dispatch(ctx, mode, a, mode != 0, s, wb, 0.0);
+  const double wf = in_cycle ? 0.0 : ns_residual_flops_per_element(ctx->p) * (double)ctx->ne + (mode == 0 ? 0.0 : 6.0 * nd);
+  return dispatch(ctx, mode, a, mode != 0, s, wb, wf);
 }
 
 int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {

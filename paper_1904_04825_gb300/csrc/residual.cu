@@ -33,6 +33,9 @@ struct ResArgs {
   double shift;
   double eps_rel;
   double eps_fixed;
+  double* lin_fg;  // mode 3 writes / mixed A z reads: F(U), G(U) [ne][8][NP]
+  double* lin_fx;  // per element's west face point: q-, q+, f^num (4 each) [ne][N][12]
+  double* lin_fy;  // per element's south face point, same layout
   Tables tab;
 };
 
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
   constexpr int NXF = (TX + 1) * TY * N;  // points on the tile's x-faces (normal +x)
   constexpr int NYF = (TY + 1) * TX * N;  // points on the tile's y-faces (normal +y)
-  constexpr bool PERTURB = MODE > 0;
+  constexpr bool PERTURB = MODE == 1 || MODE == 2;  // MODE 3: R's fluxes at U into the caches
   __shared__ double sq[NE][4][NP];
   __shared__ double sF[NE][4][NP];
   __shared__ double sG[NE][4][NP];
@@ -120,6 +123,10 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     for (int v = 0; v < 4; ++v) {
       sF[el][v][t] = f[v];
       sG[el][v][t] = g[v];
+      if (MODE == 3) {
+        a.lin_fg[(e * 8 + v) * NP + t] = f[v];
+        a.lin_fg[(e * 8 + 4 + v) * NP + t] = g[v];
+      }
     }
   }
   __syncthreads();
@@ -163,6 +170,15 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
       rusanov(qm, qp, 0, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfx[fy][xf][v][k] = fc[v];
+      if (MODE == 3 && xf < ax) {  // the west face of tile element xf
+        double* c = a.lin_fx + (((long long)(ix0 + xf) + (long long)a.nx * gy) * N + k) * 12;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          c[v] = qm[v];
+          c[4 + v] = qp[v];
+          c[8 + v] = fc[v];
+        }
+      }
     } else {
       const int i2 = idx - NXF;
       const int k = i2 % N, rr = i2 / N, yf = rr % (TY + 1), fx = rr / (TY + 1);
@@ -189,12 +205,21 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
       rusanov(qm, qp, 1, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfy[fx][yf][v][k] = fc[v];
+      if (MODE == 3 && yf < ay) {  // the south face of tile element yf
+        double* c = a.lin_fy + ((long long)gx + (long long)a.nx * (iy0 + yf)) * N * 12 + k * 12;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          c[v] = qm[v];
+          c[4 + v] = qp[v];
+          c[8 + v] = fc[v];
+        }
+      }
     }
   }
   __syncthreads();
 
   // ---- 3: corrected divergence and the output ----
-  if (!active) return;
+  if (MODE == 3 || !active) return;
   const double hx = a.hx[ix0 + lx], hy = a.hy[iy0 + ly];
   const int i = t % N, j = t / N;
   // with unscaled fluxes, -(1/|J|)(dF~/dxi + dG~/deta) = -(2/hx) df~ - (2/hy) dg~
@@ -222,6 +247,170 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   }
 }
 
+// A z with FP32 linear parts (jv_precision 1).  R(U+eps z) - R(U) is the
+// corrected divergence of the flux differences dF = F(U+eps z) - F(U) at the
+// points and df = f^num(U+eps z) - f^num(U) on the faces; the divergence and
+// correction are linear, so they run in FP32 on dF, df.  The nonlinear parts
+// stay FP64: the pointwise fluxes at U + eps z and their difference from the
+// cached F(U), the face states q(U) + eps trace(z) (trace of z in FP32, the
+// state itself in FP64) and the Rusanov fluxes at them, differenced against
+// the cached f^num(U).  Same element tiles as k_residual; MODE 1: A z,
+// MODE 2: b - A z.
+template <int P, int MODE, int TV>
+__global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
+  constexpr int N = P + 1, NP = N * N;
+  constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
+  constexpr int NXF = (TX + 1) * TY * N;
+  constexpr int NYF = (TY + 1) * TX * N;
+  __shared__ float sdF[NE][4][NP], sdG[NE][4][NP], sz[NE][4][NP];
+  __shared__ float strz[NE][4][4][N];         // own traces of z [face W,E,S,N][var][k]
+  __shared__ float sfx[TY][TX + 1][4][N];     // df on x-faces
+  __shared__ float sfy[TX][TY + 1][4][N];     // df on y-faces
+  __shared__ float sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+
+  if (a.done && *a.done) return;
+  if (threadIdx.x < N * N) sDt[threadIdx.x / N][threadIdx.x % N] = (float)a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
+  if (threadIdx.x < N) {
+    slm[threadIdx.x] = (float)a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = (float)a.tab.lp[threadIdx.x];
+    sdgL[threadIdx.x] = (float)a.tab.dgL[threadIdx.x];
+    sdgR[threadIdx.x] = (float)a.tab.dgR[threadIdx.x];
+  }
+  const int tiles_x = (a.nx + TX - 1) / TX;
+  const int ix0 = (int)(blockIdx.x % tiles_x) * TX, iy0 = (int)(blockIdx.x / tiles_x) * TY;
+  const int ax = min(TX, a.nx - ix0), ay = min(TY, a.ny - iy0);
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  const int lx = el % TX, ly = el / TX;
+  const bool active = el < NE && lx < ax && ly < ay;
+  const long long e = (long long)(ix0 + lx) + (long long)a.nx * (iy0 + ly);
+  const double eps = a.eps2[0], ieps = a.eps2[1];
+  // ---- 1: perturbed state, point fluxes (FP64) and their differences ----
+  if (active) {
+    const long long base = e * 4 * NP + t;
+    double q[4], f[4], g[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const long long o = base + v * NP;
+      const double zv = a.z[o];
+      q[v] = fma(eps, zv, a.U[o]);
+      sz[el][v][t] = (float)zv;
+    }
+    euler_fluxes(q, a.gam, f, g);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sdF[el][v][t] = (float)(f[v] - a.lin_fg[(e * 8 + v) * NP + t]);
+      sdG[el][v][t] = (float)(g[v] - a.lin_fg[(e * 8 + 4 + v) * NP + t]);
+    }
+  }
+  __syncthreads();
+  // ---- 2a: own traces of z (FP32) ----
+  for (int idx = threadIdx.x; idx < NE * 4 * N; idx += blockDim.x) {
+    const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
+    if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
+    const int off = face < 2 ? N * k : k;
+    const int stride = face < 2 ? 1 : N;
+    const float* c = (face == 0 || face == 2) ? slm : slp;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float s2 = c[0] * sz[e2][v][off];
+#pragma unroll
+      for (int q = 1; q < N; ++q) s2 = fmaf(c[q], sz[e2][v][off + q * stride], s2);
+      strz[e2][face][v][k] = s2;
+    }
+  }
+  __syncthreads();
+  // ---- 2b: face states q(U) + eps trace(z), Rusanov (FP64), df ----
+  for (int idx = threadIdx.x; idx < NXF + NYF; idx += blockDim.x) {
+    double qm[4], qp[4], fc[4];
+    float tzm[4], tzp[4];
+    const double* cache;
+    int dir;
+    int sx0, sx1, sx2, sx3;  // destination (row/column, face index, -, k)
+    if (idx < NXF) {
+      const int k = idx % N, rr = idx / N, xf = rr % (TX + 1), fy = rr / (TX + 1);
+      if (fy >= ay || xf > ax) continue;
+      const int gy = iy0 + fy;
+      const long long ep = (long long)((ix0 + xf) % a.nx) + (long long)a.nx * gy;  // element east of the face
+      cache = a.lin_fx + (ep * N + k) * 12;
+      if (xf >= 1) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzm[v] = strz[xf - 1 + TX * fy][1][v][k];
+      } else {
+        const long long nb = (long long)((ix0 + a.nx - 1) % a.nx) + (long long)a.nx * gy;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzm[v] = (float)trace_sum<N>(a.z + nb * 4 * NP + v * NP + N * k, 1, a.tab.lp);
+      }
+      if (xf < ax) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzp[v] = strz[xf + TX * fy][0][v][k];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzp[v] = (float)trace_sum<N>(a.z + ep * 4 * NP + v * NP + N * k, 1, a.tab.lm);
+      }
+      dir = 0; sx0 = fy; sx1 = xf; sx3 = k; sx2 = 0;
+    } else {
+      const int i2 = idx - NXF;
+      const int k = i2 % N, rr = i2 / N, yf = rr % (TY + 1), fx = rr / (TY + 1);
+      if (fx >= ax || yf > ay) continue;
+      const int gx = ix0 + fx;
+      const long long ep = (long long)gx + (long long)a.nx * ((iy0 + yf) % a.ny);  // element north of the face
+      cache = a.lin_fy + (ep * N + k) * 12;
+      if (yf >= 1) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzm[v] = strz[fx + TX * (yf - 1)][3][v][k];
+      } else {
+        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + a.ny - 1) % a.ny);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzm[v] = (float)trace_sum<N>(a.z + nb * 4 * NP + v * NP + k, N, a.tab.lp);
+      }
+      if (yf < ay) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzp[v] = strz[fx + TX * yf][2][v][k];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tzp[v] = (float)trace_sum<N>(a.z + ep * 4 * NP + v * NP + k, N, a.tab.lm);
+      }
+      dir = 1; sx0 = fx; sx1 = yf; sx3 = k; sx2 = 0;
+    }
+    (void)sx2;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      qm[v] = fma(eps, (double)tzm[v], cache[v]);
+      qp[v] = fma(eps, (double)tzp[v], cache[4 + v]);
+    }
+    rusanov(qm, qp, dir, a.gam, fc);
+    if (dir == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sfx[sx0][sx1][v][sx3] = (float)(fc[v] - cache[8 + v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sfy[sx0][sx1][v][sx3] = (float)(fc[v] - cache[8 + v]);
+    }
+  }
+  __syncthreads();
+  // ---- 3: corrected divergence of the differences (FP32), output (FP64) ----
+  if (!active) return;
+  const float sx = (float)(2.0 / a.hx[ix0 + lx]), sy = (float)(2.0 / a.hy[iy0 + ly]);
+  const int i = t % N, j = t / N;
+  const long long base = e * 4 * NP + t;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float dF = sdgL[i] * sfx[ly][lx][v][j];
+    dF = fmaf(sdgR[i], sfx[ly][lx + 1][v][j], dF);
+#pragma unroll
+    for (int k = 0; k < N; ++k) dF = fmaf(sDt[i][k], sdF[el][v][k + N * j], dF);
+    float dG = sdgL[j] * sfy[lx][ly][v][i];
+    dG = fmaf(sdgR[j], sfy[lx][ly + 1][v][i], dG);
+#pragma unroll
+    for (int k = 0; k < N; ++k) dG = fmaf(sDt[j][k], sdG[el][v][i + N * k], dG);
+    const float dR = -fmaf(sx, dF, sy * dG);  // R(U + eps z) - R(U)
+    const long long o = base + v * NP;
+    const double zo = a.z[o];
+    const double Az = eps > 0.0 ? fma(-(double)dR, ieps, a.shift * zo) : a.shift * zo;
+    a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
+  }
+}
+
 template <int P, int TV>
 int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   constexpr int NP = (P + 1) * (P + 1), TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY;
@@ -234,8 +423,12 @@ int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   const bool in_cycle = a.done != nullptr;
   const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
   const double wf = in_cycle ? 0.0 : (mode == 0 ? fl : fl + 6.0 * nd);
+  const bool mixed = ctx->opts.jv_precision == 1;
   if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 3) { ProfScope ps_(ctx, FR_KF_OTHER, s); k_residual<P, 3, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 1 && mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 1, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
   else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 2, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
   else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
@@ -258,6 +451,7 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
   a.gam = ctx->opts.gamma; a.shift = shift;
   a.eps_rel = ctx->opts.eps_rel; a.eps_fixed = ctx->opts.eps_fixed;
+  a.lin_fg = ctx->lin_fg; a.lin_fx = ctx->lin_fx; a.lin_fy = ctx->lin_fy;
   a.tab = ctx->tab;
   switch (ctx->p) {
     case 2: return launch_p<2>(ctx, mode, a, s);
@@ -265,6 +459,11 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
     case 4: return launch_p<4>(ctx, mode, a, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "degree %d not compiled", ctx->p);
   }
+}
+
+int launch_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
+  if (ctx->opts.jv_precision != 1 || ctx->viscous) return FR_OK;
+  return launch_residual(ctx, 3, U, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, s);
 }
 
 }  // namespace frk

@@ -71,3 +71,68 @@ def test_reduced_precision_run_matches_fp64_oracle(fr, prec):
         it += st.gmres_iters
         Uo, _ = o_row(prob, ROW[2](), 0.05, Uo, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
     assert np.linalg.norm(U.cpu().numpy() - Uo) / np.linalg.norm(Uo) < 1e-9
+
+
+# ------------------------------------------------- FP32 linear parts of A z --
+# jv_precision = 1: the divergence, correction and z-traces of
+# R(U + eps z) - R(U) run in FP32 on the flux differences.  Their rounding
+# (u_32 = 6e-8) is amplified by the cancellation inside the derivative
+# (coefficients up to (p+1)^2/2, smooth differences) by at most ~100, so A z
+# matches the oracle's FP64 finite-difference product to 1e-5 relative L2;
+# a wrong sign, index or missing term errs by O(1).
+TOL_JV32 = 1e-5
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("nx,ny", [(5, 4), (13, 11), (24, 7)])
+def test_mixed_jv_matches_oracle(fr, p, nx, ny):
+    from oracle.jfnk import fd_jv
+    xe, ye = S.stretched_mesh(nx, ny, seed=nx * p)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.smooth_random_state(X, Y, seed=p, amp=0.1)
+    z0 = S.random_vector(U0.shape, seed=nx + p)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(jv_precision=1))
+    U, z, Rg = _t(U0), _t(z0), _t(R0)
+    y = ctx.empty()
+    for shift in (0.0, 7.5):
+        fr.fr_jv(ctx, U, Rg, z, shift, y)
+        yo = fd_jv(prob, U0, R0, z0, shift)
+        assert np.linalg.norm(y.cpu().numpy() - yo) / np.linalg.norm(yo) < TOL_JV32
+    # a zero direction gives zero
+    fr.fr_jv(ctx, U, Rg, _t(np.zeros_like(z0)), 3.0, y)
+    assert np.array_equal(y.cpu().numpy(), np.zeros_like(z0))
+
+
+def test_mixed_jv_run_within_tolerance(fr):
+    """ROW3 steps of the 20 x 20 p = 3 vortex with the mixed A z at
+    tol_lin = 1e-8 against the FP64 oracle at tol_lin = 1e-12: the stage
+    solves converge to the mixed operator's solution, which differs from the
+    FP64 one by the A z error (1e-7 relative) times the step, so the states
+    agree to 1e-7 relative."""
+    p = 3
+    xe, ye = S.uniform_mesh(20)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-8, gmres_max_restarts=60, jv_precision=1))
+    ref = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-8, gmres_max_restarts=60))
+    U, V = _t(U0), _t(U0)
+    Uo = U0.copy()
+    for _ in range(3):
+        st = fr.step_row(ctx, 3, 0.05, U)
+        sr = fr.step_row(ref, 3, 0.05, V)
+        assert st.converged and sr.converged
+        assert abs(st.gmres_iters - sr.gmres_iters) <= 0.1 * sr.gmres_iters + 2
+        Uo, _ = o_row(prob, ROW[3](), 0.05, Uo, SolverOpts(tol_lin=1e-12, m=30, max_restarts=60))
+    assert np.linalg.norm(U.cpu().numpy() - Uo) / np.linalg.norm(Uo) < 1e-7
+
+
+def test_mixed_jv_rejected_for_navier_stokes(fr):
+    ch = S.Channel()
+    xe = np.linspace(0.0, 2.0, 5)
+    ye = S.channel_y_edges(4)
+    with pytest.raises(fr.FrError):
+        fr.Context(xe, ye, 2, fr.default_opts(jv_precision=1, mu=ch.mu, wall_temperature=ch.temperature),
+                   wall_y=True)

@@ -101,6 +101,59 @@ def test_bf16_tensor_core_inference(fr):
     assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) < 3e-2
 
 
+def _bf16_forward(params, X):
+    h = _bf16_round(X)
+    for li, (W, b) in enumerate(params):
+        z = h @ _bf16_round(W).T + b
+        h = _bf16_round(np.maximum(z, 0.0)) if li < 2 else z
+    return h
+
+
+@pytest.mark.parametrize("sizes,M", [
+    ([20, 64, 64, 7], 5),          # one partial tile everywhere (K 20 -> 24, N 7 -> 16)
+    ([300, 256, 256, 100], 1000),  # the p = 4 network shape, ragged last row tile
+    ([36, 300, 300, 17], 257),     # hidden width above one 256-column tile
+    ([108, 256, 256, 36], 128),    # exactly one row tile
+])
+def test_tensor_core_gemm_shapes(fr, sizes, M):
+    """The tcgen05 GEMMs on ragged shapes: rows, columns and K slices that
+    do not fill a tile are zero-filled, so every output matches the oracle
+    network on BF16-rounded operands (FP32 accumulation) to 1e-3."""
+    import torch
+    rng = np.random.default_rng(len(sizes) + M)
+    params = [(W.astype(np.float32).astype(np.float64), (0.1 * rng.standard_normal(b.shape)).astype(np.float32).astype(np.float64))
+              for W, b in init_params(sizes, seed=M)]
+    X = rng.standard_normal((M, sizes[0])).astype(np.float32).astype(np.float64)
+    m = fr.MLP(sizes[0], sizes[1], sizes[-1], max_batch=M)
+    m.set_params(fr.flat_params(params))
+    Y = torch.full((M, sizes[-1]), float("nan"), dtype=torch.float32, device="cuda")
+    m.forward(_f32(X), Y, bf16=True)
+    yg = Y.cpu().numpy()
+    assert np.isfinite(yg).all()
+    h = _bf16_forward(params, X)
+    assert np.linalg.norm(yg - h) / np.linalg.norm(h) < 1e-3
+    assert np.max(np.abs(yg - h)) < 1e-2 * np.max(np.abs(h))
+
+
+def test_tensor_core_gemm_full_size_sampled(fr):
+    """The largest inference (73,728 elements of a 384 x 192 p = 4 mesh,
+    300-256-256-100): 512 sampled rows against the oracle."""
+    import torch
+    sizes, M = [300, 256, 256, 100], 384 * 192
+    rng = np.random.default_rng(3)
+    params = [(W.astype(np.float32).astype(np.float64), (0.1 * rng.standard_normal(b.shape)).astype(np.float32).astype(np.float64))
+              for W, b in init_params(sizes, seed=3)]
+    X = rng.standard_normal((M, sizes[0])).astype(np.float32)
+    m = fr.MLP(300, 256, 100, max_batch=M)
+    m.set_params(fr.flat_params(params))
+    Y = torch.empty((M, 100), dtype=torch.float32, device="cuda")
+    m.forward(_f32(X), Y, bf16=True)
+    rows = np.sort(rng.choice(M, 512, replace=False))
+    yg = Y.cpu().numpy()[rows]
+    h = _bf16_forward(params, X[rows].astype(np.float64))
+    assert np.linalg.norm(yg - h) / np.linalg.norm(h) < 1e-3
+
+
 def test_learned_guess_in_row_stages(fr):
     """Train on stage solves captured from plain ROW2 steps (zero guess) of
     20 x 20, p = 2 vortices; then run a held-out vortex with the zero guess,

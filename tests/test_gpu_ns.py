@@ -173,3 +173,43 @@ def test_ns_esdirk3_step_matches_oracle(fr):
                       SolverOpts(m=30, max_restarts=60))
     assert st.converged and so.converged
     assert _rel(U.cpu().numpy(), Uo) < 1e-9
+
+
+def test_ns_residual_channel_full_size(fr):
+    """The channel workload at its full size (256 x 128, p = 3, 2.1 M DOFs,
+    first cell 1e-3, ratio 1.15) in the bench's launch configuration: every
+    output against the oracle.  R is a small difference (|R| <= 0.05) of
+    flux-derivative terms that reach 1e5-1e6 next to the walls (2/h = 2000,
+    pressure ~18), so, as for the Euler residual at full size, 1e-12 is
+    measured against the magnitude of those terms."""
+    ch = S.Channel()
+    p = 3
+    xe = np.linspace(0.0, ch.lx, 257)
+    ye = S.channel_y_edges(128, first=1e-3, ratio=1.15)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = ch.state(X, Y, seed=0)
+    ctx = fr.Context(xe, ye, p, _opts(fr, ch.mu, ch.body_force, ch.temperature), wall_y=True)
+    R = ctx.empty()
+    fr.fr_residual(ctx, _t(U0), R)
+    Ro = ns_residual(U0, Mesh(xe, ye, wall_y=True), p,
+                     Viscous(mu=ch.mu, prandtl=ch.prandtl, gx=ch.body_force, t_wall=ch.temperature))
+    d = R.cpu().numpy() - Ro
+    scale = _term_scale(U0, xe, ye, p)
+    assert np.linalg.norm(d) < 1e-12 * np.linalg.norm(scale)
+    assert np.max(np.abs(d)) < 1e-12 * np.max(scale)
+
+
+def _term_scale(U0, xe, ye, p):
+    """sJ (|D| |F| + |D| |G|) per point with the inviscid fluxes: the size of
+    the terms whose difference is R (oracle-side fluxes, test only)."""
+    from oracle.fr2d import as_grid, flux_x, flux_y, from_grid
+    m = Mesh(xe, ye)
+    b = Basis(p)
+    Q = as_grid(U0, m, p)
+    hx = m.hx[None, :, :, None, None]
+    hy = m.hy[None, :, :, None, None]
+    F = np.abs(0.5 * hy * flux_x(Q))
+    G = np.abs(0.5 * hx * flux_y(Q))
+    aD = np.abs(b.D)
+    Sg = np.einsum("ik,...jk->...ji", aD, F) + np.einsum("jk,...ki->...ji", aD, G)
+    return from_grid(Sg * 4.0 / (hx * hy), m, p)

@@ -118,6 +118,24 @@ def test_residual_vortex_full_size_c2(fr):
     assert np.max(np.abs(d)) < TOL_R * np.max(scale)
 
 
+def test_jv_vortex_full_size_c2(fr):
+    """The FD operator at 160 x 160, p = 3 (the bench's size and launch
+    configuration) against the oracle's product, all 1.6 M outputs."""
+    p = 3
+    xe, ye = S.uniform_mesh(160)
+    X, Y = S.point_coords(xe, ye, p)
+    U0 = S.Vortex().state(X, Y)
+    z0 = S.random_vector(U0.shape, seed=160)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    ctx = fr.Context(xe, ye, p)
+    y = ctx.empty()
+    shift = 1.0 / (0.435866521508459 * 0.05)
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(z0), shift, y)
+    yo = fd_jv(prob, U0, R0, z0, shift)
+    assert _rel(y.cpu().numpy(), yo) < TOL_FD
+
+
 def _term_scale(U0, xe, ye, p):
     """sJ (|D| |F| + |D| |G|) per point: magnitude of the terms whose
     difference is R (oracle-side fluxes, test only)."""
