@@ -205,7 +205,8 @@ def our_arm(args):
         U0 = S.Vortex().state(X, Y)
         p, dt, wall = P, (args.dt or DT), False
         opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
-                               jv_precision=1 if args.jv_precision == "fp32" else 0)
+                               jv_precision=1 if args.jv_precision == "fp32" else 0,
+                               riemann=1 if args.riemann == "roe" else 0)
         wl = f"vortex-160x160-p3-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
     else:
         ch = S.Channel()
@@ -222,6 +223,8 @@ def our_arm(args):
         wl += f"-{args.block_precision}blocks"
     if args.jv_precision == "fp32":
         wl += "-fp32linearjv"
+    if args.riemann == "roe":
+        wl += "-roe"
     ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
     U = torch.from_numpy(U0).to(dev)
     Uprev = torch.empty_like(U)
@@ -354,7 +357,7 @@ def our_arm(args):
 
     line = {
         "metric": METRIC if (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt
-                             and args.jv_precision == "fp64")
+                             and args.jv_precision == "fp64" and args.riemann == "rusanov")
         else f"DOF*GMRES-iters/s ({wl})",
         "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -407,7 +410,8 @@ def t_end_arm(args):
     ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else 1e-1, gmres_m=30,
                                                 gmres_max_restarts=20, block_precision=prec,
                                                 guess=args.guess,
-                                                jv_precision=1 if args.jv_precision == "fp32" else 0))
+                                                jv_precision=1 if args.jv_precision == "fp32" else 0,
+                                                riemann=1 if args.riemann == "roe" else 0))
     if not args.no_autotune:
         fr.autotune(ctx, U, 1.0 / (0.5 * dt), reps=1)
     ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=args.tol_lin)
@@ -415,17 +419,29 @@ def t_end_arm(args):
     bad = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    failed = None
     for k in range(nsteps):
-        if kind == "row":
-            st = fr.step_row(ctx, order, dt, U)
-        elif kind == "esdirk":
-            st = fr.step_esdirk(ctx, order, dt, U, ptc)
-        else:
-            st = fr.step_bdf2(ctx, dt, U, Uprev, k == 0, ptc)
+        try:
+            if kind == "ssprk":
+                st = fr.step_ssprk3(ctx, dt, U)
+            elif kind == "row":
+                st = fr.step_row(ctx, order, dt, U)
+            elif kind == "esdirk":
+                st = fr.step_esdirk(ctx, order, dt, U, ptc)
+            else:
+                st = fr.step_bdf2(ctx, dt, U, Uprev, k == 0, ptc)
+        except fr.FrError as e:  # e.g. an explicit step above its stability limit
+            failed = {"step": k, "error": str(e)}
+            break
         iters += st.gmres_iters
         bad += 0 if st.converged else 1
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    if failed:
+        print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
+                          "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 3), "steps": nsteps,
+                          "riemann": args.riemann, "failed": failed}))
+        return 0
     x, w = np.polynomial.legendre.leggauss(p + 1)
     w2 = np.outer(w, w).reshape(-1)
     exact = vort.state(X, Y, t=args.t_end)
@@ -435,7 +451,7 @@ def t_end_arm(args):
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
                       "block_precision": args.block_precision, "jv_precision": args.jv_precision,
-                      "guess": args.guess, "t_end": args.t_end,
+                      "riemann": args.riemann, "guess": args.guess, "t_end": args.t_end,
                       "time_to_t_end_s": wall, "E_rho": err, "gmres_iters": iters,
                       "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
     return 0
@@ -718,12 +734,14 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
+    ap.add_argument("--riemann", choices=["rusanov", "roe"], default="rusanov",
+                    help="common inviscid flux (roe: the paper's; Euler only)")
     ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: linear parts of the FD operator in FP32 (Euler only)")
     ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,
-                    choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2"])
+                    choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])
     ap.add_argument("--dt", type=float, default=None)
     ap.add_argument("--t-end", type=float, default=None,
                     help="vortex only: run to t_end, report time-to-t_end and E(rho)")

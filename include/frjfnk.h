@@ -102,6 +102,9 @@ typedef struct fr_opts {
                             F(U), f^num(U) in FP64.  A z then carries a relative
                             error of ~1e-7, so use it only with tol_lin >= 1e-6
                             (ROW at loose tolerances, ESDIRK/BDF2 inner solves) */
+  int riemann;           /* common inviscid flux at the faces (Sec. 3, Eq. invis_com):
+                            0 = Rusanov (default), 1 = Roe without entropy fix (the
+                            paper's); Euler residual only */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with
@@ -217,6 +220,14 @@ int step_esdirk(fr_ctx* ctx, int scheme, double dt, double* U, const fr_ptc_opts
 int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int first_step,
               const fr_ptc_opts* ptc, fr_step_stats* stats, void* stream);
 
+/* One explicit SSPRK3 step (the three-stage, third-order strong-stability-
+ * preserving Runge-Kutta scheme the paper's introduction sets the implicit
+ * schemes against): u1 = U + dt R(U), u2 = 3/4 U + 1/4 (u1 + dt R(u1)),
+ * U <- 1/3 U + 2/3 (u2 + dt R(u2)).  Three residual evaluations, no
+ * linear solves; stable only below the explicit CFL limit.  U (device) is
+ * advanced in place; FR_ERR_NONFINITE leaves it unchanged. */
+int step_ssprk3(fr_ctx* ctx, double dt, double* U, fr_step_stats* stats, void* stream);
+
 /* ---- learned initial guess (no counterpart in the paper) ---------------
  * A per-element MLP for ROW stage i of step n, features
  * [b_e/s, (b - b^{n-1})_e/s, Y_i^{n-1}_e/s] -> (Y_i^n - Y_i^{n-1})_e/s with
@@ -287,7 +298,8 @@ int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
  *    that overlap on the GPU (other streams, other host threads) race.
  *    Serialise them on one stream.
  *  - mesh: HOST edge arrays (copied on `stream`); opts may be NULL
- *    (defaults; gamma, eps_rel and eps_fixed are used).  U, R0, z, y: device,
+ *    (defaults; gamma, eps_rel, eps_fixed and riemann are used; the product
+ *    is always the FP64 Euler one).  U, R0, z, y: device,
  *    ndof doubles as for fr_jv.  Errors are reported by fr_last_error(NULL). */
 int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opts, const double* U,
                   const double* R0, const double* z, double shift, double* y, void* stream);

@@ -98,6 +98,57 @@ def rusanov(qm, qp, direction, gamma=GAMMA):
     return 0.5 * (fm + fp) - 0.5 * lam * (qp - qm)
 
 
+def roe(qm, qp, direction, gamma=GAMMA):
+    """Roe's approximate Riemann flux (the paper's common flux, Sec. 3) along
+    +x (direction 0) or +y (direction 1), without entropy fix:
+    F = (f(qm) + f(qp))/2 - sum_k |lambda_k| alpha_k r_k / 2 with the
+    eigen-decomposition of the flux Jacobian at the Roe average (density
+    weights sqrt(rho): velocity and total enthalpy H = (E + p)/rho averaged,
+    a^2 = (gamma - 1)(H - |u|^2/2)).  Waves: u_n - a, the entropy and the
+    shear wave (both u_n), u_n + a."""
+    flux = flux_x if direction == 0 else flux_y
+    fm, fp = flux(qm, gamma), flux(qp, gamma)
+    rm, rp = qm[0], qp[0]
+    um, vm, up, vp = qm[1] / rm, qm[2] / rm, qp[1] / rp, qp[2] / rp
+    pm, pp = pressure(qm, gamma), pressure(qp, gamma)
+    Hm, Hp = (qm[3] + pm) / rm, (qp[3] + pp) / rp
+    sm, sp = np.sqrt(rm), np.sqrt(rp)
+    w = 1.0 / (sm + sp)
+    u = (sm * um + sp * up) * w
+    v = (sm * vm + sp * vp) * w
+    H = (sm * Hm + sp * Hp) * w
+    rho = sm * sp
+    a2 = (gamma - 1.0) * (H - 0.5 * (u * u + v * v))
+    a = np.sqrt(a2)
+    un, dun = (u, up - um) if direction == 0 else (v, vp - vm)
+    dut = (vp - vm) if direction == 0 else (up - um)
+    drho, dp = rp - rm, pp - pm
+    al1 = (dp - rho * a * dun) / (2.0 * a2)
+    al2 = drho - dp / a2
+    al3 = rho * dut
+    al4 = (dp + rho * a * dun) / (2.0 * a2)
+    l1, l2, l4 = np.abs(un - a), np.abs(un), np.abs(un + a)
+    one = np.ones_like(u)
+    zero = np.zeros_like(u)
+    if direction == 0:
+        r1 = np.stack([one, u - a, v, H - u * a])
+        r3 = np.stack([zero, zero, one, v])
+        r4 = np.stack([one, u + a, v, H + u * a])
+    else:
+        r1 = np.stack([one, u, v - a, H - v * a])
+        r3 = np.stack([zero, one, zero, u])
+        r4 = np.stack([one, u, v + a, H + v * a])
+    r2 = np.stack([one, u, v, 0.5 * (u * u + v * v)])
+    diss = l1 * al1 * r1 + l2 * al2 * r2 + l2 * al3 * r3 + l4 * al4 * r4
+    return 0.5 * (fm + fp) - 0.5 * diss
+
+
+def common_flux(qm, qp, direction, gamma=GAMMA, riemann="rusanov"):
+    if riemann == "roe":
+        return roe(qm, qp, direction, gamma)
+    return rusanov(qm, qp, direction, gamma)
+
+
 # ----------------------------------------------------------- FR residual --
 
 def as_grid(U, mesh: Mesh, p: int):
@@ -124,7 +175,7 @@ def traces(Q, b: Basis):
     return qW, qE, qS, qN
 
 
-def local_residual(Q, hx, hy, nW, nE, nS, nN, b: Basis, gamma=GAMMA):
+def local_residual(Q, hx, hy, nW, nE, nS, nN, b: Basis, gamma=GAMMA, riemann="rusanov"):
     """R on elements given their own state Q (4, E..., n, n) and the traces the
     neighbours present on each face (nW: the west neighbour's east trace,
     etc., each (4, E..., n)).  hx, hy broadcast against E...."""
@@ -142,10 +193,10 @@ def local_residual(Q, hx, hy, nW, nE, nS, nN, b: Basis, gamma=GAMMA):
     # step 3: common fluxes; q- is the element the +x / +y normal leaves
     hy_f = hy[..., 0]
     hx_f = hx[..., 0]
-    FnW = 0.5 * hy_f * rusanov(nW, qW, 0, gamma)
-    FnE = 0.5 * hy_f * rusanov(qE, nE, 0, gamma)
-    GnS = 0.5 * hx_f * rusanov(nS, qS, 1, gamma)
-    GnN = 0.5 * hx_f * rusanov(qN, nN, 1, gamma)
+    FnW = 0.5 * hy_f * common_flux(nW, qW, 0, gamma, riemann)
+    FnE = 0.5 * hy_f * common_flux(qE, nE, 0, gamma, riemann)
+    GnS = 0.5 * hx_f * common_flux(nS, qS, 1, gamma, riemann)
+    GnN = 0.5 * hx_f * common_flux(qN, nN, 1, gamma, riemann)
     # step 4: divergence of the corrected flux
     dF = (np.einsum("ik,...jk->...ji", b.D, F)
           + (FnW - FlW)[..., :, None] * b.dgL[None, :]
@@ -167,10 +218,10 @@ def neighbour_traces(Q, b: Basis):
     return nW, nE, nS, nN
 
 
-def residual(U, mesh: Mesh, p: int, basis: Basis | None = None, gamma=GAMMA):
+def residual(U, mesh: Mesh, p: int, basis: Basis | None = None, gamma=GAMMA, riemann="rusanov"):
     """R(q) for the whole periodic mesh; U and the result are (Ne, 4, Np)."""
     b = basis or Basis(p)
     Q = as_grid(U, mesh, p)
     nW, nE, nS, nN = neighbour_traces(Q, b)
-    R = local_residual(Q, mesh.hx, mesh.hy, nW, nE, nS, nN, b, gamma)
+    R = local_residual(Q, mesh.hx, mesh.hy, nW, nE, nS, nN, b, gamma, riemann)
     return from_grid(R, mesh, p)

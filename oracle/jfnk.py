@@ -38,7 +38,10 @@ class Problem:
     """A mesh, a degree and the 1D basis: what R(q) needs.  With ``viscous``
     (an ``ns2d.Viscous``) R is the Navier-Stokes BR2 residual."""
 
-    def __init__(self, mesh: Mesh, p: int, gamma: float = 1.4, viscous=None):
+    def __init__(self, mesh: Mesh, p: int, gamma: float = 1.4, viscous=None, riemann: str = "rusanov"):
+        if viscous is not None and riemann != "rusanov":
+            raise ValueError("the Navier-Stokes residual uses the Rusanov flux")
+        self.riemann = riemann
         self.mesh = mesh
         self.p = p
         self.np = (p + 1) ** 2
@@ -57,7 +60,7 @@ class Problem:
         if self.viscous is not None:
             from .ns2d import ns_residual
             return ns_residual(U, self.mesh, self.p, self.viscous, self.basis)
-        return residual(U, self.mesh, self.p, self.basis, self.gamma)
+        return residual(U, self.mesh, self.p, self.basis, self.gamma, self.riemann)
 
 
 def fd_epsilon(U, z, eps_rel=1e-7, eps_fixed=None):
@@ -106,7 +109,7 @@ def element_jacobians(prob: Problem, U, elements=None, eps_rel=1e-7):
     args = [t[:, iy, ix] for t in (nW, nE, nS, nN)]
     hx = mesh.hx[iy, ix]
     hy = mesh.hy[iy, ix]
-    R0 = local_residual(Qe, hx, hy, *args, b, prob.gamma).reshape(4, len(elements), n * n)
+    R0 = local_residual(Qe, hx, hy, *args, b, prob.gamma, prob.riemann).reshape(4, len(elements), n * n)
     q0 = Qe.reshape(4, len(elements), n * n)
     nb = 4 * n * n
     J = np.zeros((len(elements), nb, nb))
@@ -116,7 +119,7 @@ def element_jacobians(prob: Problem, U, elements=None, eps_rel=1e-7):
         Qp = q0.copy()
         Qp[v, :, pt] += eps
         Rp = local_residual(Qp.reshape(4, len(elements), n, n), hx, hy, *args, b,
-                            prob.gamma).reshape(4, len(elements), n * n)
+                            prob.gamma, prob.riemann).reshape(4, len(elements), n * n)
         J[:, :, col] = ((Rp - R0) / eps[None, :, None]).transpose(1, 0, 2).reshape(len(elements), nb)
     return J
 

@@ -20,6 +20,11 @@
   is started; ``first_step=True`` takes one backward-Euler step
   (omega = 1, a = (1, 0)).
 
+* ``step_ssprk3``: the explicit three-stage, third-order strong-stability-
+  preserving Runge-Kutta scheme the paper's introduction contrasts the
+  implicit schemes with (Shu-Osher form: u1 = u + dt R(u),
+  u2 = 3/4 u + 1/4 (u1 + dt R(u1)), u_new = 1/3 u + 2/3 (u2 + dt R(u2))).
+
 Pins (tests/test_oracle_steppers.py): observed temporal order of every
 scheme on a smooth vortex problem at tight tolerances, BDF2 coefficients,
 rejection / halving path, agreement of ROW at tight tolerance with ESDIRK
@@ -180,3 +185,10 @@ def step_bdf2(prob: Problem, dt, U, U_prev, first_step=False, popts: PtcOpts = P
     q, _ = ptc_solve(prob, rhs, omega * dt, U, dt, popts, sopts, stats)
     stats.residual_evals = prob.n_residuals - n0
     return q, U.copy(), stats
+
+
+def step_ssprk3(prob, dt, U):
+    """One explicit SSPRK3 step (Shu-Osher form); ``prob`` needs only ``R``."""
+    u1 = U + dt * prob.R(U)
+    u2 = 0.75 * U + 0.25 * (u1 + dt * prob.R(u1))
+    return U / 3.0 + (2.0 / 3.0) * (u2 + dt * prob.R(u2))

@@ -60,7 +60,7 @@ class fr_opts(ctypes.Structure):
                 ("mu", ctypes.c_double), ("prandtl", ctypes.c_double),
                 ("body_force_x", ctypes.c_double), ("wall_temperature", ctypes.c_double),
                 ("block_precision", ctypes.c_int), ("precond_refresh", ctypes.c_int),
-                ("guess", ctypes.c_int), ("jv_precision", ctypes.c_int)]
+                ("guess", ctypes.c_int), ("jv_precision", ctypes.c_int), ("riemann", ctypes.c_int)]
 
 
 class fr_ptc_opts(ctypes.Structure):
@@ -106,6 +106,7 @@ def _load():
                             ctypes.POINTER(fr_step_stats), V]),
         "step_bdf2": (I, [P, D, P, P, I, ctypes.POINTER(fr_ptc_opts),
                           ctypes.POINTER(fr_step_stats), V]),
+        "step_ssprk3": (I, [P, D, P, ctypes.POINTER(fr_step_stats), V]),
         "fr_kernel_launches": (ctypes.c_longlong, []),
         "fr_jv_noalloc": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts), P, P, P, D, P, V]),
         "fr_mlp_create": (I, [I, I, I, I, ctypes.POINTER(ctypes.c_void_p)]),
@@ -312,6 +313,13 @@ def step_bdf2(ctx: Context, dt: float, U, U_prev, first_step: bool, ptc: fr_ptc_
                        ctypes.byref(ptc) if ptc is not None else None, ctypes.byref(st),
                        _stream(stream))
     ctx.check(rc, allow=allow)
+    return _stats(st, rc)
+
+
+def step_ssprk3(ctx: Context, dt: float, U, stream=None):
+    st = fr_step_stats()
+    rc = lib.step_ssprk3(ctx.handle, float(dt), _ptr(U), ctypes.byref(st), _stream(stream))
+    ctx.check(rc)
     return _stats(st, rc)
 
 

@@ -260,6 +260,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->precond_refresh = 0;
   o->guess = 0;
   o->jv_precision = 0;
+  o->riemann = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -287,8 +288,9 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
       (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1 ||
-      o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1)
+      o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
     return FR_ERR_INVALID_ARG;
+  if (o.riemann == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
   if (o.jv_precision == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

@@ -27,6 +27,7 @@ struct FactorArgs {
   double gam;
   double shift;
   double beps;       // block_eps_rel
+  int riemann;       // common flux: 0 Rusanov, 1 Roe
   Tables tab;
 };
 
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
       nt[(face * 4 + v) * N + k] = qn[v];
     }
     const int dir = face < 2 ? 0 : 1;
-    if (face == 0 || face == 2) rusanov(qn, qo, dir, a.gam, fc);
-    else rusanov(qo, qn, dir, a.gam, fc);
+    if (face == 0 || face == 2) riemann_flux(a.riemann, qn, qo, dir, a.gam, fc);
+    else riemann_flux(a.riemann, qo, qn, dir, a.gam, fc);
     const double sc = face < 2 ? 0.5 * hy : 0.5 * hx;
 #pragma unroll
     for (int v = 0; v < 4; ++v) fn[(face * 4 + v) * N + k] = sc * fc[v];
@@ -222,8 +223,8 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
       }
       qo[vv] = fma(cf, eps, qo[vv]);
       const int dir = face < 2 ? 0 : 1;
-      if (face == 0 || face == 2) rusanov(qn, qo, dir, a.gam, fc);
-      else rusanov(qo, qn, dir, a.gam, fc);
+      if (face == 0 || face == 2) riemann_flux(a.riemann, qn, qo, dir, a.gam, fc);
+      else riemann_flux(a.riemann, qo, qn, dir, a.gam, fc);
       const double sc = face < 2 ? 0.5 * hy : 0.5 * hx;
 #pragma unroll
       for (int v = 0; v < 4; ++v) dFn[face][v] = sc * fc[v] - fn[(face * 4 + v) * N + k];
@@ -638,6 +639,7 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
   a.U = U; a.blocks = ctx->blocks; a.mst = ctx->mst; a.hx = ctx->hx; a.hy = ctx->hy;
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
   a.gam = ctx->opts.gamma; a.shift = shift; a.beps = ctx->opts.block_eps_rel;
+  a.riemann = ctx->opts.riemann;
   a.tab = ctx->tab;
   switch (ctx->p) {
     case 2: return factor_p<2>(ctx, a, s);

@@ -114,6 +114,59 @@ __device__ __forceinline__ void write_eps(const EpsArgs& ea, double nz2) {
   ea.out[1] = eps > 0.0 ? 1.0 / eps : 0.0;
 }
 
+// Roe's approximate Riemann flux (no entropy fix) along +x (dir 0) or +y
+// (dir 1): the mean of the two fluxes minus half the sum over the four waves
+// |lambda_k| alpha_k r_k of the flux Jacobian at the Roe average
+// (sqrt(rho)-weighted velocity and total enthalpy; waves u_n - a, entropy
+// and shear at u_n, u_n + a).
+__device__ __forceinline__ void roe(const double qm[4], const double qp[4], int dir, double gam,
+                                    double out[4]) {
+  double fm[4], fp[4];
+  (void)normal_flux(qm, dir, gam, fm);
+  (void)normal_flux(qp, dir, gam, fp);
+  const double rim = 1.0 / qm[0], rip = 1.0 / qp[0];
+  const double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
+  const double pm = (gam - 1.0) * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
+  const double pp = (gam - 1.0) * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
+  const double Hm = (qm[3] + pm) * rim, Hp = (qp[3] + pp) * rip;
+  const double sm = sqrt(qm[0]), sp = sqrt(qp[0]);
+  const double w = 1.0 / (sm + sp);
+  const double u = (sm * um + sp * up) * w, v = (sm * vm + sp * vp) * w, H = (sm * Hm + sp * Hp) * w;
+  const double rho = sm * sp;
+  const double a2 = (gam - 1.0) * (H - 0.5 * (u * u + v * v));
+  const double a = sqrt(a2), ia2 = 1.0 / a2;
+  const double un = dir == 0 ? u : v;
+  const double dun = dir == 0 ? up - um : vp - vm;
+  const double dut = dir == 0 ? vp - vm : up - um;
+  const double dr = qp[0] - qm[0], dp = pp - pm;
+  const double al1 = 0.5 * (dp - rho * a * dun) * ia2;
+  const double al2 = dr - dp * ia2;
+  const double al3 = rho * dut;
+  const double al4 = 0.5 * (dp + rho * a * dun) * ia2;
+  const double l1 = fabs(un - a) * al1, l2 = fabs(un) * al2, l3 = fabs(un) * al3, l4 = fabs(un + a) * al4;
+  const double k2 = 0.5 * (u * u + v * v);
+  double d[4];
+  d[0] = l1 + l2 + l4;
+  if (dir == 0) {
+    d[1] = l1 * (u - a) + l2 * u + l4 * (u + a);
+    d[2] = (l1 + l2 + l4) * v + l3;
+    d[3] = l1 * (H - u * a) + l2 * k2 + l3 * v + l4 * (H + u * a);
+  } else {
+    d[1] = (l1 + l2 + l4) * u + l3;
+    d[2] = l1 * (v - a) + l2 * v + l4 * (v + a);
+    d[3] = l1 * (H - v * a) + l2 * k2 + l3 * u + l4 * (H + v * a);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] = 0.5 * (fm[k] + fp[k]) - 0.5 * d[k];
+}
+
+// the common inviscid flux selected by fr_opts.riemann (0 Rusanov, 1 Roe)
+__device__ __forceinline__ void riemann_flux(int kind, const double qm[4], const double qp[4], int dir,
+                                             double gam, double out[4]) {
+  if (kind == 1) roe(qm, qp, dir, gam, out);
+  else rusanov(qm, qp, dir, gam, out);
+}
+
 // ---- asynchronous bulk copies (TMA engine) with mbarrier completion ----
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -249,26 +250,71 @@ __global__ void __launch_bounds__(128) k_umma_gemm(int M, int N, int kp, const _
     if (tid == 0) atomicExch(err, 1);
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < bn; c0 += 16) {
-      unsigned v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+    // Accumulator -> bias, activation, output type -> a row-major tile of 64
+    // rows in the (now idle) stage buffers, then coalesced 16-byte row
+    // stores; two passes (warps 0-1, then warps 2-3) keep the staged tile
+    // within the stage buffers for FP32 output too.
+    using OutT = typename std::conditional<OUT_BF16, __nv_bfloat16, float>::type;
+    constexpr int ES = (int)sizeof(OutT);
+    const int pitch = bn * ES + 16;  // bytes per staged row (+16 spreads the banks)
+    unsigned char* tile = usm;
+    const int wcols = min(bn, ldo - n0);  // output columns of this tile
+    const bool vec = ((ldo * ES) % 16 == 0) && ((wcols * ES) % 16 == 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((warp >> 1) == pass) {
+        const int lrow = (warp & 1) * 32 + lane;  // row within the pass
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+          unsigned v[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          float x[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int j = n0 + c0 + q;
-          if (j - n0 >= bn || j >= ldo) continue;
-          float x = __uint_as_float(v[q]) + (j < N ? bias[j] : 0.f);
-          if (RELU) x = fmaxf(x, 0.f);
-          if (OUT_BF16) reinterpret_cast<__nv_bfloat16*>(out)[(size_t)row * ldo + j] = __float2bfloat16_rn(x);
-          else if (j < N) reinterpret_cast<float*>(out)[(size_t)row * ldo + j] = x;
+          for (int q = 0; q < 16; ++q) {
+            const int j = n0 + c0 + q;
+            x[q] = __uint_as_float(v[q]) + (j < N ? bias[j] : 0.f);
+            if (RELU) x[q] = fmaxf(x[q], 0.f);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(tile + (size_t)lrow * pitch + (size_t)c0 * ES);
+          if (OUT_BF16) {
+            unsigned w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+              w[q] = *reinterpret_cast<const unsigned*>(&h);
+            }
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_uint4(__float_as_uint(x[4 * q]), __float_as_uint(x[4 * q + 1]), __float_as_uint(x[4 * q + 2]),
+                                  __float_as_uint(x[4 * q + 3]));
+          }
         }
       }
+      __syncthreads();
+      const int r0 = m0 + pass * 64;
+      const int rows = max(0, min(64, M - r0));
+      if (vec) {
+        const int cpr = wcols * ES / 16;  // 16-byte chunks per row
+        for (int c = tid; c < rows * cpr; c += 128) {
+          const int r = c / cpr, k = c % cpr;
+          const uint4 val = *reinterpret_cast<const uint4*>(tile + (size_t)r * pitch + k * 16);
+          *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(out) + ((size_t)(r0 + r) * ldo + n0) * ES +
+                                    k * 16) = val;
+        }
+      } else {
+        for (int c = tid; c < rows * wcols; c += 128) {
+          const int r = c / wcols, k = c % wcols;
+          reinterpret_cast<OutT*>(out)[(size_t)(r0 + r) * ldo + n0 + k] =
+              reinterpret_cast<const OutT*>(tile + (size_t)r * pitch)[k];
+        }
+      }
+      __syncthreads();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

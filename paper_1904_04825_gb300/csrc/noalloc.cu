@@ -113,10 +113,12 @@ extern "C" int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opt
   fr_opts o;
   fr_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.gamma > 1.0) || !(o.eps_rel > 0.0)) {
-    set_static_error("fr_jv_noalloc: bad gamma or eps_rel");
+  if (!(o.gamma > 1.0) || !(o.eps_rel > 0.0) || o.riemann < 0 || o.riemann > 1) {
+    set_static_error("fr_jv_noalloc: bad gamma, eps_rel or riemann");
     return FR_ERR_INVALID_ARG;
   }
+  o.jv_precision = 0;  // the FP32-linear-parts product needs per-context caches
+  o.mu = 0.0;          // Euler residual
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     set_static_error("fr_jv_noalloc: cudaGetDevice failed");

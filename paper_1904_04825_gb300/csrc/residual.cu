@@ -36,6 +36,7 @@ struct ResArgs {
   double* lin_fg;  // mode 3 writes / mixed A z reads: F(U), G(U) [ne][8][NP]
   double* lin_fx;  // per element's west face point: q-, q+, f^num (4 each) [ne][N][12]
   double* lin_fy;  // per element's south face point, same layout
+  int riemann;     // common flux: 0 Rusanov, 1 Roe
   Tables tab;
 };
 
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
         for (int v = 0; v < 4; ++v)
           qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slm, eps);
       }
-      rusanov(qm, qp, 0, a.gam, fc);
+      riemann_flux(a.riemann, qm, qp, 0, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfx[fy][xf][v][k] = fc[v];
       if (MODE == 3 && xf < ax) {  // the west face of tile element xf
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
         for (int v = 0; v < 4; ++v)
           qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slm, eps);
       }
-      rusanov(qm, qp, 1, a.gam, fc);
+      riemann_flux(a.riemann, qm, qp, 1, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfy[fx][yf][v][k] = fc[v];
       if (MODE == 3 && yf < ay) {  // the south face of tile element yf
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
       qm[v] = fma(eps, (double)tzm[v], cache[v]);
       qp[v] = fma(eps, (double)tzp[v], cache[4 + v]);
     }
-    rusanov(qm, qp, dir, a.gam, fc);
+    riemann_flux(a.riemann, qm, qp, dir, a.gam, fc);
     if (dir == 0) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfx[sx0][sx1][v][sx3] = (float)(fc[v] - cache[8 + v]);
@@ -452,6 +453,7 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
   a.gam = ctx->opts.gamma; a.shift = shift;
   a.eps_rel = ctx->opts.eps_rel; a.eps_fixed = ctx->opts.eps_fixed;
   a.lin_fg = ctx->lin_fg; a.lin_fx = ctx->lin_fx; a.lin_fy = ctx->lin_fy;
+  a.riemann = ctx->opts.riemann;
   a.tab = ctx->tab;
   switch (ctx->p) {
     case 2: return launch_p<2>(ctx, mode, a, s);

@@ -457,6 +457,47 @@ extern "C" int step_bdf2(fr_ctx* ctx, double dt, double* U, double* U_prev, int 
   return FR_OK;
 }
 
+extern "C" int step_ssprk3(fr_ctx* ctx, double dt, double* U, fr_step_stats* stats, void* stream) {
+  if (!ctx || !U) return set_error(ctx, FR_ERR_INVALID_ARG, "step_ssprk3: null argument");
+  if (!(dt > 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "step_ssprk3: dt must be > 0");
+  cudaStream_t s = as_stream(stream);
+  fr_step_stats st{};
+  st.converged = 1;
+  double* u1 = ctx->buf[B_STAGE];
+  double* u2 = ctx->buf[B_Q];
+  double* r = ctx->buf[B_RSTAGE];
+  // u1 = U + dt R(U)
+  FRK_TRY(launch_residual(ctx, 0, U, nullptr, nullptr, nullptr, r, 0.0, nullptr, nullptr, s));
+  {
+    const double* xs[2] = {U, r};
+    const double cs[2] = {1.0, dt};
+    FRK_TRY(launch_lincomb(ctx, u1, 2, xs, cs, nullptr, s));
+  }
+  // u2 = 3/4 U + 1/4 u1 + dt/4 R(u1)
+  FRK_TRY(launch_residual(ctx, 0, u1, nullptr, nullptr, nullptr, r, 0.0, nullptr, nullptr, s));
+  {
+    const double* xs[3] = {U, u1, r};
+    const double cs[3] = {0.75, 0.25, 0.25 * dt};
+    FRK_TRY(launch_lincomb(ctx, u2, 3, xs, cs, nullptr, s));
+  }
+  // U_new = 1/3 U + 2/3 u2 + 2 dt/3 R(u2), checked before it overwrites U
+  FRK_TRY(launch_residual(ctx, 0, u2, nullptr, nullptr, nullptr, r, 0.0, nullptr, nullptr, s));
+  {
+    const double* xs[3] = {U, u2, r};
+    const double cs[3] = {1.0 / 3.0, 2.0 / 3.0, 2.0 * dt / 3.0};
+    FRK_TRY(launch_lincomb(ctx, ctx->buf[B_NEW], 3, xs, cs, ctx->scal + S_NX2, s));
+  }
+  st.residual_evals = 3;
+  double nn;
+  FRK_TRY(read_scalar(ctx, ctx->scal + S_NX2, &nn, s));
+  if (stats) *stats = st;
+  if (!std::isfinite(nn)) return set_error(ctx, FR_ERR_NONFINITE, "step_ssprk3: new state not finite");
+  FRK_TRY(launch_copy(ctx, U, ctx->buf[B_NEW], s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->hist_row = 0;
+  return FR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batches of independent instances (uneven meshes and degrees) advanced
 // together: the per-instance kernels of each phase run concurrently on one

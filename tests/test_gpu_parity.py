@@ -440,3 +440,78 @@ def test_step_esdirk_refresh_every_iterate_matches_oracle(fr):
                       PtcOpts(tol_nl=1e-12, tol_lin=1e-3, refresh="iterate"), TIGHT)
     assert st.converged and so.converged
     assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_step_ssprk3_matches_oracle(fr, p):
+    """Explicit SSPRK3 steps on a jittered mesh: only the rounding of three
+    residual evaluations per step differs, 1e-12 after five steps."""
+    from oracle.steppers import step_ssprk3 as o_ssprk3
+    xe, ye, X, Y = _case("stretched", 9, 7, p, seed=p)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p)
+    U = _t(U0)
+    Uo = U0.copy()
+    dt = 0.2 * 10.0 / 9 / (3 * math.sqrt(2) * (p + 1))  # CFL 0.2 on the mean cell
+    for _ in range(5):
+        st = fr.step_ssprk3(ctx, dt, U)
+        assert st.residual_evals == 3
+        Uo = o_ssprk3(prob, dt, Uo)
+    assert _rel(U.cpu().numpy(), Uo) < 1e-12
+
+
+# ------------------------------------------------------- Roe common flux --
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_roe_residual_jv_blocks_match_oracle(fr, p):
+    """riemann = 1 (the paper's Roe flux): R(U), the FD operator (FP64 and
+    with FP32 linear parts) and the element blocks against the oracle with
+    the Roe flux, at the tolerances of the Rusanov tests."""
+    from oracle.jfnk import fd_jv
+    xe, ye, X, Y = _case("stretched", 11, 9, p, seed=20 + p)
+    U0 = S.smooth_random_state(X, Y, seed=40 + p, amp=0.1)
+    z0 = S.random_vector(U0.shape, seed=41 + p)
+    prob = Problem(Mesh(xe, ye), p, riemann="roe")
+    Ro = prob.R(U0)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(riemann=1))
+    U, z = _t(U0), _t(z0)
+    R = ctx.empty()
+    fr.fr_residual(ctx, U, R)
+    assert _rel(R.cpu().numpy(), Ro) < TOL_R
+    # and it differs from the Rusanov residual
+    assert _rel(Problem(Mesh(xe, ye), p).R(U0), Ro) > 1e-6
+    y = ctx.empty()
+    fr.fr_jv(ctx, U, _t(Ro), z, 5.0, y)
+    yo = fd_jv(prob, U0, Ro, z0, 5.0)
+    assert _rel(y.cpu().numpy(), yo) < TOL_FD
+    mix = fr.Context(xe, ye, p, fr.default_opts(riemann=1, jv_precision=1))
+    fr.fr_jv(mix, U, _t(Ro), z, 5.0, y)
+    assert _rel(y.cpu().numpy(), yo) < 1e-5
+    # element blocks through their action z = M^-1 r
+    shift = 40.0
+    fr.ejacobi_factor(ctx, U, None, shift)
+    r0 = S.random_vector(U0.shape, seed=43 + p)
+    zg = ctx.empty()
+    fr.ejacobi_apply(ctx, _t(r0), zg)
+    zo = ElementJacobi(element_blocks(prob, U0, shift))(r0)
+    assert _rel(zg.cpu().numpy(), zo) < TOL_FD
+
+
+def test_roe_step_row_matches_oracle(fr):
+    p = 2
+    xe, ye, X, Y = _case("uniform", 6, 6, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p, riemann="roe")
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=40, riemann=1))
+    U = _t(U0)
+    Uo = U0.copy()
+    for _ in range(2):
+        assert fr.step_row(ctx, 3, 0.1, U).converged
+        Uo, _ = o_row(prob, ROW[3](), 0.1, Uo, TIGHT)
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
+
+
+def test_roe_rejected_for_navier_stokes(fr):
+    xe, ye = np.linspace(0.0, 2.0, 5), S.channel_y_edges(4)
+    with pytest.raises(fr.FrError):
+        fr.Context(xe, ye, 2, fr.default_opts(riemann=1, mu=0.01, wall_temperature=1.0), wall_y=True)

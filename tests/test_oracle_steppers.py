@@ -7,7 +7,7 @@ import pytest
 import synthetic as S
 from oracle.fr2d import Mesh
 from oracle.jfnk import Problem
-from oracle.steppers import PtcOpts, SolverOpts, step_bdf2, step_esdirk, step_row
+from oracle.steppers import PtcOpts, SolverOpts, step_bdf2, step_esdirk, step_row, step_ssprk3
 from oracle.tableaus import ESDIRK, ROW
 
 
@@ -98,3 +98,33 @@ def test_ptc_converges_loose_tolerances(vortex):
     U1, st = step_esdirk(prob, ESDIRK[3](), 0.1, U0, popts, SolverOpts())
     assert st.converged and st.rejections == 0
     assert np.all(np.isfinite(U1))
+
+
+class _Linear:
+    """R(u) = A u (a fixed non-normal matrix)."""
+
+    def __init__(self, A):
+        self.A = A
+
+    def R(self, U):
+        return self.A @ U
+
+
+def test_ssprk3_is_the_third_order_taylor_polynomial_on_linear_problems():
+    """Any three-stage third-order Runge-Kutta scheme advances u' = A u by
+    exactly (I + hA + (hA)^2/2 + (hA)^3/6) u."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((6, 6)) + np.triu(rng.standard_normal((6, 6)), 1) * 3.0
+    u = rng.standard_normal(6)
+    h = 0.07
+    hA = h * A
+    want = u + hA @ u + hA @ (hA @ u) / 2.0 + hA @ (hA @ (hA @ u)) / 6.0
+    got = step_ssprk3(_Linear(A), h, u)
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+def test_ssprk3_temporal_order(vortex):
+    prob, U0 = vortex
+    step = lambda U, Up, dt, k: (step_ssprk3(prob, dt, U), None)
+    errs, rates = _rate(step, U0, 0.4, (16, 32, 64), 512)
+    assert 2.7 < rates[-1] < 3.4, (errs, rates)
