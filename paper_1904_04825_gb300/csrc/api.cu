@@ -28,6 +28,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->hy);
   cudaFree(c->blocks);
   cudaFree(c->tb);
+  cudaFree(c->fb);
   cudaFree(c->mst);
   cudaFree(c->lin_fg);
   cudaFree(c->lin_fx);
@@ -107,6 +108,7 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   c->viscous = (o->mu > 0.0 || c->wall_y) ? 1 : 0;
   if (c->viscous) {
     FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 4 * c->n1 * 4 * 3));
+    FRK_TRY(dalloc(c, &c->fb, (size_t)c->ne * 3 * c->n1 * 8));
     FRK_TRY(dalloc(c, &c->rloc, n));
   }
   FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));

@@ -127,6 +127,7 @@ struct fr_ctx {
   double* z = nullptr;       // preconditioned basis vector
   double* buf[16] = {};      // stepper buffers, ndof each
   double* scal = nullptr;    // frk::S_COUNT device scalars
+  double* fb = nullptr;      // Navier-Stokes face data [ne][3][n1][8] (q_com, f_n)
   double* lin_fg = nullptr;  // mixed A z: F(U), G(U) at the points [ne][8][np]
   double* lin_fx = nullptr;  // mixed A z: per element's west face point (q-, q+, f^num) [ne][n1][12]
   double* lin_fy = nullptr;  // mixed A z: per element's south face point, same layout

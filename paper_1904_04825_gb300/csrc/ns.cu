@@ -31,6 +31,7 @@ struct NsArgs {
   const double* b;
   double* out;
   double* tb;          // traces [ne][4 faces][N][4 vars][3] = (q, q_x, q_y)
+  double* fb;          // common data per element's W, S (and top-wall N) face [ne][3][N][8] = (q_com, f_n)
   const double* hx;
   const double* hy;
   const double* eps2;
@@ -368,9 +369,193 @@ __global__ void __launch_bounds__(256) k_ns_res(const NsArgs a) {
   }
 }
 
+// Modes 0-2 in two passes so every face's common data is formed once:
+// k_ns_face: one thread per (element, face W or S, point): q_com and the
+//   common total flux from the two traces in the trace buffer (or the wall
+//   state), into the face buffer; top-row elements also form their north
+//   wall face.
+// k_ns_cell: per element the FR-corrected gradient with q_com of its four
+//   faces, the point fluxes, the corrected divergence with the common fluxes
+//   of its four faces (W, S own; E, N the neighbours' W, S), body force and
+//   the output.  Both elements of a face read the same stored flux, so
+//   conservation holds to round-off.
+template <int P>
+__global__ void __launch_bounds__(256) k_ns_face(const NsArgs a) {
+  constexpr int N = P + 1;
+  constexpr double cbr2 = (P + 1) * (P + 2) / 2.0;
+  if (a.done && *a.done) return;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = a.ne * 3 * N;
+  if (tid >= total) return;
+  const int k = (int)(tid % N);
+  const int slot = (int)((tid / N) % 3);  // 0: west face, 1: south face, 2: north wall
+  const long long e = tid / (3 * N);
+  const int ix = (int)(e % a.nx), iy = (int)(e / a.nx);
+  if (slot == 2 && !(a.wall_y && iy == a.ny - 1)) return;
+  const double hx = a.hx[ix], hy = a.hy[iy];
+  double o[4][3], nb[4][3], qc[4], fn[4];
+  const int oface = slot == 0 ? 0 : (slot == 1 ? 2 : 3);
+  const double* src = a.tb + (((e * 4 + oface) * N + k) * 4) * 3;
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[v][c] = src[v * 3 + c];
+  if (slot == 2) {
+    wall_flux(o, false, hy, cbr2, a, qc, fn);
+  } else if (slot == 1 && a.wall_y && iy == 0) {
+    wall_flux(o, true, hy, cbr2, a, qc, fn);
+  } else {
+    long long nbe;
+    double hn;
+    int nface;
+    if (slot == 0) { const int jx = (ix + a.nx - 1) % a.nx; nbe = jx + (long long)a.nx * iy; nface = 1; hn = a.hx[jx]; }
+    else { const int jy = (iy + a.ny - 1) % a.ny; nbe = ix + (long long)a.nx * jy; nface = 3; hn = a.hy[jy]; }
+    const double* ns = a.tb + (((nbe * 4 + nface) * N + k) * 4) * 3;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nb[v][c] = ns[v * 3 + c];
+    common_flux(nb, o, slot == 0 ? 0 : 1, hn, slot == 0 ? hx : hy, cbr2, a, qc, fn);
+  }
+  double* dst = a.fb + ((e * 3 + slot) * N + k) * 8;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    dst[v] = qc[v];
+    dst[4 + v] = fn[v];
+  }
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) k_ns_cell(const NsArgs a) {
+  constexpr int N = P + 1, NP = N * N, E = NsSlots<P>::E;
+  constexpr bool PERTURB = MODE == 1 || MODE == 2;
+  __shared__ double sq[E][4 * NP], dxi[E][4 * NP], deta[E][4 * NP];
+  __shared__ double cq[E][4][N][4];    // q_com on the own faces [W,E,S,N]
+  __shared__ double tq[E][4][N][4];    // own face traces of q
+  __shared__ double fnum[E][4][N][4];  // common total flux on the own faces
+  __shared__ double sD[N][N], sDt[N][N], sdgL[N], sdgR[N];
+  if (a.done && *a.done) return;
+  if (threadIdx.x < N * N) {
+    sD[threadIdx.x / N][threadIdx.x % N] = a.tab.D[threadIdx.x / N][threadIdx.x % N];
+    sDt[threadIdx.x / N][threadIdx.x % N] = a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
+  }
+  if (threadIdx.x < N) {
+    sdgL[threadIdx.x] = a.tab.dgL[threadIdx.x];
+    sdgR[threadIdx.x] = a.tab.dgR[threadIdx.x];
+  }
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  const long long e = (long long)blockIdx.x * E + el;
+  const bool active = el < E && e < a.ne;
+  double eps = 0.0, ieps = 0.0;
+  if (PERTURB) {
+    eps = a.eps2[0];
+    ieps = a.eps2[1];
+  }
+  int ix = 0, iy = 0;
+  double hx = 1.0, hy = 1.0;
+  if (active) {
+    ix = (int)(e % a.nx);
+    iy = (int)(e / a.nx);
+    hx = a.hx[ix];
+    hy = a.hy[iy];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const long long o = e * 4 * NP + v * NP + t;
+      sq[el][v * NP + t] = PERTURB ? fma(eps, a.z[o], a.U[o]) : a.U[o];
+    }
+    // own traces of q and the common data of the four faces
+    for (int fp = t; fp < 4 * N; fp += NP) {
+      const int face = fp / N, k = fp % N;
+      const double* tr = a.tb + (((e * 4 + face) * N + k) * 4) * 3;
+      long long fe;
+      int fs;
+      if (face == 0) { fe = e; fs = 0; }
+      else if (face == 2) { fe = e; fs = 1; }
+      else if (face == 1) { fe = (long long)((ix + 1) % a.nx) + (long long)a.nx * iy; fs = 0; }
+      else if (a.wall_y && iy == a.ny - 1) { fe = e; fs = 2; }
+      else { fe = (long long)ix + (long long)a.nx * ((iy + 1) % a.ny); fs = 1; }
+      const double* fd = a.fb + ((fe * 3 + fs) * N + k) * 8;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        tq[el][face][k][v] = tr[v * 3];
+        cq[el][face][k][v] = fd[v];
+        fnum[el][face][k][v] = fd[4 + v];
+      }
+    }
+  }
+  __syncthreads();
+  const int i = t % N, j = t / N;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double d1 = 0.0, d2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        d1 = fma(sD[i][k], sq[el][v * NP + k + N * j], d1);
+        d2 = fma(sD[j][k], sq[el][v * NP + i + N * k], d2);
+      }
+      dxi[el][v * NP + t] = d1;
+      deta[el][v * NP + t] = d2;
+    }
+  }
+  __syncthreads();
+  const double sx = 2.0 / hx, sy = 2.0 / hy;
+  // corrected gradient and total flux at the own point (overwrites dxi / deta)
+  if (active) {
+    double q[4], gxv[4], gyv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      q[v] = sq[el][v * NP + t];
+      double dx = dxi[el][v * NP + t];
+      dx = fma(cq[el][0][j][v] - tq[el][0][j][v], sdgL[i], dx);
+      dx = fma(cq[el][1][j][v] - tq[el][1][j][v], sdgR[i], dx);
+      double dy = deta[el][v * NP + t];
+      dy = fma(cq[el][2][i][v] - tq[el][2][i][v], sdgL[j], dy);
+      dy = fma(cq[el][3][i][v] - tq[el][3][i][v], sdgR[j], dy);
+      gxv[v] = sx * dx;
+      gyv[v] = sy * dy;
+    }
+    double f[4], g[4], fv[4], gv[4];
+    euler_fluxes(q, a.gam, f, g);
+    visc_flux(q, gxv, gyv, a.gam, a.mu, a.kappa, fv, gv);
+    // each thread reads and overwrites only its own point
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      dxi[el][v * NP + t] = f[v] - fv[v];
+      deta[el][v * NP + t] = g[v] - gv[v];
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const long long base = e * 4 * NP + t;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double dF = sdgL[i] * fnum[el][0][j][v];
+    dF = fma(sdgR[i], fnum[el][1][j][v], dF);
+#pragma unroll
+    for (int k = 0; k < N; ++k) dF = fma(sDt[i][k], dxi[el][v * NP + k + N * j], dF);
+    double dG = sdgL[j] * fnum[el][2][i][v];
+    dG = fma(sdgR[j], fnum[el][3][i][v], dG);
+#pragma unroll
+    for (int k = 0; k < N; ++k) dG = fma(sDt[j][k], deta[el][v * NP + i + N * k], dG);
+    double R = -fma(sx, dF, sy * dG);
+    if (v == 1) R = fma(sq[el][t], a.gx, R);
+    if (v == 3) R = fma(sq[el][NP + t], a.gx, R);
+    const long long o = base + v * NP;
+    if (MODE == 0) {
+      a.out[o] = R;
+    } else {
+      const double zo = a.z[o];
+      const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
+      a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
+    }
+  }
+}
+
 NsArgs make_args(fr_ctx* ctx) {
   NsArgs a{};
   a.tb = ctx->tb;
+  a.fb = ctx->fb;
   a.hx = ctx->hx;
   a.hy = ctx->hy;
   a.ne = ctx->ne;
@@ -400,10 +585,17 @@ int ns_launch(fr_ctx* ctx, int mode, const NsArgs& a, bool perturb_trace, cudaSt
     else k_ns_trace<P, false><<<gt, E * NP, 0, s>>>(a);
     FRK_LAUNCHED(ctx);
     count_launch();  // the scope counted the trace kernel
-    if (mode == 0) k_ns_res<P, 0><<<gt, E * NP, 0, s>>>(a);
-    else if (mode == 1) k_ns_res<P, 1><<<gt, E * NP, 0, s>>>(a);
-    else if (mode == 2) k_ns_res<P, 2><<<gt, E * NP, 0, s>>>(a);
-    else k_ns_res<P, 3><<<(unsigned)((ctx->ne * NB + E - 1) / E), E * NP, 0, s>>>(a);
+    if (mode == 3) {
+      k_ns_res<P, 3><<<(unsigned)((ctx->ne * NB + E - 1) / E), E * NP, 0, s>>>(a);
+    } else {
+      const long long nf = ctx->ne * 3 * (P + 1);
+      k_ns_face<P><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(a);
+      FRK_LAUNCHED(ctx);
+      count_launch();
+      if (mode == 0) k_ns_cell<P, 0><<<gt, E * NP, 0, s>>>(a);
+      else if (mode == 1) k_ns_cell<P, 1><<<gt, E * NP, 0, s>>>(a);
+      else k_ns_cell<P, 2><<<gt, E * NP, 0, s>>>(a);
+    }
   }
   FRK_LAUNCHED(ctx);
   return FR_OK;

@@ -72,7 +72,7 @@ template <> struct Tile<3, 1> { static constexpr int TX = 8, TY = 2; };
 template <> struct Tile<4, 0> { static constexpr int TX = 3, TY = 3; };
 template <> struct Tile<4, 1> { static constexpr int TX = 5, TY = 2; };
 
-template <int P, int MODE, int TV>
+template <int P, int MODE, int TV, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   constexpr int N = P + 1, NP = N * N;
   constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
         for (int v = 0; v < 4; ++v)
           qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slm, eps);
       }
-      riemann_flux(a.riemann, qm, qp, 0, a.gam, fc);
+      riemann_flux(RM, qm, qp, 0, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfx[fy][xf][v][k] = fc[v];
       if (MODE == 3 && xf < ax) {  // the west face of tile element xf
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
         for (int v = 0; v < 4; ++v)
           qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slm, eps);
       }
-      riemann_flux(a.riemann, qm, qp, 1, a.gam, fc);
+      riemann_flux(RM, qm, qp, 1, a.gam, fc);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfy[fx][yf][v][k] = fc[v];
       if (MODE == 3 && yf < ay) {  // the south face of tile element yf
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
 // state itself in FP64) and the Rusanov fluxes at them, differenced against
 // the cached f^num(U).  Same element tiles as k_residual; MODE 1: A z,
 // MODE 2: b - A z.
-template <int P, int MODE, int TV>
+template <int P, int MODE, int TV, int RM>
 __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
   constexpr int N = P + 1, NP = N * N;
   constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
       qm[v] = fma(eps, (double)tzm[v], cache[v]);
       qp[v] = fma(eps, (double)tzp[v], cache[4 + v]);
     }
-    riemann_flux(a.riemann, qm, qp, dir, a.gam, fc);
+    riemann_flux(RM, qm, qp, dir, a.gam, fc);
     if (dir == 0) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) sfx[sx0][sx1][v][sx3] = (float)(fc[v] - cache[8 + v]);
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
   }
 }
 
-template <int P, int TV>
-int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
+template <int P, int TV, int RM>
+int launch_pvr(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   constexpr int NP = (P + 1) * (P + 1), TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY;
   const long long grid = (long long)((ctx->nx + TX - 1) / TX) * ((ctx->ny + TY - 1) / TY);
   const dim3 blk(TX * TY * NP);
@@ -425,14 +425,20 @@ int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
   const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
   const double wf = in_cycle ? 0.0 : (mode == 0 ? fl : fl + 6.0 * nd);
   const bool mixed = ctx->opts.jv_precision == 1;
-  if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else if (mode == 3) { ProfScope ps_(ctx, FR_KF_OTHER, s); k_residual<P, 3, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else if (mode == 1 && mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 1, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else if (mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 2, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
-  else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2, TV><<<(unsigned)grid, blk, 0, s>>>(a); }
+  if (mode == 0) { ProfScope ps_(ctx, FR_KF_RESIDUAL, s, wb, wf); k_residual<P, 0, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 3) { ProfScope ps_(ctx, FR_KF_OTHER, s); k_residual<P, 3, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 1 && mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 1, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mode == 1) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 1, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else if (mixed) { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_jv32<P, 2, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
+  else { ProfScope ps_(ctx, FR_KF_JV, s, wb, wf); k_residual<P, 2, TV, RM><<<(unsigned)grid, blk, 0, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+// the common flux is a template parameter so each flux gets its own register allocation
+template <int P, int TV>
+int launch_pv(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
+  return a.riemann == 1 ? launch_pvr<P, TV, 1>(ctx, mode, a, s) : launch_pvr<P, TV, 0>(ctx, mode, a, s);
 }
 
 template <int P>
