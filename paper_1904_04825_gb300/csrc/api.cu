@@ -206,17 +206,17 @@ double residual_flops_per_element(int p) {
 }
 
 // Navier-Stokes (BR2) residual per element, counted like the Euler one
-// (a fused multiply-add = 2): per kernel pass (trace and residual kernel
-// each) the state and its reference derivatives (8Np + 16 Np N) and the face
-// traces of (q, q_x, q_y) (96 N^2 + 32 N); per own face point (4N, each face
-// evaluated from both sides) averages and BR2 liftings (48), Rusanov (70),
-// the viscous flux (50) and the total (4); per point the corrected gradient
-// (56), the inviscid and viscous fluxes (80), the corrected divergence
-// (16 (N+2) + 4) and the body force (4).
+// (a fused multiply-add = 2) from the method's steps, each once: the state
+// and its reference derivatives (8Np + 16 Np N), the face traces of
+// (q, q_x, q_y) (96 N^2 + 32 N); per face point, with each face shared by
+// two elements (2N per element), averages and BR2 liftings (48), Rusanov
+// (70), the viscous flux (50) and the total (4); per point the corrected
+// gradient (56), the inviscid and viscous fluxes and their difference (80),
+// the corrected divergence (16 (N+2) + 4) and the body force (4).
 double ns_residual_flops_per_element(int p) {
   const double N = p + 1, Np = N * N;
-  return 2 * (8 * Np + 16 * Np * N + 96 * N * N + 32 * N) + 4 * N * (48 + 70 + 50 + 4) +
-         Np * (56 + 80 + 4 * (16 * (N + 2) + 4) + 4);
+  return 8 * Np + 16 * Np * N + 96 * N * N + 32 * N + 2 * N * (48 + 70 + 50 + 4) +
+         Np * (56 + 80 + 16 * (N + 2) + 4 + 4);
 }
 
 double jv_flops_per_element(const fr_ctx* ctx) {
