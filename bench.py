@@ -397,18 +397,21 @@ def t_end_arm(args):
     kind, order = args.scheme[:-1], int(args.scheme[-1])
     nx = args.nx or NX
     p = args.p or P
-    xe, ye = S.uniform_mesh(nx)
+    L = args.box
+    box = (-L / 2, L / 2, -L / 2, L / 2)
+    xe, ye = S.uniform_mesh(nx, box=box)
     X, Y = S.point_coords(xe, ye, p)
     vort = S.Vortex()
-    U = torch.from_numpy(vort.state(X, Y)).cuda()
+    U = torch.from_numpy(vort.state(X, Y, box=box)).cuda()
     Uprev = torch.empty_like(U)
-    h = 10.0 / nx
+    h = L / nx
     dt = args.dt if args.dt else args.cfl * h / (3 * math.sqrt(2) * (p + 1))
     nsteps = int(round(args.t_end / dt))
     dt = args.t_end / nsteps
     tol = args.tol
-    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else 1e-1, gmres_m=30,
-                                                gmres_max_restarts=20, block_precision=prec,
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else args.tol_lin,
+                                                gmres_m=args.gmres_m, gmres_max_restarts=20,
+                                                eps_fixed=args.eps_fixed, block_precision=prec,
                                                 guess=args.guess,
                                                 jv_precision=1 if args.jv_precision == "fp32" else 0,
                                                 riemann=1 if args.riemann == "roe" else 0))
@@ -438,16 +441,18 @@ def t_end_arm(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if failed:
-        print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
+        print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": args.scheme.upper(), "dt": dt,
+                      "gmres_m": args.gmres_m, "eps_fixed": args.eps_fixed,
                           "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 3), "steps": nsteps,
                           "riemann": args.riemann, "failed": failed}))
         return 0
     x, w = np.polynomial.legendre.leggauss(p + 1)
     w2 = np.outer(w, w).reshape(-1)
-    exact = vort.state(X, Y, t=args.t_end)
+    exact = vort.state(X, Y, t=args.t_end, box=box)
     rho = U[:, 0].cpu().numpy()
-    err = math.sqrt(np.sum((exact[:, 0] - rho) ** 2 * w2[None, :]) * (h * h / 4) / 100.0)
-    print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}", "scheme": args.scheme.upper(), "dt": dt,
+    err = math.sqrt(np.sum((exact[:, 0] - rho) ** 2 * w2[None, :]) * (h * h / 4) / (L * L))
+    print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": args.scheme.upper(), "dt": dt,
+                      "gmres_m": args.gmres_m, "eps_fixed": args.eps_fixed,
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
                       "block_precision": args.block_precision, "jv_precision": args.jv_precision,
@@ -751,6 +756,9 @@ def main():
     ap.add_argument("--tol-lin", type=float, default=1e-1, help="--t-end: ESDIRK/BDF2 GMRES tolerance")
     ap.add_argument("--guess", type=int, default=0, choices=[0, 1],
                     help="--t-end, ROW: stage-solve initial guess (0 zero, 1 previous step's)")
+    ap.add_argument("--box", type=float, default=10.0, help="--t-end: side of the periodic square")
+    ap.add_argument("--gmres-m", type=int, default=30, help="--t-end: GMRES restart length (<= 31)")
+    ap.add_argument("--eps-fixed", type=float, default=0.0, help="--t-end: fixed FD step (the paper's 1e-8)")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     args = ap.parse_args()
