@@ -410,7 +410,8 @@ def t_end_arm(args):
     dt = args.t_end / nsteps
     tol = args.tol
     ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else args.tol_lin,
-                                                gmres_m=args.gmres_m, gmres_max_restarts=20,
+                                                gmres_m=args.gmres_m, m_max=max(30, args.gmres_m),
+                                                gmres_max_restarts=20,
                                                 eps_fixed=args.eps_fixed, block_precision=prec,
                                                 guess=args.guess,
                                                 jv_precision=1 if args.jv_precision == "fp32" else 0,
@@ -757,7 +758,7 @@ def main():
     ap.add_argument("--guess", type=int, default=0, choices=[0, 1],
                     help="--t-end, ROW: stage-solve initial guess (0 zero, 1 previous step's)")
     ap.add_argument("--box", type=float, default=10.0, help="--t-end: side of the periodic square")
-    ap.add_argument("--gmres-m", type=int, default=30, help="--t-end: GMRES restart length (<= 31)")
+    ap.add_argument("--gmres-m", type=int, default=30, help="--t-end: GMRES restart length (<= 63; the paper's 60)")
     ap.add_argument("--eps-fixed", type=float, default=0.0, help="--t-end: fixed FD step (the paper's 1e-8)")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)

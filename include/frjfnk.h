@@ -61,7 +61,8 @@ typedef struct fr_mesh_desc {
 /* Options (fill with fr_default_opts first). */
 typedef struct fr_opts {
   double gamma;          /* ratio of specific heats, 1.4 (Sec. 2) */
-  int m_max;             /* largest GMRES restart length the workspace holds (30) */
+  int m_max;             /* largest GMRES restart length the workspace holds (30; at
+                            most 63, so the paper's GMRES(60) fits) */
   double eps_rel;        /* FD Jv step eps = eps_rel (1 + ||U||_2) / ||z||_2 (1e-7) */
   double eps_fixed;      /* > 0: fixed eps instead (the paper's 1e-8, Sec. 4.5) */
   double block_eps_rel;  /* element-block FD step eps_j = block_eps_rel (1 + |U_j|) (1e-7) */
@@ -289,7 +290,7 @@ int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
  * up front, or code that must not allocate after start-up (cudaMalloc can
  * synchronise the device and fail under memory pressure).
  *  - Working memory is one fixed static device array inside the library
- *    (about 250 KB, held on every GPU that loads the library until the
+ *    (about 365 KB, held on every GPU that loads the library until the
  *    process exits).  It limits the mesh to 2 <= nx, ny <= 4096; larger
  *    meshes are rejected with FR_ERR_INVALID_ARG.  p must be 2, 3 or 4.
  *  - The first call on a device looks up the array's device address (with

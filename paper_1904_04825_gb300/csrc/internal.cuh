@@ -13,7 +13,7 @@ namespace frk {
 
 constexpr int kMaxN = 5;          // p <= 4
 constexpr int kThreads = 256;     // default block size of the vector kernels
-constexpr int kMaxVec = 32;       // largest Krylov basis slice handled per call (m_max + 1)
+constexpr int kMaxVec = 64;       // largest Krylov basis slice handled per call (m_max + 1)
 constexpr int kVecBlocks = 456;   // default grid of the streaming vector kernels (3 x 152 SMs)
 constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
 

@@ -257,6 +257,29 @@ def test_gmres_matches_oracle(fr, precond):
     assert abs(rg - ro) <= 1e-3 * ro + 1e-9 * np.linalg.norm(b0)
 
 
+def test_gmres_paper_restart_length_60(fr):
+    """The paper's GMRES(60) (restart lengths up to 63 fit the workspace):
+    the same answer and iteration count as the oracle's GMRES(60)."""
+    p = 2
+    xe, ye, X, Y = _case("stretched", 7, 6, p, seed=60)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    R0 = prob.R(U0)
+    b0 = S.random_vector(U0.shape, 60)
+    shift = 2.0
+    ctx = fr.Context(xe, ye, p, fr.default_opts(m_max=60, gmres_m=60))
+    U = _t(U0)
+    fr.ejacobi_factor(ctx, U, None, shift)
+    x = ctx.empty().zero_()
+    info = fr.gmres_solve(ctx, U, _t(R0), shift, _t(b0), x, m=60, rtol=1e-11, max_restarts=20)
+    assert info.converged and info.iters > 30
+    A = lambda v: fd_jv(prob, U0, R0, v, shift)
+    xo, io = gmres(A, b0, None, 60, 1e-11, 20, ElementJacobi(element_blocks(prob, U0, shift)))
+    assert io.converged
+    assert abs(info.iters - io.iters) <= 3
+    assert _rel(x.cpu().numpy(), xo) < 1e-7
+
+
 @pytest.mark.parametrize("eta", [0.0, 1.0 / 64.0, 1.0])
 def test_gmres_orthogonalisation_variants_track_mgs(fr, eta):
     """One classical Gram-Schmidt pass (eta = 0), the selective second pass
