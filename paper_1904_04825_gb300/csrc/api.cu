@@ -281,7 +281,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
   *out = nullptr;
   if (!mesh || !mesh->x_edges || !mesh->y_edges || mesh->nx < 2 || mesh->ny < 2)
     return FR_ERR_INVALID_ARG;
-  if (p < 2 || p > 4) return FR_ERR_UNSUPPORTED;
+  if (p < 2 || p > 6) return FR_ERR_UNSUPPORTED;
   fr_opts o;
   fr_default_opts(&o);
   if (opts) o = *opts;
@@ -294,6 +294,9 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
     return FR_ERR_INVALID_ARG;
   if (o.riemann == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
   if (o.jv_precision == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
+  // degrees 5 and 6: Euler residual only; p = 6 FP64 blocks (196 x 196) exceed shared memory
+  if (p > 4 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;
+  if (p == 6 && o.precond && o.block_precision == 0) return FR_ERR_UNSUPPORTED;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->ny; ++i)

@@ -47,6 +47,8 @@ struct FactorLayout {
                                   NB * sizeof(int) + 64;
 };
 
+constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA
+
 template <typename S> struct StoreT;
 template <> struct StoreT<double> { __device__ static double to(double x) { return x; } };
 template <> struct StoreT<float> { __device__ static float to(float x) { return x; } };
@@ -321,6 +323,12 @@ template <> struct ApplyShape<100, float> { static constexpr int KS = 2, NS = 3;
 template <> struct ApplyShape<36, __nv_bfloat16> { static constexpr int KS = 4, NS = 8; };
 template <> struct ApplyShape<64, __nv_bfloat16> { static constexpr int KS = 2, NS = 6; };
 template <> struct ApplyShape<100, __nv_bfloat16> { static constexpr int KS = 2, NS = 4; };
+template <> struct ApplyShape<144, double> { static constexpr int KS = 1, NS = 1; };
+template <> struct ApplyShape<144, float> { static constexpr int KS = 1, NS = 2; };
+template <> struct ApplyShape<144, __nv_bfloat16> { static constexpr int KS = 1, NS = 4; };
+template <> struct ApplyShape<196, double> { static constexpr int KS = 1, NS = 1; };  // does not fit: rejected
+template <> struct ApplyShape<196, float> { static constexpr int KS = 1, NS = 1; };
+template <> struct ApplyShape<196, __nv_bfloat16> { static constexpr int KS = 1, NS = 2; };
 
 template <int NB, typename S, typename A>
 struct ApplyLayout {
@@ -508,6 +516,10 @@ __global__ void k_solupdate_plain(const double* __restrict__ V, long long ldv, c
 template <int P, typename T, typename S>
 int factor_pts(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
   using L = FactorLayout<P, T>;
+  if constexpr (L::BYTES > kSmemMax) {
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "FP64 element blocks of degree %d exceed shared memory; "
+                     "use block_precision 1 or 2", P);
+  }
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_factor<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)L::BYTES));
   // work: read U (8 B/DOF), write ne nb^2 entries of S; flops per element as counted
@@ -545,6 +557,9 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
   const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
   using L = ApplyLayout<NB, S, A>;
+  if constexpr (L::BYTES > kSmemMax) {
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "element blocks of %d rows in this precision exceed shared memory", NB);
+  }
   static int per_sm = 0;  // resident CTAs per SM (function attribute set once per process)
   if (per_sm == 0) {
     FRK_CUDA(ctx, cudaFuncSetAttribute(k_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
@@ -599,7 +614,10 @@ unsigned vec_grid(const fr_ctx* ctx, long long n) {
 
 template <int NB, typename T, typename S>
 int invert_nbts(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
-  const size_t bytes = (size_t)(NB * (NB + 1) + NB) * sizeof(T) + NB * sizeof(int) + 64;
+  constexpr size_t bytes = (size_t)(NB * (NB + 1) + NB) * sizeof(T) + NB * sizeof(int) + 64;
+  if constexpr (bytes > kSmemMax) {
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "element blocks of %d rows in this precision exceed shared memory", NB);
+  }
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_invert<NB, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)bytes));
   { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, 2.0 * NB * NB * (double)NB * (double)ctx->ne);
@@ -622,6 +640,8 @@ int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStrea
     case 36: return invert_nb<36>(ctx, mst, dshift, s);
     case 64: return invert_nb<64>(ctx, mst, dshift, s);
     case 100: return invert_nb<100>(ctx, mst, dshift, s);
+    case 144: return invert_nb<144>(ctx, mst, dshift, s);
+    case 196: return invert_nb<196>(ctx, mst, dshift, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }
@@ -645,6 +665,8 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
     case 2: return factor_p<2>(ctx, a, s);
     case 3: return factor_p<3>(ctx, a, s);
     case 4: return factor_p<4>(ctx, a, s);
+    case 5: return factor_p<5>(ctx, a, s);
+    case 6: return factor_p<6>(ctx, a, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "degree %d not compiled", ctx->p);
   }
 }
@@ -664,6 +686,8 @@ int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, d
     case 36: return apply_nb<36>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 64: return apply_nb<64>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 100: return apply_nb<100>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 144: return apply_nb<144>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 196: return apply_nb<196>(ctx, r, scale, z, sumsq, done, s, with_eps);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }
@@ -679,6 +703,8 @@ int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
     case 36: return solupdate_nb<36>(ctx, x, s);
     case 64: return solupdate_nb<64>(ctx, x, s);
     case 100: return solupdate_nb<100>(ctx, x, s);
+    case 144: return solupdate_nb<144>(ctx, x, s);
+    case 196: return solupdate_nb<196>(ctx, x, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }

@@ -11,7 +11,7 @@
 
 namespace frk {
 
-constexpr int kMaxN = 5;          // p <= 4
+constexpr int kMaxN = 7;          // p <= 6 (Euler); p <= 4 with viscous terms
 constexpr int kThreads = 256;     // default block size of the vector kernels
 constexpr int kMaxVec = 64;       // largest Krylov basis slice handled per call (m_max + 1)
 constexpr int kVecBlocks = 456;   // default grid of the streaming vector kernels (3 x 152 SMs)

@@ -71,6 +71,10 @@ template <> struct Tile<3, 0> { static constexpr int TX = 4, TY = 4; };
 template <> struct Tile<3, 1> { static constexpr int TX = 8, TY = 2; };
 template <> struct Tile<4, 0> { static constexpr int TX = 3, TY = 3; };
 template <> struct Tile<4, 1> { static constexpr int TX = 5, TY = 2; };
+template <> struct Tile<5, 0> { static constexpr int TX = 2, TY = 3; };
+template <> struct Tile<5, 1> { static constexpr int TX = 3, TY = 2; };
+template <> struct Tile<6, 0> { static constexpr int TX = 2, TY = 2; };
+template <> struct Tile<6, 1> { static constexpr int TX = 5, TY = 1; };
 
 template <int P, int MODE, int TV, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
@@ -465,6 +469,8 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
     case 2: return launch_p<2>(ctx, mode, a, s);
     case 3: return launch_p<3>(ctx, mode, a, s);
     case 4: return launch_p<4>(ctx, mode, a, s);
+    case 5: return launch_p<5>(ctx, mode, a, s);
+    case 6: return launch_p<6>(ctx, mode, a, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "degree %d not compiled", ctx->p);
   }
 }

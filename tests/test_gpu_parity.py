@@ -538,3 +538,51 @@ def test_roe_rejected_for_navier_stokes(fr):
     xe, ye = np.linspace(0.0, 2.0, 5), S.channel_y_edges(4)
     with pytest.raises(fr.FrError):
         fr.Context(xe, ye, 2, fr.default_opts(riemann=1, mu=0.01, wall_temperature=1.0), wall_y=True)
+
+
+# ------------------------------------------------- degrees 5 and 6 (Euler) --
+@pytest.mark.parametrize("p", [5, 6])
+def test_high_degree_residual_jv_blocks_match_oracle(fr, p):
+    """p = 5, 6 (the paper's P6 vortex runs): R(U) and A z at the usual
+    tolerances; the element-Jacobi action with FP64 blocks at p = 5 (1e-6)
+    and FP32 blocks at p = 6 (196 x 196 FP64 blocks do not fit in shared
+    memory; FP32 Gauss-Jordan: 1e-4, as for the other reduced-precision
+    tests)."""
+    xe, ye, X, Y = _case("stretched", 7, 5, p, seed=50 + p)
+    U0 = S.smooth_random_state(X, Y, seed=60 + p, amp=0.1)
+    z0 = S.random_vector(U0.shape, seed=61 + p)
+    prob = Problem(Mesh(xe, ye), p, riemann="roe")
+    R0 = prob.R(U0)
+    prec = 0 if p == 5 else 1
+    ctx = fr.Context(xe, ye, p, fr.default_opts(riemann=1, block_precision=prec))
+    U = _t(U0)
+    R = ctx.empty()
+    fr.fr_residual(ctx, U, R)
+    assert _rel(R.cpu().numpy(), R0) < TOL_R
+    y = ctx.empty()
+    fr.fr_jv(ctx, U, _t(R0), _t(z0), 4.0, y)
+    assert _rel(y.cpu().numpy(), fd_jv(prob, U0, R0, z0, 4.0)) < TOL_FD
+    shift = 40.0
+    fr.ejacobi_factor(ctx, U, None, shift)
+    r0 = S.random_vector(U0.shape, seed=62 + p)
+    zg = ctx.empty()
+    fr.ejacobi_apply(ctx, _t(r0), zg)
+    zo = ElementJacobi(element_blocks(prob, U0, shift))(r0)
+    assert _rel(zg.cpu().numpy(), zo) < (TOL_FD if p == 5 else 1e-4)
+
+
+def test_degree_6_step_matches_oracle_and_fp64_blocks_rejected(fr):
+    p = 6
+    xe, ye, X, Y = _case("uniform", 4, 4, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    with pytest.raises(fr.FrError):
+        fr.Context(xe, ye, p, fr.default_opts(block_precision=0))
+    prob = Problem(Mesh(xe, ye), p, riemann="roe")
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=1e-12, gmres_max_restarts=40, riemann=1,
+                                                block_precision=1))
+    U = _t(U0)
+    Uo = U0.copy()
+    for _ in range(2):
+        assert fr.step_row(ctx, 3, 0.2, U).converged
+        Uo, _ = o_row(prob, ROW[3](), 0.2, Uo, TIGHT)
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN
