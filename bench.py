@@ -450,15 +450,17 @@ def t_end_arm(args):
     x, w = np.polynomial.legendre.leggauss(p + 1)
     w2 = np.outer(w, w).reshape(-1)
     exact = vort.state(X, Y, t=args.t_end, box=box)
-    rho = U[:, 0].cpu().numpy()
+    Uh = U.cpu().numpy()
+    rho = Uh[:, 0]
     err = math.sqrt(np.sum((exact[:, 0] - rho) ** 2 * w2[None, :]) * (h * h / 4) / (L * L))
+    err_u = math.sqrt(np.sum((exact[:, 1] / exact[:, 0] - Uh[:, 1] / rho) ** 2 * w2[None, :]) * (h * h / 4) / (L * L))
     print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": args.scheme.upper(), "dt": dt,
                       "gmres_m": args.gmres_m, "eps_fixed": args.eps_fixed,
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
                       "block_precision": args.block_precision, "jv_precision": args.jv_precision,
                       "riemann": args.riemann, "guess": args.guess, "t_end": args.t_end,
-                      "time_to_t_end_s": wall, "E_rho": err, "gmres_iters": iters,
+                      "time_to_t_end_s": wall, "E_rho": err, "E_u": err_u, "gmres_iters": iters,
                       "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
     return 0
 
