@@ -34,7 +34,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("nx,ny,p", [(0, 4, 2), (1, 4, 2), (4, 1, 3), (4, 4, 1), (4, 4, 5)])
+@pytest.mark.parametrize("nx,ny,p", [(0, 4, 2), (1, 4, 2), (4, 1, 3), (4, 4, 1), (4, 4, 7)])
 def test_degenerate_meshes_and_degrees_rejected(fr, nx, ny, p):
     xe = np.linspace(-1, 1, nx + 1) if nx > 0 else np.zeros(1)
     ye = np.linspace(-1, 1, ny + 1)
