@@ -52,7 +52,7 @@ def test_radau_correction_end_values_and_slope(p):
     assert abs(dgr[1] - (p + 1) ** 2 / 2.0) < 1e-12
 
 
-@pytest.mark.parametrize("p", range(1, 6))
+@pytest.mark.parametrize("p", range(1, 7))
 def test_radau_g_dg_orthogonal_to_degree_p_minus_1(p):
     """g_L is the right Radau polynomial: orthogonal to P_{p-1} and below."""
     xq, wq = np.polynomial.legendre.leggauss(p + 4)
@@ -61,7 +61,7 @@ def test_radau_g_dg_orthogonal_to_degree_p_minus_1(p):
         assert abs(np.dot(wq, g * xq ** k)) < 1e-13
 
 
-@pytest.mark.parametrize("p", range(1, 6))
+@pytest.mark.parametrize("p", range(1, 7))
 def test_fr_dg_identity(p):
     """With g_DG on Gauss points the FR correction equals the DG lifting:
     sum_i w_i l_m(x_i) g_L'(x_i) = -l_m(-1) for every basis function."""

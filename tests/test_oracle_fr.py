@@ -18,7 +18,7 @@ def _mesh(kind, nx, ny, seed=0):
     return S.stretched_mesh(nx, ny, seed=seed)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("kind", ["uniform", "stretched"])
 def test_free_stream_preserved(p, kind):
     xe, ye = _mesh(kind, 5, 4, seed=p)
@@ -29,7 +29,7 @@ def test_free_stream_preserved(p, kind):
     assert np.max(np.abs(R)) < 1e-13 * 10
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 def test_discrete_conservation(p):
     xe, ye = S.stretched_mesh(6, 5, seed=3)
     X, Y = S.point_coords(xe, ye, p)
