@@ -1,21 +1,21 @@
 // Viscous (Navier-Stokes) FR residual with BR2 common gradients, Sec. 2-3
 // (Eqs. com_q, com_grad_q and the BR2 lifting with g'(+-1) = +-(P+1)(P+2)/2).
 //
-// Two kernels per evaluation:
+// R(U), A z and b - A z take three kernels:
 //  k_ns_trace: per element, the (possibly perturbed) state and its own
 //    polynomial gradient traced to the 4 (p+1) face points -> trace buffer.
-//  k_ns_res:   per element slot, own traces recomputed from the state (same
-//    arithmetic as k_ns_trace), neighbour traces read from the buffer;
-//    common solution, BR2 common gradient and common total flux
-//    (Rusanov inviscid minus viscous) on every face point; FR-corrected
-//    gradient and total flux at the solution points; corrected divergence;
-//    body-force source.  The two elements of a face evaluate its common flux
-//    from the same (left, right) data in the same order, so conservation
-//    holds to round-off.
-// Mode 3 of k_ns_res forms element-Jacobi columns: slot = (element, column
-// c), own state perturbed in DOF c by eps_c = beps (1 + |q_c|), neighbour
-// traces frozen at the unperturbed state; column c of shift*I - J_ee is
-// staged for the inversion kernel.
+//  k_ns_face:  per west / south face point (and north wall), the common
+//    solution, BR2 common gradient and common total flux (Rusanov inviscid
+//    minus viscous) from the two traces -> face buffer, each face once.
+//  k_ns_cell:  per element, the FR-corrected gradient and total flux at the
+//    solution points, the corrected divergence with the four faces' common
+//    fluxes, the body-force source and the output.  Both elements of a face
+//    read the same stored flux, so conservation holds to round-off.
+// Element-Jacobi columns use k_ns_res (its mode 3) after a trace pass of the
+// unperturbed state: slot = (element, column c), own state perturbed in DOF
+// c by eps_c = beps (1 + |q_c|), own traces recomputed, neighbour traces
+// frozen; it forms the element's four face fluxes itself and stages column c
+// of shift*I - J_ee for the inversion kernel.
 // Walls (isothermal, no slip) at the y ends: boundary state
 // (rho_int, 0, 0, rho_int R T_w / (gamma - 1)), common gradient = own
 // gradient + own lifting, inviscid wall flux g(q_b).  Gas constant R = 1.
