@@ -413,7 +413,7 @@ def t_end_arm(args):
                                                 gmres_m=args.gmres_m, m_max=max(30, args.gmres_m),
                                                 gmres_max_restarts=20,
                                                 eps_fixed=args.eps_fixed, block_precision=prec,
-                                                guess=args.guess,
+                                                guess=args.guess, precond_refresh=args.precond_refresh,
                                                 jv_precision=1 if args.jv_precision == "fp32" else 0,
                                                 riemann=1 if args.riemann == "roe" else 0))
     if not args.no_autotune:
@@ -459,7 +459,8 @@ def t_end_arm(args):
                       "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
                       "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
                       "block_precision": args.block_precision, "jv_precision": args.jv_precision,
-                      "riemann": args.riemann, "guess": args.guess, "t_end": args.t_end,
+                      "riemann": args.riemann, "guess": args.guess,
+                      "precond_refresh": args.precond_refresh, "t_end": args.t_end,
                       "time_to_t_end_s": wall, "E_rho": err, "E_u": err_u, "gmres_iters": iters,
                       "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
     return 0
@@ -759,6 +760,8 @@ def main():
     ap.add_argument("--tol-lin", type=float, default=1e-1, help="--t-end: ESDIRK/BDF2 GMRES tolerance")
     ap.add_argument("--guess", type=int, default=0, choices=[0, 1],
                     help="--t-end, ROW: stage-solve initial guess (0 zero, 1 previous step's)")
+    ap.add_argument("--precond-refresh", type=int, default=0, choices=[0, 1, 2],
+                    help="--t-end: ESDIRK/BDF2 element-Jacobi refresh (0 per stage + re-invert, 1 per iterate, 2 frozen)")
     ap.add_argument("--box", type=float, default=10.0, help="--t-end: side of the periodic square")
     ap.add_argument("--gmres-m", type=int, default=30, help="--t-end: GMRES restart length (<= 63; the paper's 60)")
     ap.add_argument("--eps-fixed", type=float, default=0.0, help="--t-end: fixed FD step (the paper's 1e-8)")

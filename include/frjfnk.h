@@ -86,7 +86,12 @@ typedef struct fr_opts {
   int precond_refresh;   /* pseudo-transient continuation (ESDIRK, BDF2): 0 = form
                             J_ee once per stage at its first pseudo iterate and
                             re-invert shift*I - J_ee when dtau changes (default);
-                            1 = form the blocks again at every pseudo iterate.
+                            1 = form the blocks again at every pseudo iterate;
+                            2 = form them once per stage and keep them, shift
+                            included (no re-inversion when dtau changes: any
+                            fixed right preconditioner leaves the converged
+                            answer unchanged, and the loose inner solves of
+                            PTC need no exact one).
                             The paper does not say; ROW forms them once per step */
   int guess;             /* initial guess of ROW stage solves: 0 = zero (the
                             paper's); 1 = the same stage's solution at the previous

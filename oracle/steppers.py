@@ -59,7 +59,7 @@ class PtcOpts:
     max_iters: int = 200
     max_rejections: int = 30
     reject_above: float = 0.1        # GMRES relres above this -> reject
-    refresh: str = "stage"           # "stage" or "iterate" (element-Jacobi J_ee)
+    refresh: str = "stage"           # "stage", "iterate" or "frozen" (element-Jacobi blocks)
 
 
 @dataclass
@@ -134,7 +134,10 @@ def ptc_solve(prob: Problem, rhs_const, omega_dt, q0, dt, popts: PtcOpts, sopts:
             if J is None or (popts.refresh == "iterate" and J_k != k):
                 J = diagonal_blocks(prob, q, eps_rel=sopts.eps_rel)
                 J_k = k
-            blocks = shift * np.eye(J.shape[1])[None] - J
+                shift0 = shift
+            # "frozen": the blocks keep the stage's first shift (any fixed
+            # right preconditioner leaves the converged answer unchanged)
+            blocks = (shift0 if popts.refresh == "frozen" else shift) * np.eye(J.shape[1])[None] - J
         dq, info = _linear_solve(prob, q, Rq, shift, -F, sopts, popts.tol_lin, stats, blocks)
         if info.relres > popts.reject_above:
             rejections += 1

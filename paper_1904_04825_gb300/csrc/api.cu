@@ -289,7 +289,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
       !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) ||
-      (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 1 ||
+      (mesh->wall_y && !(o.wall_temperature > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 2 ||
       o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
     return FR_ERR_INVALID_ARG;
   if (o.riemann == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only

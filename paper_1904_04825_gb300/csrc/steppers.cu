@@ -215,10 +215,10 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
       } else if (ctx->opts.precond_refresh == 1 && formed_k != k) {
         FRK_TRY(launch_block_factor(ctx, q, shift, s));
         formed_k = k;
-      } else if (blocks_shift != shift) {
+      } else if (ctx->opts.precond_refresh != 2 && blocks_shift != shift) {
         FRK_TRY(launch_block_reshift(ctx, shift, s));
       }
-      blocks_shift = shift;
+      blocks_shift = shift;  // precond_refresh = 2 keeps the stage's first blocks and shift
     }
     ctx->blocks_valid = ctx->opts.precond;
     // b = -F into B_RHS

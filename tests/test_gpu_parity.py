@@ -596,3 +596,20 @@ def test_degree_6_fp64_blocks_rejected(fr):
     xe, ye, X, Y = _case("uniform", 4, 4, 6, seed=0)
     with pytest.raises(fr.FrError):
         fr.Context(xe, ye, 6, fr.default_opts(block_precision=0))
+
+
+def test_step_esdirk_frozen_preconditioner_matches_oracle(fr):
+    """precond_refresh = 2 (each stage's first blocks kept, no re-inversion)
+    against the oracle's refresh = "frozen"."""
+    p = 2
+    xe, ye, X, Y = _case("uniform", 5, 5, p, seed=0)
+    U0 = S.Vortex().state(X, Y)
+    prob = Problem(Mesh(xe, ye), p)
+    ctx = fr.Context(xe, ye, p, fr.default_opts(gmres_max_restarts=40, precond_refresh=2))
+    po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
+    U = _t(U0)
+    st = fr.step_esdirk(ctx, 3, 0.1, U, po)
+    Uo, so = o_esdirk(prob, ESDIRK[3](), 0.1, U0,
+                      PtcOpts(tol_nl=1e-12, tol_lin=1e-3, refresh="frozen"), TIGHT)
+    assert st.converged and so.converged
+    assert _rel(U.cpu().numpy(), Uo) < TOL_RUN

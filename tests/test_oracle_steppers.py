@@ -128,3 +128,14 @@ def test_ssprk3_temporal_order(vortex):
     step = lambda U, Up, dt, k: (step_ssprk3(prob, dt, U), None)
     errs, rates = _rate(step, U0, 0.4, (16, 32, 64), 512)
     assert 2.7 < rates[-1] < 3.4, (errs, rates)
+
+
+def test_frozen_stage_preconditioner_reaches_the_same_stage_solution(vortex):
+    """refresh = "frozen" keeps each stage's first element-Jacobi blocks (and
+    their shift) for all its pseudo steps: a different right preconditioner,
+    so a different Krylov path, but PTC converges to the same stage values."""
+    prob, U0 = vortex
+    tab = ESDIRK[3]()
+    base = step_esdirk(prob, tab, 0.2, U0, PtcOpts(tol_nl=1e-11, tol_lin=1e-3), TIGHT)[0]
+    frz = step_esdirk(prob, tab, 0.2, U0, PtcOpts(tol_nl=1e-11, tol_lin=1e-3, refresh="frozen"), TIGHT)[0]
+    assert np.linalg.norm(frz - base) / np.linalg.norm(base) < 1e-9
