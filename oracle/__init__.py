@@ -13,10 +13,14 @@ step, NumPy doing only library work (matrix products, dense solves, norms):
 
   basis      Gauss-Legendre points, Lagrange basis, Radau g_DG correction (Sec. 3)
   fr2d       Euler fluxes, Rusanov common flux, FR residual R(q) (Sec. 3, Eq. simplified_ode)
+  ns2d       Navier-Stokes BR2 residual, walls, body force (Sec. 2-3)
+  fr3d       3D Navier-Stokes FR residual on hexahedra, Taylor-Green
+             dissipation rate (Sec. 3, Sec. 5)
   jfnk       FD Jacobian-vector product, brute-force Jacobian, element-Jacobi
              blocks, restarted right-preconditioned GMRES(m) (Sec. 4.5)
   tableaus   ROW / ESDIRK coefficient sets (Sec. 4.2, 4.3)
-  steppers   ROW, ESDIRK + pseudo-transient continuation + SER, BDF2 (Sec. 4.1-4.4)
+  steppers   ROW, ESDIRK + pseudo-transient continuation + SER, BDF2, SSPRK3 (Sec. 4.1-4.4)
+  mlp        per-element MLP forward, backward, Adam (learned initial guess)
 
 Parity status of each function is stated in its module docstring; every
 function listed above is pinned by a ``-m "not gpu"`` test against facts the

@@ -125,7 +125,10 @@ def element_jacobians(prob: Problem, U, elements=None, eps_rel=1e-7):
 
 
 def diagonal_blocks(prob: Problem, U, elements=None, eps_rel=1e-7):
-    """J_ee for the Euler or the Navier-Stokes residual of ``prob``."""
+    """J_ee for the Euler or the Navier-Stokes residual of ``prob`` (a
+    problem with its own ``element_jacobians``, such as the 3D one, forms them)."""
+    if hasattr(prob, "element_jacobians"):
+        return prob.element_jacobians(U, elements, eps_rel)
     if prob.viscous is not None:
         from .ns2d import ns_element_jacobians
         return ns_element_jacobians(U, prob.mesh, prob.p, prob.viscous, elements, eps_rel, prob.basis)

@@ -294,3 +294,105 @@ def batch_instances(count: int = 64, seed: int = 0, meshes=BATCH_MESHES, degrees
         p = int(degrees[rng.integers(len(degrees))])
         out.append(Instance(n, p, Vortex(alpha=float(alpha), theta=float(theta), x0=float(x0), y0=float(y0))))
     return out
+
+
+# ------------------------------------------------------------------ 3D ------
+# State arrays of the 3D path have shape ``(Ne, 5, Np)`` with ``Np = (p+1)**3``;
+# point ``i + n*j + n*n*k`` (i along x, j along y, k along z, n = p+1);
+# element ``ix + Nx*(iy + Ny*iz)``; variables (rho, rho u, rho v, rho w, E).
+
+def point_coords3d(x_edges, y_edges, z_edges, p: int):
+    """Physical coordinates ``X, Y, Z`` of shape ``(Ne, Np)`` (3D layout)."""
+    s = sample_nodes(p)
+    n = p + 1
+    nx, ny, nz = len(x_edges) - 1, len(y_edges) - 1, len(z_edges) - 1
+    def place(edges):
+        a, h = np.asarray(edges[:-1]), np.diff(edges)
+        return a[:, None] + 0.5 * (s[None, :] + 1.0) * h[:, None]      # (n_el, n)
+    px, py, pz = place(x_edges), place(y_edges), place(z_edges)
+    shape = (nz, ny, nx, n, n, n)                                      # [iz, iy, ix, k, j, i]
+    X = np.broadcast_to(px[None, None, :, None, None, :], shape)
+    Y = np.broadcast_to(py[None, :, None, None, :, None], shape)
+    Z = np.broadcast_to(pz[:, None, None, :, None, None], shape)
+    ne = nx * ny * nz
+    return tuple(np.ascontiguousarray(A.reshape(ne, n ** 3)) for A in (X, Y, Z))
+
+
+def conserved3d(rho, u, v, w, pr, gamma: float = GAMMA) -> np.ndarray:
+    """Stack primitive fields into conserved ``(Ne, 5, Np)``."""
+    E = pr / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.ascontiguousarray(np.stack([rho, rho * u, rho * v, rho * w, E], axis=1))
+
+
+def uniform_mesh3d(n: int, lo: float = -math.pi, hi: float = math.pi):
+    e = uniform_edges(n, lo, hi)
+    return e, e.copy(), e.copy()
+
+
+def stretched_mesh3d(nx: int, ny: int, nz: int, seed: int = 0, amp: float = 0.3,
+                     lo: float = -math.pi, hi: float = math.pi):
+    """Tensor-product hexahedral mesh with randomly jittered edges."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in (nx, ny, nz):
+        e = np.linspace(lo, hi, n + 1)
+        e[1:-1] += rng.uniform(-amp, amp, n - 1) * (hi - lo) / n
+        out.append(e)
+    return tuple(out)
+
+
+def smooth_random_state3d(X, Y, Z, seed: int, amp: float = 0.05, modes: int = 3,
+                          lo: float = -math.pi, hi: float = math.pi,
+                          base=(1.0, 0.7, -0.4, 0.3, 2.0), gamma: float = GAMMA) -> np.ndarray:
+    """Free stream ``base = (rho, u, v, w, p)`` plus random periodic Fourier
+    modes of relative amplitude ``amp`` in every primitive field."""
+    rng = np.random.default_rng(seed)
+    L = hi - lo
+    fields = []
+    for b in base:
+        f = np.full_like(X, b)
+        for _ in range(modes):
+            k = rng.integers(-2, 3, size=3)
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.uniform(-1, 1) * amp * max(abs(b), 1.0)
+            f = f + a * np.sin(2 * math.pi * (k[0] * X + k[1] * Y + k[2] * Z) / L + ph)
+        fields.append(f)
+    return conserved3d(*fields, gamma=gamma)
+
+
+@dataclass(frozen=True)
+class TaylorGreen:
+    """Initial field of the Taylor-Green vortex (Sec. 5): on [-pi L, pi L]^3,
+    u = V0 sin(x/L) cos(y/L) cos(z/L), v = -V0 cos(x/L) sin(y/L) cos(z/L),
+    w = 0, p = p0 + rho0 V0^2/16 (cos(2x/L) + cos(2y/L)) (cos(2z/L) + 2),
+    Ma = V0 / c0 = 0.1 with c0 the sound speed at (rho0, p0), Re = rho0 V0 L / mu
+    = 1600, Pr = 0.71.  The paper does not give the initial density; the
+    temperature is taken uniform, T0 = p0 / (rho0 R), so rho = rho0 p / p0."""
+    rho0: float = 1.0
+    v0: float = 1.0
+    length: float = 1.0
+    mach: float = 0.1
+    reynolds: float = 1600.0
+    prandtl: float = 0.71
+    gamma: float = GAMMA
+
+    @property
+    def p0(self) -> float:
+        return self.rho0 * self.v0 ** 2 / (self.gamma * self.mach ** 2)
+
+    @property
+    def mu(self) -> float:
+        return self.rho0 * self.v0 * self.length / self.reynolds
+
+    @property
+    def t_c(self) -> float:
+        return self.length / self.v0
+
+    def state(self, X, Y, Z) -> np.ndarray:
+        L, V0 = self.length, self.v0
+        u = V0 * np.sin(X / L) * np.cos(Y / L) * np.cos(Z / L)
+        v = -V0 * np.cos(X / L) * np.sin(Y / L) * np.cos(Z / L)
+        w = np.zeros_like(X)
+        pr = self.p0 + self.rho0 * V0 ** 2 / 16.0 * (np.cos(2 * X / L) + np.cos(2 * Y / L)) * (np.cos(2 * Z / L) + 2.0)
+        rho = self.rho0 * pr / self.p0
+        return conserved3d(rho, u, v, w, pr, self.gamma)
