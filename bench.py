@@ -208,6 +208,20 @@ def our_arm(args):
                                jv_precision=1 if args.jv_precision == "fp32" else 0,
                                riemann=1 if args.riemann == "roe" else 0)
         wl = f"vortex-160x160-p3-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
+    elif args.workload == "tgv":
+        # Taylor-Green vortex (Sec. 5): 64^3 hexahedra at p = 3, Re 1600, Ma 0.1,
+        # dt = t_c / 25, tol_lin 1e-6; element-Jacobi blocks only where built (p <= 2)
+        tg = S.TaylorGreen()
+        p = args.p or 3
+        n3 = args.nx or 64
+        edges3 = S.uniform_mesh3d(n3)
+        X, Y, Z = S.point_coords3d(*edges3, p)
+        U0 = tg.state(X, Y, Z)
+        del X, Y, Z
+        dt, wall = (args.dt or tg.t_c / 25.0), False
+        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
+                               mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 2 else 0)
+        wl = f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}" + ("" if p <= 2 else "-noprecond")
     else:
         ch = S.Channel()
         xe = np.linspace(0.0, ch.lx, 257)
@@ -225,8 +239,12 @@ def our_arm(args):
         wl += "-fp32linearjv"
     if args.riemann == "roe":
         wl += "-roe"
-    ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
+    if args.workload == "tgv":
+        ctx = fr.Context3D(*edges3, p, opts)
+    else:
+        ctx = fr.Context(xe, ye, p, opts, wall_y=wall)
     U = torch.from_numpy(U0).to(dev)
+    del U0
     Uprev = torch.empty_like(U)
     tuned = None
     if not args.no_autotune:
@@ -367,7 +385,8 @@ def our_arm(args):
                            "block_precision": args.block_precision, "jv_precision": args.jv_precision,
                            "workload": wl,
                            "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
-                           "mesh": f"{ctx.nx}x{ctx.ny}", "launch_config": tuned,
+                           "mesh": f"{ctx.nx}x{ctx.ny}" + (f"x{ctx.nz}" if args.workload == "tgv" else ""),
+                           "launch_config": tuned,
                            "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / dt) if args.workload == "vortex" else None}),
         "gpu_launches": launches,
         "clocks": clk,
@@ -747,7 +766,7 @@ def main():
                     help="common inviscid flux (roe: the paper's; Euler only)")
     ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: linear parts of the FD operator in FP32 (Euler only)")
-    ap.add_argument("--workload", choices=["vortex", "channel", "batch"], default="vortex")
+    ap.add_argument("--workload", choices=["vortex", "channel", "batch", "tgv"], default="vortex")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])

@@ -149,11 +149,45 @@ void fr_default_ptc_opts(fr_ptc_opts* opts);
  * basis, Radau g_DG correction derivatives, Sec. 3) and allocates every
  * workspace buffer.  *out receives the handle (NULL on failure). */
 int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opts, fr_ctx** out);
+/* ---- 3D hexahedral Navier-Stokes path (Sec. 2-3 in three directions;
+ * the Taylor-Green vortex of Sec. 5) ----
+ * Periodic tensor-product mesh of axis-aligned hexahedra: element
+ * ix + nx (iy + ny iz) spans [x_edges[ix], x_edges[ix+1]] x [y_edges[iy], ...]
+ * x [z_edges[iz], ...].  nx, ny, nz >= 2; host arrays of nx+1, ny+1, nz+1
+ * strictly increasing values. */
+typedef struct fr_mesh3d_desc {
+  int nx, ny, nz;
+  const double* x_edges;
+  const double* y_edges;
+  const double* z_edges;
+} fr_mesh3d_desc;
+/* Create a 3D context: state layout double[Ne][5][(p+1)^3] with variables
+ * (rho, rho u, rho v, rho w, E) and point index i + N j + N^2 k (N = p+1, i
+ * along x).  1 <= p <= 4.  R(q) is the FR residual with the Rusanov common
+ * flux and, for opts->mu > 0, the BR2 viscous terms (kappa = mu Cp / Pr,
+ * R_gas = 1); mu = 0 gives the Euler residual.  Every call of this header
+ * that takes a context works on a 3D one (fr_residual, fr_jv, ejacobi_*,
+ * gmres_solve, the steppers, fr_autotune, profiling) except the batch and
+ * learned-guess calls.  Element-Jacobi blocks (5 (p+1)^3 rows) are built
+ * for p <= 2; opts->precond with p > 2, opts->riemann = 1,
+ * opts->jv_precision = 1, opts->guess = 2 or a body force return
+ * FR_ERR_UNSUPPORTED.  The blocks and their staging (2 Ne nb^2 doubles) are
+ * allocated only when opts->precond is set. */
+int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* opts, fr_ctx** out);
+/* Kinetic-energy dissipation rate of the Taylor-Green study (Sec. 5) of the
+ * 3D state U (device, ndof doubles): out[0] = eps1 = 2 mu / rho0 <S^d : S^d>,
+ * out[1] = eps3 = -<p div v> / rho0 (eps2 = 0: zero bulk viscosity), out[2] =
+ * <rho |v|^2 / 2> / rho0, <.> the volume average by Gauss-Legendre
+ * quadrature at the solution points, the velocity differentiated as each
+ * element's degree-p interpolant.  out: host, 3 doubles.  Synchronises the
+ * stream.  FR_ERR_UNSUPPORTED on a 2D context. */
+int fr_dissipation_rate(fr_ctx* ctx, const double* U, double rho0, double* out, void* stream);
+
 /* Free the context and its device memory. NULL is accepted. */
 int fr_ctx_destroy(fr_ctx* ctx);
 /* Message of the last failing call on ctx ("" if none); static string for ctx == NULL. */
 const char* fr_last_error(const fr_ctx* ctx);
-/* Number of doubles in one state vector (Ne * 4 * (p+1)^2). */
+/* Number of doubles in one state vector (2D: Ne * 4 * (p+1)^2; 3D: Ne * 5 * (p+1)^3). */
 long long fr_ndof(const fr_ctx* ctx);
 
 /* R = R(U), the FR/CPR semi-discrete right-hand side dq/dt = R(q)

@@ -51,6 +51,13 @@ class fr_mesh_desc(ctypes.Structure):
                 ("wall_y", ctypes.c_int)]
 
 
+class fr_mesh3d_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x_edges", ctypes.POINTER(ctypes.c_double)),
+                ("y_edges", ctypes.POINTER(ctypes.c_double)),
+                ("z_edges", ctypes.POINTER(ctypes.c_double))]
+
+
 class fr_opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("m_max", ctypes.c_int),
                 ("eps_rel", ctypes.c_double), ("eps_fixed", ctypes.c_double),
@@ -93,6 +100,9 @@ def _load():
         "fr_default_ptc_opts": (None, [ctypes.POINTER(fr_ptc_opts)]),
         "fr_ctx_create": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts),
                               ctypes.POINTER(ctypes.c_void_p)]),
+        "fr_ctx_create_3d": (I, [ctypes.POINTER(fr_mesh3d_desc), I, ctypes.POINTER(fr_opts),
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+        "fr_dissipation_rate": (I, [P, P, D, ctypes.POINTER(ctypes.c_double), V]),
         "fr_ctx_destroy": (I, [P]),
         "fr_last_error": (ctypes.c_char_p, [P]),
         "fr_ndof": (ctypes.c_longlong, [P]),
@@ -236,6 +246,34 @@ class Context:
     def empty(self):
         import torch
         return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+
+class Context3D(Context):
+    """Owns a 3D ``fr_ctx``: periodic hexahedra, state ``(Ne, 5, (p+1)**3)``."""
+
+    def __init__(self, x_edges, y_edges, z_edges, p: int, opts: fr_opts | None = None):
+        es = [np.ascontiguousarray(e, dtype=np.float64) for e in (x_edges, y_edges, z_edges)]
+        dp = [e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for e in es]
+        desc = fr_mesh3d_desc(len(es[0]) - 1, len(es[1]) - 1, len(es[2]) - 1, *dp)
+        self.opts = opts if opts is not None else default_opts()
+        h = ctypes.c_void_p()
+        rc = lib.fr_ctx_create_3d(ctypes.byref(desc), p, ctypes.byref(self.opts), ctypes.byref(h))
+        if rc != FR_OK:
+            raise FrError(rc, "fr_ctx_create_3d failed")
+        self.handle = h
+        self.p = p
+        self.nx, self.ny, self.nz = (len(e) - 1 for e in es)
+        self.ne = self.nx * self.ny * self.nz
+        self.np = (p + 1) ** 3
+        self.ndof = int(lib.fr_ndof(h))
+        self.shape = (self.ne, 5, self.np)
+
+
+def fr_dissipation_rate(ctx: Context3D, U, rho0: float = 1.0, stream=None):
+    """(eps1, eps3, kinetic energy) of the Taylor-Green study for the 3D state U."""
+    out = (ctypes.c_double * 3)()
+    ctx.check(lib.fr_dissipation_rate(ctx.handle, _ptr(U), rho0, out, _stream(stream)))
+    return out[0], out[1], out[2]
 
 
 def fr_residual(ctx: Context, U, R, stream=None):

@@ -26,6 +26,8 @@ void free_ctx(fr_ctx* c) {
   if (!c) return;
   cudaFree(c->hx);
   cudaFree(c->hy);
+  cudaFree(c->hz);
+  cudaFree(c->diss);
   cudaFree(c->blocks);
   cudaFree(c->tb);
   cudaFree(c->fb);
@@ -146,6 +148,78 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   return FR_OK;
 }
 
+// 3D context: periodic hexahedra, 5 variables, (p+1)^3 points per element.
+// Element blocks and their staging exist only where they are built (p <= 2
+// with the preconditioner on).
+int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
+  c->opts = *o;
+  c->dim3 = 1;
+  c->viscous = o->mu > 0.0 ? 1 : 0;
+  c->p = p;
+  c->n1 = p + 1;
+  c->np = c->n1 * c->n1 * c->n1;
+  c->nb = 5 * c->np;
+  c->nx = mesh->nx;
+  c->ny = mesh->ny;
+  c->nz = mesh->nz;
+  c->ne = (long long)mesh->nx * mesh->ny * mesh->nz;
+  c->ndof = c->ne * c->nb;
+  c->volume = (mesh->x_edges[mesh->nx] - mesh->x_edges[0]) * (mesh->y_edges[mesh->ny] - mesh->y_edges[0]) *
+              (mesh->z_edges[mesh->nz] - mesh->z_edges[0]);
+  FRK_CUDA(c, cudaGetDevice(&c->device));
+  build_tables(p, &c->tab);
+  const double* edges[3] = {mesh->x_edges, mesh->y_edges, mesh->z_edges};
+  const int counts[3] = {mesh->nx, mesh->ny, mesh->nz};
+  double** dst[3] = {&c->hx, &c->hy, &c->hz};
+  for (int d = 0; d < 3; ++d) {
+    double* h = new double[counts[d]];
+    for (int i = 0; i < counts[d]; ++i) h[i] = edges[d][i + 1] - edges[d][i];
+    int rc = dalloc(c, dst[d], counts[d]);
+    if (rc == FR_OK && cudaMemcpy(*dst[d], h, counts[d] * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = set_error(c, FR_ERR_CUDA, "copying the mesh failed");
+    delete[] h;
+    FRK_TRY(rc);
+  }
+  const size_t n = (size_t)c->ndof;
+  const int m = o->m_max;
+  const size_t n2 = (size_t)c->n1 * c->n1;
+  FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 6 * n2 * 20));
+  FRK_TRY(dalloc(c, &c->fb, (size_t)c->ne * 3 * n2 * 10));
+  if (o->precond) {
+    FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * c->nb * c->nb));
+    FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
+    FRK_TRY(dalloc(c, &c->rloc, n));
+  }
+  FRK_TRY(dalloc(c, &c->diss, 4));
+  FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
+  FRK_TRY(dalloc(c, &c->z, n));
+  for (double*& b : c->buf) FRK_TRY(dalloc(c, &b, n));
+  FRK_TRY(dalloc(c, &c->scal, S_COUNT));
+  FRK_TRY(dalloc(c, &c->red.partials, (size_t)kRedBlocks * kMaxVec));
+  FRK_TRY(dalloc(c, &c->red.counter, 1));
+  c->gd.ldh = m + 1;
+  FRK_TRY(dalloc(c, &c->gd.H, (size_t)(m + 1) * m));
+  FRK_TRY(dalloc(c, &c->gd.cs, m));
+  FRK_TRY(dalloc(c, &c->gd.sn, m));
+  FRK_TRY(dalloc(c, &c->gd.g, m + 1));
+  FRK_TRY(dalloc(c, &c->gd.y, m));
+  FRK_TRY(dalloc(c, &c->gd.h1, kMaxVec));
+  FRK_TRY(dalloc(c, &c->gd.h2, kMaxVec));
+  FRK_TRY(dalloc(c, &c->gd.invh, m + 1));
+  FRK_TRY(dalloc(c, &c->gd.done, 1));
+  FRK_TRY(dalloc(c, &c->gd.rflag, m));
+  FRK_TRY(dalloc(c, &c->gd.k, 1));
+  FRK_TRY(dalloc(c, &c->gd.res, 1));
+  FRK_TRY(dalloc(c, &c->gd.target, 1));
+  FRK_TRY(dalloc(c, &c->kerr, 1));
+  FRK_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_stat), (4 + kMaxVec) * sizeof(int)));
+  FRK_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 8 * sizeof(double)));
+  for (cudaEvent_t& e : c->chunk_ev) FRK_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  FRK_CUDA(c, cudaDeviceSynchronize());
+  return FR_OK;
+}
+
 std::atomic<long long> g_launches{0};
 
 int check_vec(fr_ctx* ctx, const void* p, const char* name) {
@@ -220,6 +294,7 @@ double ns_residual_flops_per_element(int p) {
 }
 
 double jv_flops_per_element(const fr_ctx* ctx) {
+  if (ctx->dim3) return ns3d_residual_flops_per_element(ctx->p);
   return ctx->viscous ? ns_residual_flops_per_element(ctx->p) : residual_flops_per_element(ctx->p);
 }
 
@@ -309,6 +384,59 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
     return rc;
   }
   *out = c;
+  return FR_OK;
+}
+
+extern "C" int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* opts, fr_ctx** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !mesh->x_edges || !mesh->y_edges || !mesh->z_edges || mesh->nx < 2 || mesh->ny < 2 ||
+      mesh->nz < 2)
+    return FR_ERR_INVALID_ARG;
+  if (p < 1 || p > 4) return FR_ERR_UNSUPPORTED;
+  fr_opts o;
+  fr_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.m_max < 1 || o.m_max > kMaxVec - 1 || o.gmres_m < 1 || o.gmres_m > o.m_max ||
+      o.gmres_max_restarts < 0 || !(o.gamma > 1.0) || !(o.eps_rel > 0.0) || !(o.block_eps_rel > 0.0) ||
+      !(o.reorth_eta >= 0.0 && o.reorth_eta <= 1.0) || o.block_precision < 0 || o.block_precision > 2 ||
+      !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 2 ||
+      o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
+    return FR_ERR_INVALID_ARG;
+  // the 3D path: Rusanov flux, FP64 operator, no body force; element blocks
+  // for p <= 2 (5 (p+1)^3 = 40 or 135 rows), no learned guess
+  if (o.riemann != 0 || o.jv_precision != 0 || o.guess == 2 || o.body_force_x != 0.0) return FR_ERR_UNSUPPORTED;
+  if (o.precond && p > 2) return FR_ERR_UNSUPPORTED;
+  for (int i = 0; i < mesh->nx; ++i)
+    if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;
+  for (int i = 0; i < mesh->ny; ++i)
+    if (!(mesh->y_edges[i + 1] > mesh->y_edges[i])) return FR_ERR_INVALID_ARG;
+  for (int i = 0; i < mesh->nz; ++i)
+    if (!(mesh->z_edges[i + 1] > mesh->z_edges[i])) return FR_ERR_INVALID_ARG;
+  fr_ctx* c = new (std::nothrow) fr_ctx();
+  if (!c) return FR_ERR_CUDA;
+  const int rc = create3d(mesh, p, &o, c);
+  if (rc != FR_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return FR_OK;
+}
+
+extern "C" int fr_dissipation_rate(fr_ctx* ctx, const double* U, double rho0, double* out, void* stream) {
+  if (!ctx || !out) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  if (!ctx->dim3) return set_error(ctx, FR_ERR_UNSUPPORTED, "fr_dissipation_rate: 3D contexts only");
+  if (!(rho0 > 0.0)) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_dissipation_rate: rho0 must be > 0");
+  cudaStream_t s = as_stream(stream);
+  FRK_TRY(launch_f3_dissipation(ctx, U, ctx->diss, s));
+  FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->diss, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  const double V = ctx->volume;
+  out[0] = 2.0 * ctx->opts.mu / rho0 * ctx->h_scal[0] / V;
+  out[1] = -ctx->h_scal[1] / (rho0 * V);
+  out[2] = ctx->h_scal[2] / (rho0 * V);
   return FR_OK;
 }
 

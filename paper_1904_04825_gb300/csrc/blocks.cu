@@ -323,6 +323,9 @@ template <> struct ApplyShape<100, float> { static constexpr int KS = 2, NS = 3;
 template <> struct ApplyShape<36, __nv_bfloat16> { static constexpr int KS = 4, NS = 8; };
 template <> struct ApplyShape<64, __nv_bfloat16> { static constexpr int KS = 2, NS = 6; };
 template <> struct ApplyShape<100, __nv_bfloat16> { static constexpr int KS = 2, NS = 4; };
+template <> struct ApplyShape<40, double> { static constexpr int KS = 4, NS = 6; };
+template <> struct ApplyShape<40, float> { static constexpr int KS = 4, NS = 8; };
+template <> struct ApplyShape<40, __nv_bfloat16> { static constexpr int KS = 4, NS = 8; };
 template <> struct ApplyShape<144, double> { static constexpr int KS = 1, NS = 1; };
 template <> struct ApplyShape<144, float> { static constexpr int KS = 1, NS = 2; };
 template <> struct ApplyShape<144, __nv_bfloat16> { static constexpr int KS = 1, NS = 4; };
@@ -429,6 +432,53 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
       (void)mbar_wait(&bar[u % NS], (unsigned)((u / NS) & 1), kWaitPolls);
   }
   if (sumsq) {  // every CTA takes part, so the reduction's counter stays consistent
+    const double bs = block_sum(ss, sh);
+    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+    if (last_block(red.counter)) {
+      finish_sums(red, 1, sumsq);
+      if (threadIdx.x == 0) write_eps(ea, *sumsq);
+    }
+  }
+}
+
+// z_e = M_e^-1 (s r_e) for blocks whose rows are not 16-byte multiples (3D
+// degree 2: nb = 135), without bulk copies: EPC elements per pass, one
+// thread per row, column-major blocks so thread i reads consecutive
+// addresses; optional r_e *= s written back and sum of squares of z.
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(256) k_apply_rows(const S* __restrict__ Minv, double* r, const double* scale,
+                                                    double* z, long long ne, double* sumsq, Reduce red,
+                                                    const int* done, EpsArgs ea) {
+  constexpr int EPC = 256 / NB;
+  __shared__ A rs[EPC][NB];
+  __shared__ double sh[32];
+  if (done && *done) return;
+  const double sc = scale ? *scale : 1.0;
+  const int el = threadIdx.x / NB, i = threadIdx.x % NB;
+  double ss = 0.0;
+  for (long long e0 = (long long)blockIdx.x * EPC; e0 < ne; e0 += (long long)gridDim.x * EPC) {
+    const long long e = e0 + el;
+    const bool act = el < EPC && e < ne;
+    __syncthreads();
+    if (act) {
+      double v = r[e * NB + i];
+      if (scale) {
+        v *= sc;
+        r[e * NB + i] = v;
+      }
+      rs[el][i] = (A)v;
+    }
+    __syncthreads();
+    if (act) {
+      const S* Me = Minv + e * (long long)NB * NB;
+      A acc = 0;
+      for (int kk = 0; kk < NB; ++kk) acc = fma(load_acc(Me + kk * NB + i), rs[el][kk], acc);
+      const double zi = (double)acc;
+      z[e * NB + i] = zi;
+      ss = fma(zi, zi, ss);
+    }
+  }
+  if (sumsq) {
     const double bs = block_sum(ss, sh);
     if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
     if (last_block(red.counter)) {
@@ -560,6 +610,9 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
   if constexpr (L::BYTES > kSmemMax) {
     return set_error(ctx, FR_ERR_UNSUPPORTED, "element blocks of %d rows in this precision exceed shared memory", NB);
   }
+  // the staged apply copies r with the bulk-copy engine: 16-byte aligned rows
+  if (reinterpret_cast<uintptr_t>(r) % 16 != 0)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply: r must be 16-byte aligned");
   static int per_sm = 0;  // resident CTAs per SM (function attribute set once per process)
   if (per_sm == 0) {
     FRK_CUDA(ctx, cudaFuncSetAttribute(k_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
@@ -575,6 +628,31 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
                                                                   sumsq, ctx->red, done, eps_args(ctx, with_eps), ctx->kerr); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+template <int NB, typename S, typename A>
+int apply_rows_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
+                   const int* done, cudaStream_t s, bool with_eps) {
+  const bool in_cycle = done != nullptr;
+  const double nd = (double)ctx->ndof;
+  const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
+  const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
+  constexpr int threads = ((256 / NB) * NB + 31) / 32 * 32;  // whole warps (the reduction shuffles)
+  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf);
+    k_apply_rows<NB, S, A><<<apply_grid<NB>(ctx->ne), threads, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z,
+                                                                       ctx->ne, sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+template <int NB>
+int apply_rows_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
+                  const int* done, cudaStream_t s, bool with_eps) {
+  switch (ctx->opts.block_precision) {
+    case 1: return apply_rows_nbs<NB, float, float>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 2: return apply_rows_nbs<NB, __nv_bfloat16, float>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    default: return apply_rows_nbs<NB, double, double>(ctx, r, scale, z, sumsq, done, s, with_eps);
+  }
 }
 
 template <int NB>
@@ -638,6 +716,8 @@ int invert_nb(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
   switch (ctx->nb) {
     case 36: return invert_nb<36>(ctx, mst, dshift, s);
+    case 40: return invert_nb<40>(ctx, mst, dshift, s);
+    case 135: return invert_nb<135>(ctx, mst, dshift, s);
     case 64: return invert_nb<64>(ctx, mst, dshift, s);
     case 100: return invert_nb<100>(ctx, mst, dshift, s);
     case 144: return invert_nb<144>(ctx, mst, dshift, s);
@@ -654,6 +734,7 @@ int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s) {
 
 int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
   ctx->staged_shift = shift;
+  if (ctx->dim3) return launch_f3_factor(ctx, U, shift, s);
   if (ctx->viscous) return launch_ns_factor(ctx, U, shift, s);
   FactorArgs a;
   a.U = U; a.blocks = ctx->blocks; a.mst = ctx->mst; a.hx = ctx->hx; a.hy = ctx->hy;
@@ -673,9 +754,6 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
 
 int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
                        const int* done, cudaStream_t s, bool with_eps) {
-  // the staged apply copies r with the bulk-copy engine: 16-byte aligned rows
-  if (reinterpret_cast<uintptr_t>(r) % 16 != 0)
-    return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply: r must be 16-byte aligned");
   if (!ctx->opts.precond) {
     { ProfScope ps_(ctx, FR_KF_APPLY, s); k_scale_copy<<<vec_grid(ctx, ctx->ndof), kThreads, 0, s>>>(r, scale, z, ctx->ndof, sumsq, ctx->red,
                                                           done, eps_args(ctx, with_eps)); }
@@ -684,6 +762,8 @@ int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, d
   }
   switch (ctx->nb) {
     case 36: return apply_nb<36>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 40: return apply_nb<40>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 135: return apply_rows_nb<135>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 64: return apply_nb<64>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 100: return apply_nb<100>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 144: return apply_nb<144>(ctx, r, scale, z, sumsq, done, s, with_eps);
@@ -701,6 +781,8 @@ int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
   }
   switch (ctx->nb) {
     case 36: return solupdate_nb<36>(ctx, x, s);
+    case 40: return solupdate_nb<40>(ctx, x, s);
+    case 135: return solupdate_nb<135>(ctx, x, s);
     case 64: return solupdate_nb<64>(ctx, x, s);
     case 100: return solupdate_nb<100>(ctx, x, s);
     case 144: return solupdate_nb<144>(ctx, x, s);

@@ -1,0 +1,697 @@
+// 3D Navier-Stokes FR residual on periodic axis-aligned hexahedra (Sec. 2-3
+// in three reference directions, BR2 common gradients, Eqs. com_q and
+// com_grad_q, g'(+-1) = +-(P+1)(P+2)/2) and the kinetic-energy dissipation
+// rate of the Taylor-Green study (Sec. 5).  mu = 0 gives the Euler residual.
+//
+// Layout: U[ne][5][Np], Np = N^3 (N = p+1), point i + N j + N^2 k (i along x),
+// element ix + nx (iy + ny iz).  Face 2d is the low face of direction d
+// (d = 0 x, 1 y, 2 z), face 2d+1 the high face; face point f = a + N b over
+// the two other directions in increasing order.
+//
+// R(U), A z and b - A z take three kernels, like the 2D viscous path:
+//  k3_trace: per element, the (possibly perturbed) state and its own
+//    polynomial gradient traced to the 6 N^2 face points -> trace buffer
+//    [ne][6][N^2][5][4] = (q, q_x, q_y, q_z).
+//  k3_face:  per low face point of every element (each face once), the
+//    common solution, BR2 common gradient and common total normal flux
+//    (Rusanov inviscid minus viscous) from the two traces -> face buffer
+//    [ne][3][N^2][10] = (q_com, f_n).
+//  k3_cell:  per element, the FR-corrected gradient, the total fluxes along
+//    x, y, z at the solution points and their corrected divergence with the
+//    six faces' common fluxes (low faces its own, high faces the neighbours'
+//    low faces), then the output of the mode.  Both elements of a face read
+//    the same stored flux, so conservation holds to round-off.
+// Element-Jacobi columns (k3_cell mode 3, degrees 1 and 2): slot = (element,
+// column c), own state perturbed in DOF c by eps_c = beps (1 + |q_c|), own
+// traces recomputed in the kernel, neighbour traces frozen (trace buffer of
+// the unperturbed state); the slot forms its six faces' common data itself
+// and stages column c of shift I - J_ee for the inversion kernel.
+#include "device.cuh"
+
+namespace frk {
+namespace {
+
+struct F3Args {
+  const double* U;
+  const double* z;
+  const double* R0;
+  const double* b;
+  double* out;
+  double* tb;          // traces [ne][6][N^2][5][4]
+  double* fb;          // low-face common data [ne][3][N^2][10]
+  const double* hx;
+  const double* hy;
+  const double* hz;
+  const double* eps2;
+  const int* done;
+  long long ne;
+  int nx, ny, nz;
+  double gam, mu, kappa, shift, beps;
+  Tables tab;
+};
+
+// elements per CTA, one thread per solution point
+template <int P> struct F3Slots;
+template <> struct F3Slots<1> { static constexpr int E = 16; };
+template <> struct F3Slots<2> { static constexpr int E = 8; };
+template <> struct F3Slots<3> { static constexpr int E = 4; };
+template <> struct F3Slots<4> { static constexpr int E = 2; };
+
+// doubles of dynamic shared memory per element of k3_cell: state, three
+// derivative / flux arrays, q_com - q_face and f_n on the 6 N^2 face points
+template <int P> struct CellLayout {
+  static constexpr int N = P + 1, N2 = N * N, NP = N2 * N;
+  static constexpr int PER = 20 * NP + 60 * N2;
+  static constexpr size_t BYTES = (size_t)F3Slots<P>::E * PER * sizeof(double);
+};
+
+template <int N>
+__device__ __forceinline__ double tsum3(const double* x, int stride, const double* c) {
+  double s = c[0] * x[0];
+#pragma unroll
+  for (int l = 1; l < N; ++l) s = fma(c[l], x[l * stride], s);
+  return s;
+}
+
+// first point and stride of the line through face point f normal to direction d
+template <int N>
+__device__ __forceinline__ void line_of(int d, int f, int* off, int* stride) {
+  constexpr int N2 = N * N;
+  if (d == 0) { *off = N * (f % N) + N2 * (f / N); *stride = 1; }
+  else if (d == 1) { *off = (f % N) + N2 * (f / N); *stride = N; }
+  else { *off = f; *stride = N2; }
+}
+
+// inviscid flux along direction d and |v_d| + c (selects instead of indexing
+// by d, so the arrays stay in registers when d is not a constant)
+__device__ __forceinline__ double flux3(const double q[5], int d, double gam, double f[5]) {
+  const double ri = 1.0 / q[0];
+  const double md = d == 0 ? q[1] : (d == 1 ? q[2] : q[3]);
+  const double vd = md * ri;
+  const double p = (gam - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ri);
+  f[0] = md;
+  f[1] = fma(q[1], vd, d == 0 ? p : 0.0);
+  f[2] = fma(q[2], vd, d == 1 ? p : 0.0);
+  f[3] = fma(q[3], vd, d == 2 ? p : 0.0);
+  f[4] = vd * (q[4] + p);
+  return fabs(vd) + sqrt(gam * p * ri);
+}
+
+__device__ __forceinline__ void rusanov3(const double qm[5], const double qp[5], int d, double gam,
+                                         double fn[5]) {
+  double fm[5], fp[5];
+  const double lm = flux3(qm, d, gam, fm);
+  const double lp = flux3(qp, d, gam, fp);
+  const double lam = fmax(lm, lp);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fn[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * lam * (qp[v] - qm[v]);
+}
+
+// viscous fluxes along the directions d with mask bit d set, from q and the
+// gradients g[c][v] (c: direction); R = 1
+__device__ __forceinline__ void visc3(const double q[5], const double g[3][5], double gam, double mu,
+                                      double kappa, int mask, double fv[3][5]) {
+  const double ri = 1.0 / q[0];
+  const double vel[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  const double e = q[4] * ri;
+  double dv[3][3];  // dv[c][m] = d v_m / d x_c
+  double dT[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) dv[c][m] = (g[c][1 + m] - vel[m] * g[c][0]) * ri;
+    dT[c] = (gam - 1.0) * ((g[c][4] - e * g[c][0]) * ri - (vel[0] * dv[c][0] + vel[1] * dv[c][1] + vel[2] * dv[c][2]));
+  }
+  const double div = dv[0][0] + dv[1][1] + dv[2][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!(mask & (1 << d))) continue;
+    double tau[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) tau[m] = mu * (dv[d][m] + dv[m][d]);
+    tau[d] -= (2.0 / 3.0) * mu * div;
+    fv[d][0] = 0.0;
+    fv[d][1] = tau[0];
+    fv[d][2] = tau[1];
+    fv[d][3] = tau[2];
+    fv[d][4] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * dT[d];
+  }
+}
+
+// common solution and total normal flux on a face normal to d from the (-)
+// and (+) traces m, pp ([v][q, q_x, q_y, q_z]); hm, hp: the two elements'
+// sizes along d; cbr2 = (P+1)(P+2)/2
+__device__ __forceinline__ void common3(const double m[5][4], const double pp[5][4], int d, double hm,
+                                        double hp, double cbr2, const F3Args& a, double qc[5],
+                                        double fn[5]) {
+  double qm[5], qp[5], g[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qm[v] = m[v][0];
+    qp[v] = pp[v][0];
+    qc[v] = 0.5 * (qm[v] + qp[v]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c][v] = 0.5 * (m[v][1 + c] + pp[v][1 + c]);
+    const double rm = (2.0 / hm) * cbr2 * (qc[v] - qm[v]);   // lifting of the (-) element
+    const double rp = -(2.0 / hp) * cbr2 * (qc[v] - qp[v]);  // lifting of the (+) element
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c == d) g[c][v] = 0.5 * ((m[v][1 + c] + rm) + (pp[v][1 + c] + rp));
+  }
+  double fi[5], fv[3][5];
+  rusanov3(qm, qp, d, a.gam, fi);
+  visc3(qc, g, a.gam, a.mu, a.kappa, 1 << d, fv);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fn[v] = fi[v] - (d == 0 ? fv[0][v] : (d == 1 ? fv[1][v] : fv[2][v]));
+}
+
+__device__ __forceinline__ void coords(long long e, const F3Args& a, int* ix, int* iy, int* iz) {
+  *ix = (int)(e % a.nx);
+  const long long r = e / a.nx;
+  *iy = (int)(r % a.ny);
+  *iz = (int)(r / a.ny);
+}
+
+__device__ __forceinline__ long long elem(int ix, int iy, int iz, const F3Args& a) {
+  return (long long)ix + (long long)a.nx * ((long long)iy + (long long)a.ny * iz);
+}
+
+// neighbour of (ix, iy, iz) across face `face` (periodic) and its size along the face normal
+__device__ __forceinline__ long long neighbour(int ix, int iy, int iz, int face, const F3Args& a, double* h) {
+  const int d = face >> 1, s = (face & 1) ? 1 : -1;
+  if (d == 0) { ix = (ix + a.nx + s) % a.nx; *h = a.hx[ix]; }
+  else if (d == 1) { iy = (iy + a.ny + s) % a.ny; *h = a.hy[iy]; }
+  else { iz = (iz + a.nz + s) % a.nz; *h = a.hz[iz]; }
+  return elem(ix, iy, iz, a);
+}
+
+// reference derivatives of the 5 variables at point t of one element
+template <int N>
+__device__ __forceinline__ void ref_derivs(const double* sq, const double (*sD)[N], int t, double* d0,
+                                           double* d1, double* d2) {
+  constexpr int N2 = N * N, NP = N2 * N;
+  const int i = t % N, j = (t / N) % N, k = t / N2;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double* x = sq + v * NP;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      a0 = fma(sD[i][l], x[l + N * j + N2 * k], a0);
+      a1 = fma(sD[j][l], x[i + N * l + N2 * k], a1);
+      a2 = fma(sD[k][l], x[i + N * j + N2 * l], a2);
+    }
+    d0[v * NP + t] = a0;
+    d1[v * NP + t] = a1;
+    d2[v * NP + t] = a2;
+  }
+}
+
+// full trace (q and physical gradient) of face point (face, f)
+template <int N>
+__device__ __forceinline__ void own_trace(const double* sq, const double* d0, const double* d1,
+                                          const double* d2, int face, int f, const double s[3],
+                                          const double* lm, const double* lp, double o[5][4]) {
+  constexpr int NP = N * N * N;
+  int off, stride;
+  line_of<N>(face >> 1, f, &off, &stride);
+  const double* c = (face & 1) ? lp : lm;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    o[v][0] = tsum3<N>(sq + v * NP + off, stride, c);
+    o[v][1] = s[0] * tsum3<N>(d0 + v * NP + off, stride, c);
+    o[v][2] = s[1] * tsum3<N>(d1 + v * NP + off, stride, c);
+    o[v][3] = s[2] * tsum3<N>(d2 + v * NP + off, stride, c);
+  }
+}
+
+template <int P, bool PERTURB>
+__global__ void __launch_bounds__(256) k3_trace(const F3Args a) {
+  constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E;
+  __shared__ double sq[E][5 * NP], dd[3][E][5 * NP];
+  __shared__ double sD[N][N], slm[N], slp[N];
+  if (threadIdx.x < N * N) sD[threadIdx.x / N][threadIdx.x % N] = a.tab.D[threadIdx.x / N][threadIdx.x % N];
+  if (threadIdx.x < N) {
+    slm[threadIdx.x] = a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = a.tab.lp[threadIdx.x];
+  }
+  if (a.done && *a.done) return;
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  const long long e = (long long)blockIdx.x * E + el;
+  const bool active = el < E && e < a.ne;
+  const double eps = PERTURB ? a.eps2[0] : 0.0;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const long long o = e * 5 * NP + v * NP + t;
+      sq[el][v * NP + t] = PERTURB ? fma(eps, a.z[o], a.U[o]) : a.U[o];
+    }
+  }
+  __syncthreads();
+  if (active) ref_derivs<N>(sq[el], sD, t, dd[0][el], dd[1][el], dd[2][el]);
+  __syncthreads();
+  if (!active) return;
+  int ix, iy, iz;
+  coords(e, a, &ix, &iy, &iz);
+  const double s[3] = {2.0 / a.hx[ix], 2.0 / a.hy[iy], 2.0 / a.hz[iz]};
+  for (int fp = t; fp < 6 * N2; fp += NP) {
+    const int face = fp / N2, f = fp % N2;
+    double o[5][4];
+    own_trace<N>(sq[el], dd[0][el], dd[1][el], dd[2][el], face, f, s, slm, slp, o);
+    double* dst = a.tb + ((e * 6 + face) * N2 + f) * 20;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[v * 4 + c] = o[v][c];
+  }
+}
+
+// one thread per (element, direction d, point of its low face d)
+template <int P>
+__global__ void __launch_bounds__(256) k3_face(const F3Args a) {
+  constexpr int N = P + 1, N2 = N * N;
+  constexpr double cbr2 = (P + 1) * (P + 2) / 2.0;
+  if (a.done && *a.done) return;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.ne * 3 * N2) return;
+  const int f = (int)(tid % N2);
+  const int d = (int)((tid / N2) % 3);
+  const long long e = tid / (3 * N2);
+  int ix, iy, iz;
+  coords(e, a, &ix, &iy, &iz);
+  double hm;
+  const long long nbe = neighbour(ix, iy, iz, 2 * d, a, &hm);
+  const double hp = d == 0 ? a.hx[ix] : (d == 1 ? a.hy[iy] : a.hz[iz]);
+  const double* own = a.tb + ((e * 6 + 2 * d) * N2 + f) * 20;
+  const double* nb = a.tb + ((nbe * 6 + 2 * d + 1) * N2 + f) * 20;
+  double m[5][4], pp[5][4], qc[5], fn[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      m[v][c] = nb[v * 4 + c];
+      pp[v][c] = own[v * 4 + c];
+    }
+  common3(m, pp, d, hm, hp, cbr2, a, qc, fn);
+  double* dst = a.fb + ((e * 3 + d) * N2 + f) * 10;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    dst[v] = qc[v];
+    dst[5 + v] = fn[v];
+  }
+}
+
+// MODE 0: out = R(U); 1: out = A z; 2: out = b - A z (state U + eps z, face
+// data from the face buffer); 3: element-Jacobi column (see the file header)
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
+  using L = CellLayout<P>;
+  constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E, NB = 5 * NP;
+  constexpr bool PERTURB = MODE == 1 || MODE == 2;
+  constexpr bool JAC = MODE == 3;
+  constexpr double cbr2 = (P + 1) * (P + 2) / 2.0;
+  extern __shared__ double smem3[];
+  __shared__ double sD[N][N], sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+  if (a.done && *a.done) return;
+  if (threadIdx.x < N * N) {
+    sD[threadIdx.x / N][threadIdx.x % N] = a.tab.D[threadIdx.x / N][threadIdx.x % N];
+    sDt[threadIdx.x / N][threadIdx.x % N] = a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
+  }
+  if (threadIdx.x < N) {
+    slm[threadIdx.x] = a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = a.tab.lp[threadIdx.x];
+    sdgL[threadIdx.x] = a.tab.dgL[threadIdx.x];
+    sdgR[threadIdx.x] = a.tab.dgR[threadIdx.x];
+  }
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  double* base = smem3 + (size_t)(el < E ? el : 0) * L::PER;
+  double* sq = base;                 // [5][NP]
+  double* d0 = sq + 5 * NP;          // derivatives, then fluxes, along x / y / z
+  double* d1 = d0 + 5 * NP;
+  double* d2 = d1 + 5 * NP;
+  double* dq = d2 + 5 * NP;          // [6][N2][5] q_com - q_face
+  double* fn = dq + 30 * N2;         // [6][N2][5] common total normal flux
+  const long long slot = (long long)blockIdx.x * E + el;
+  const long long nslots = JAC ? a.ne * NB : a.ne;
+  const bool active = el < E && slot < nslots;
+  const long long e = JAC ? slot / NB : slot;
+  const int col = JAC ? (int)(slot % NB) : 0;
+  double eps = 0.0, ieps = 0.0;
+  if (PERTURB) {
+    eps = a.eps2[0];
+    ieps = a.eps2[1];
+  }
+  int ix = 0, iy = 0, iz = 0;
+  double s[3] = {1.0, 1.0, 1.0}, hown[3] = {1.0, 1.0, 1.0};
+  double ceps = 0.0;
+  if (active) {
+    coords(e, a, &ix, &iy, &iz);
+    hown[0] = a.hx[ix];
+    hown[1] = a.hy[iy];
+    hown[2] = a.hz[iz];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = 2.0 / hown[c];
+    if (JAC) ceps = a.beps * (1.0 + fabs(a.U[e * NB + col]));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const long long o = e * NB + v * NP + t;
+      double qv = PERTURB ? fma(eps, a.z[o], a.U[o]) : a.U[o];
+      if (JAC && v * NP + t == col) qv += ceps;
+      sq[v * NP + t] = qv;
+    }
+  }
+  __syncthreads();
+  if (active) ref_derivs<N>(sq, sD, t, d0, d1, d2);
+  __syncthreads();
+  // face data of the six faces
+  if (active) {
+    for (int fp = t; fp < 6 * N2; fp += NP) {
+      const int face = fp / N2, f = fp % N2, d = face >> 1;
+      double qface[5], qc[5], fnum[5];
+      if (JAC) {
+        double o[5][4], nbt[5][4];
+        own_trace<N>(sq, d0, d1, d2, face, f, s, slm, slp, o);
+        double hn;
+        const long long nbe = neighbour(ix, iy, iz, face, a, &hn);
+        const double* src = a.tb + ((nbe * 6 + (face ^ 1)) * N2 + f) * 20;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          qface[v] = o[v][0];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) nbt[v][c] = src[v * 4 + c];
+        }
+        if (face & 1) common3(o, nbt, d, hown[d], hn, cbr2, a, qc, fnum);
+        else common3(nbt, o, d, hn, hown[d], cbr2, a, qc, fnum);
+      } else {
+        int off, stride;
+        line_of<N>(d, f, &off, &stride);
+        const double* c = (face & 1) ? slp : slm;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qface[v] = tsum3<N>(sq + v * NP + off, stride, c);
+        long long fe = e;
+        if (face & 1) {
+          double hn;
+          fe = neighbour(ix, iy, iz, face, a, &hn);
+        }
+        const double* src = a.fb + ((fe * 3 + d) * N2 + f) * 10;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          qc[v] = src[v];
+          fnum[v] = src[5 + v];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        dq[(face * N2 + f) * 5 + v] = qc[v] - qface[v];
+        fn[(face * N2 + f) * 5 + v] = fnum[v];
+      }
+    }
+  }
+  __syncthreads();
+  const int i = t % N, j = (t / N) % N, k = t / N2;
+  const int f0 = j + N * k, f1 = i + N * k, f2 = i + N * j;  // this point's face points per direction
+  // corrected gradient and total fluxes at the own point (overwrite d0..d2)
+  if (active) {
+    double q[5], g[3][5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      q[v] = sq[v * NP + t];
+      double x = d0[v * NP + t];
+      x = fma(dq[(0 * N2 + f0) * 5 + v], sdgL[i], x);
+      x = fma(dq[(1 * N2 + f0) * 5 + v], sdgR[i], x);
+      double y = d1[v * NP + t];
+      y = fma(dq[(2 * N2 + f1) * 5 + v], sdgL[j], y);
+      y = fma(dq[(3 * N2 + f1) * 5 + v], sdgR[j], y);
+      double zz = d2[v * NP + t];
+      zz = fma(dq[(4 * N2 + f2) * 5 + v], sdgL[k], zz);
+      zz = fma(dq[(5 * N2 + f2) * 5 + v], sdgR[k], zz);
+      g[0][v] = s[0] * x;
+      g[1][v] = s[1] * y;
+      g[2][v] = s[2] * zz;
+    }
+    double fv[3][5];
+    visc3(q, g, a.gam, a.mu, a.kappa, 7, fv);
+    double* dst[3] = {d0, d1, d2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double fi[5];
+      (void)flux3(q, d, a.gam, fi);
+      // each thread reads and overwrites only its own point
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dst[d][v * NP + t] = fi[v] - fv[d][v];
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double* F = d0 + v * NP;
+    const double* G = d1 + v * NP;
+    const double* H = d2 + v * NP;
+    double dF = sdgL[i] * fn[(0 * N2 + f0) * 5 + v];
+    dF = fma(sdgR[i], fn[(1 * N2 + f0) * 5 + v], dF);
+    double dG = sdgL[j] * fn[(2 * N2 + f1) * 5 + v];
+    dG = fma(sdgR[j], fn[(3 * N2 + f1) * 5 + v], dG);
+    double dH = sdgL[k] * fn[(4 * N2 + f2) * 5 + v];
+    dH = fma(sdgR[k], fn[(5 * N2 + f2) * 5 + v], dH);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      dF = fma(sDt[i][l], F[l + N * j + N2 * k], dF);
+      dG = fma(sDt[j][l], G[i + N * l + N2 * k], dG);
+      dH = fma(sDt[k][l], H[i + N * j + N2 * l], dH);
+    }
+    const double R = -fma(s[0], dF, fma(s[1], dG, s[2] * dH));
+    const long long o = e * NB + v * NP + t;
+    if (MODE == 0) {
+      a.out[o] = R;
+    } else if (MODE == 3) {
+      // column col of M = shift I - J_ee, staged column-major [col][row]
+      const int row = v * NP + t;
+      a.out[(e * NB + col) * NB + row] = (row == col ? a.shift : 0.0) - (R - a.R0[o]) / ceps;
+    } else {
+      const double zo = a.z[o];
+      const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
+      a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
+    }
+  }
+}
+
+// Quadrature sums of S^d : S^d, p div v and rho |v|^2 / 2 (weights w_i w_j w_k
+// |J_e|) for the dissipation rate; the velocity of each element is
+// differentiated as its degree-p interpolant.  Grid-stride over element
+// groups, deterministic two-stage reduction into out[0..2].
+template <int P>
+__global__ void __launch_bounds__(256) k3_dissipation(const F3Args a, Reduce red, double* out) {
+  constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E;
+  __shared__ double vel[E][3][NP];
+  __shared__ double sD[N][N], sw[N], sh[32];
+  if (threadIdx.x < N * N) sD[threadIdx.x / N][threadIdx.x % N] = a.tab.D[threadIdx.x / N][threadIdx.x % N];
+  if (threadIdx.x < N) sw[threadIdx.x] = a.tab.w[threadIdx.x];
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  const int i = t % N, j = (t / N) % N, k = t / N2;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long e0 = (long long)blockIdx.x * E; e0 < a.ne; e0 += (long long)gridDim.x * E) {
+    const long long e = e0 + el;
+    const bool active = el < E && e < a.ne;
+    double q[5];
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) q[v] = a.U[e * 5 * NP + v * NP + t];
+      const double ri = 1.0 / q[0];
+      vel[el][0][t] = q[1] * ri;
+      vel[el][1][t] = q[2] * ri;
+      vel[el][2][t] = q[3] * ri;
+    }
+    __syncthreads();
+    if (active) {
+      int ix, iy, iz;
+      coords(e, a, &ix, &iy, &iz);
+      const double hx = a.hx[ix], hy = a.hy[iy], hz = a.hz[iz];
+      const double s[3] = {2.0 / hx, 2.0 / hy, 2.0 / hz};
+      double G[3][3];  // G[m][c] = d v_m / d x_c
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double* x = vel[el][m];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          a0 = fma(sD[i][l], x[l + N * j + N2 * k], a0);
+          a1 = fma(sD[j][l], x[i + N * l + N2 * k], a1);
+          a2 = fma(sD[k][l], x[i + N * j + N2 * l], a2);
+        }
+        G[m][0] = s[0] * a0;
+        G[m][1] = s[1] * a1;
+        G[m][2] = s[2] * a2;
+      }
+      const double div = G[0][0] + G[1][1] + G[2][2];
+      double ss = 0.0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double Sd = 0.5 * (G[m][c] + G[c][m]) - (m == c ? div / 3.0 : 0.0);
+          ss = fma(Sd, Sd, ss);
+        }
+      const double u = vel[el][0][t], v = vel[el][1][t], w = vel[el][2][t];
+      const double ke2 = q[0] * (u * u + v * v + w * w);
+      const double pr = (a.gam - 1.0) * (q[4] - 0.5 * ke2);
+      const double wt = sw[i] * sw[j] * sw[k] * (0.125 * hx * hy * hz);
+      acc[0] = fma(wt, ss, acc[0]);
+      acc[1] = fma(wt, pr * div, acc[1]);
+      acc[2] = fma(wt, 0.5 * ke2, acc[2]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double bs = block_sum(acc[c], sh);
+    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec + c] = bs;
+  }
+  if (last_block(red.counter)) finish_sums(red, 3, out);
+}
+
+F3Args make_args3(fr_ctx* ctx) {
+  F3Args a{};
+  a.tb = ctx->tb;
+  a.fb = ctx->fb;
+  a.hx = ctx->hx;
+  a.hy = ctx->hy;
+  a.hz = ctx->hz;
+  a.ne = ctx->ne;
+  a.nx = ctx->nx;
+  a.ny = ctx->ny;
+  a.nz = ctx->nz;
+  a.gam = ctx->opts.gamma;
+  a.mu = ctx->opts.mu;
+  const double cp = ctx->opts.gamma / (ctx->opts.gamma - 1.0);  // R = 1
+  a.kappa = ctx->opts.mu > 0.0 ? ctx->opts.mu * cp / ctx->opts.prandtl : 0.0;
+  a.beps = ctx->opts.block_eps_rel;
+  a.tab = ctx->tab;
+  return a;
+}
+
+template <int P>
+int f3_launch(fr_ctx* ctx, int mode, const F3Args& a, bool perturb_trace, cudaStream_t s, double wb,
+              double wf) {
+  using L = CellLayout<P>;
+  constexpr int NP = L::NP, N2 = L::N2, E = F3Slots<P>::E, NB = 5 * NP;
+  static bool attr = false;  // dynamic shared memory above 48 KB, set once per process
+  if (!attr) {
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    attr = true;
+  }
+  const unsigned gt = (unsigned)((ctx->ne + E - 1) / E);
+  const int fam = mode == 3 ? FR_KF_FACTOR : (mode == 0 ? FR_KF_RESIDUAL : FR_KF_JV);
+  {
+    ProfScope ps_(ctx, fam, s, wb, wf);  // one timed record for the three kernels
+    if (perturb_trace) k3_trace<P, true><<<gt, E * NP, 0, s>>>(a);
+    else k3_trace<P, false><<<gt, E * NP, 0, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    count_launch();  // the scope counted the trace kernel
+    if (mode == 3) {
+      const long long g3 = (ctx->ne * NB + E - 1) / E;
+      k3_cell<P, 3><<<(unsigned)g3, E * NP, L::BYTES, s>>>(a);
+    } else {
+      const long long nf = ctx->ne * 3 * N2;
+      k3_face<P><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(a);
+      FRK_LAUNCHED(ctx);
+      count_launch();
+      if (mode == 0) k3_cell<P, 0><<<gt, E * NP, L::BYTES, s>>>(a);
+      else if (mode == 1) k3_cell<P, 1><<<gt, E * NP, L::BYTES, s>>>(a);
+      else k3_cell<P, 2><<<gt, E * NP, L::BYTES, s>>>(a);
+    }
+  }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int f3_dispatch(fr_ctx* ctx, int mode, const F3Args& a, bool perturb_trace, cudaStream_t s, double wb,
+                double wf) {
+  switch (ctx->p) {
+    case 1: return f3_launch<1>(ctx, mode, a, perturb_trace, s, wb, wf);
+    case 2: return f3_launch<2>(ctx, mode, a, perturb_trace, s, wb, wf);
+    case 3: return f3_launch<3>(ctx, mode, a, perturb_trace, s, wb, wf);
+    case 4: return f3_launch<4>(ctx, mode, a, perturb_trace, s, wb, wf);
+    default: return set_error(ctx, FR_ERR_UNSUPPORTED, "3D degree %d not compiled", ctx->p);
+  }
+}
+
+template <int P>
+int dissipation_launch(fr_ctx* ctx, const double* U, double* out, cudaStream_t s) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1), E = F3Slots<P>::E;
+  F3Args a = make_args3(ctx);
+  a.U = U;
+  long long g = (ctx->ne + E - 1) / E;
+  if (g > kRedBlocks) g = kRedBlocks;
+  const int threads = (E * NP + 31) / 32 * 32;  // whole warps (the reductions shuffle)
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k3_dissipation<P><<<(unsigned)g, threads, 0, s>>>(a, ctx->red, out); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+}  // namespace
+
+// Navier-Stokes residual per element in 3D, counted like the 2D one (a fused
+// multiply-add = 2) from the method's steps, each once: the reference
+// derivatives of the 5 variables along 3 directions (30 Np N); the face
+// traces of (q, grad q) (6 N^2 faces points x 20 values x 2N); per face point,
+// with each face shared by two elements (3 N^2 per element), averages and
+// BR2 liftings (60), Rusanov (90), the viscous flux (90) and the total (5);
+// per point the corrected gradient (75), the inviscid fluxes (45), the
+// viscous fluxes (120), their difference (15), the corrected divergence
+// (30 (N+2)) and the scaling (5).
+double ns3d_residual_flops_per_element(int p) {
+  const double N = p + 1, N2 = N * N, Np = N2 * N;
+  return 30 * Np * N + 240 * N2 * N + 3 * N2 * (60 + 90 + 90 + 5) +
+         Np * (75 + 45 + 120 + 15 + 30 * (N + 2) + 5);
+}
+
+int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
+                       const double* b, double* out, double shift, const double* eps2,
+                       const int* done, cudaStream_t s) {
+  F3Args a = make_args3(ctx);
+  a.U = U;
+  a.z = z;
+  a.R0 = R0;
+  a.b = b;
+  a.out = out;
+  a.eps2 = eps2;
+  a.done = done;
+  a.shift = shift;
+  // inside a GMRES cycle all kernels return at once once the cycle is done
+  const double nd = (double)ctx->ndof;
+  const bool in_cycle = done != nullptr;
+  const double wb = in_cycle ? 0.0 : (mode == 0 ? 16.0 : (mode == 1 ? 32.0 : 40.0)) * nd;
+  const double wf = in_cycle ? 0.0 : ns3d_residual_flops_per_element(ctx->p) * (double)ctx->ne + (mode == 0 ? 0.0 : 6.0 * nd);
+  return f3_dispatch(ctx, mode, a, mode != 0, s, wb, wf);
+}
+
+int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
+  if (ctx->p > 2 || !ctx->mst)
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "3D element blocks are built for degrees 1 and 2");
+  // R0 of the element-local residuals = R(U) with the same (unperturbed) traces
+  F3Args a = make_args3(ctx);
+  a.U = U;
+  a.out = ctx->rloc;
+  FRK_TRY(f3_dispatch(ctx, 0, a, false, s, 0.0, 0.0));
+  a.R0 = ctx->rloc;
+  a.out = ctx->mst;
+  a.shift = shift;
+  FRK_TRY(f3_dispatch(ctx, 3, a, false, s, 0.0, 0.0));
+  return launch_block_invert(ctx, ctx->mst, 0.0, s);
+}
+
+int launch_f3_dissipation(fr_ctx* ctx, const double* U, double* out, cudaStream_t s) {
+  switch (ctx->p) {
+    case 1: return dissipation_launch<1>(ctx, U, out, s);
+    case 2: return dissipation_launch<2>(ctx, U, out, s);
+    case 3: return dissipation_launch<3>(ctx, U, out, s);
+    case 4: return dissipation_launch<4>(ctx, U, out, s);
+    default: return set_error(ctx, FR_ERR_UNSUPPORTED, "3D degree %d not compiled", ctx->p);
+  }
+}
+
+}  // namespace frk

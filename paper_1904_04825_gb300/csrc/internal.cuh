@@ -11,7 +11,7 @@
 
 namespace frk {
 
-constexpr int kMaxN = 7;          // p <= 6 (Euler); p <= 4 with viscous terms
+constexpr int kMaxN = 7;          // p <= 6 (2D Euler); p <= 4 with viscous terms and in 3D
 constexpr int kThreads = 256;     // default block size of the vector kernels
 constexpr int kMaxVec = 64;       // largest Krylov basis slice handled per call (m_max + 1)
 constexpr int kVecBlocks = 456;   // default grid of the streaming vector kernels (3 x 152 SMs)
@@ -103,6 +103,11 @@ struct StageCapture {
 struct fr_ctx {
   int device = 0;
   int nx = 0, ny = 0, p = 0, n1 = 0, np = 0, nb = 0;
+  int dim3 = 0;              // 3D hexahedral Navier-Stokes path (5 variables, Np = (p+1)^3)
+  int nz = 1;
+  double* hz = nullptr;      // 3D: [nz] element depths (device)
+  double volume = 0.0;       // 3D: volume of the periodic box
+  double* diss = nullptr;    // 3D: the three quadrature sums of the dissipation rate
   long long ne = 0, ndof = 0;
   fr_opts opts{};
   frk::Tables tab{};
@@ -235,6 +240,14 @@ int launch_ns_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
                        const double* b, double* out, double shift, const double* eps2,
                        const int* done, cudaStream_t s);
 int launch_ns_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
+// fr3d.cu (3D path): mode 0 R, 1 A z, 2 b - A z; element blocks (p <= 2);
+// quadrature sums (S^d:S^d, p div v, rho |v|^2/2) of the dissipation rate into out[0..2]
+double ns3d_residual_flops_per_element(int p);
+int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
+                       const double* b, double* out, double shift, const double* eps2,
+                       const int* done, cudaStream_t s);
+int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
+int launch_f3_dissipation(fr_ctx* ctx, const double* U, double* out, cudaStream_t s);
 // blocks.cu: invert staged FP64 blocks (column-major M[c][row], dshift added to
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);

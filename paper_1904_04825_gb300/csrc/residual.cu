@@ -455,6 +455,7 @@ int launch_p(fr_ctx* ctx, int mode, const ResArgs& a, cudaStream_t s) {
 int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, const double* R0,
                     const double* b, double* out, double shift, const double* eps2,
                     const int* done, cudaStream_t s) {
+  if (ctx->dim3) return launch_f3_residual(ctx, mode, U, z, R0, b, out, shift, eps2, done, s);
   if (ctx->viscous) return launch_ns_residual(ctx, mode, U, z, R0, b, out, shift, eps2, done, s);
   ResArgs a;
   a.U = U; a.z = z; a.R0 = R0; a.b = b; a.out = out;
@@ -476,7 +477,7 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
 }
 
 int launch_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
-  if (ctx->opts.jv_precision != 1 || ctx->viscous) return FR_OK;
+  if (ctx->opts.jv_precision != 1 || ctx->viscous || ctx->dim3) return FR_OK;
   return launch_residual(ctx, 3, U, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, s);
 }
 

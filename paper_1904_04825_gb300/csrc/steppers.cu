@@ -918,7 +918,7 @@ extern "C" int fr_autotune(fr_ctx* ctx, const double* U, double shift, int reps,
   int best_vb = vb0, best_tv = tv0;
   if (rc == FR_OK) rc = time_cycles(ctx, U, shift, reps, e0, e1, &dflt, s);
   best = dflt;
-  const int ntv = ctx->viscous ? 1 : 2;  // the viscous residual has one tile shape
+  const int ntv = (ctx->viscous || ctx->dim3) ? 1 : 2;  // the viscous and 3D residuals have one tile shape
   for (int tv = 0; tv < ntv && rc == FR_OK; ++tv)
     for (int vb : kTuneGrids) {
       ctx->vec_blocks = vb;
