@@ -219,9 +219,10 @@ def our_arm(args):
         U0 = tg.state(X, Y, Z)
         del X, Y, Z
         dt, wall = (args.dt or tg.t_c / 25.0), False
-        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
-                               mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 2 else 0)
-        wl = f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}" + ("" if p <= 2 else "-noprecond")
+        opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=args.gmres_m, m_max=args.gmres_m, gmres_max_restarts=20,
+                               block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 2 else 0)
+        wl = (f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}-gmres{args.gmres_m}"
+              + ("" if p <= 2 else "-noprecond"))
     else:
         ch = S.Channel()
         xe = np.linspace(0.0, ch.lx, 257)
@@ -334,6 +335,20 @@ def our_arm(args):
             dist.destroy_process_group()
         return 0
 
+    # workload description from the context actually built
+    m_used = ctx.opts.gmres_m
+    nb = ctx.ndof // ctx.ne
+    blk_bytes = ctx.ne * nb * nb * (8, 4, 2)[prec] if ctx.opts.precond else 0
+    basis_bytes = (m_used + 1) * ctx.ndof * 8
+    gmres_desc = (f"GMRES({m_used}), " + ("element-Jacobi" if ctx.opts.precond else "no preconditioner")
+                  + f", tol {ctx.opts.tol_lin:g}")
+    l2_desc = f"inputs larger than L2 (blocks {blk_bytes / 1e9:.2f} GB + Krylov basis {basis_bytes / 1e9:.2f} GB)"
+    if args.workload == "vortex":
+        cfl = round(dt * 3 * math.sqrt(2) * (p + 1) / (10.0 / NX), 2)
+    elif args.workload == "tgv":   # (|v|max + c0)(p+1) dt / h with |v|max = V0, c0 = V0 / Ma
+        cfl = round(dt * (1.0 + 10.0) * (p + 1) / (2 * math.pi / ctx.nx), 2)
+    else:
+        cfl = None
     avg_launch_s = prof["ms"] / max(prof["launches"], 1) * 1e-3
     work_flops = prof["flops"] / max(prof["launches"], 1)
     work_bytes = prof["bytes"] / max(prof["launches"], 1)
@@ -382,6 +397,7 @@ def our_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config({"parallelism": f"replicas x{world}", "gmres_iters_per_step": iters / args.steps,
+                           "p": p, "cfl": cfl, "gmres": gmres_desc, "l2": l2_desc,
                            "block_precision": args.block_precision, "jv_precision": args.jv_precision,
                            "workload": wl,
                            "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
@@ -495,12 +511,23 @@ def kernel_arm(args):
     torch.cuda.set_device(0)
     if args.kernel in ("mlp", "mlp_train"):
         return mlp_kernel_arm(args)
-    xe, ye = S.uniform_mesh(NX)
-    X, Y = S.point_coords(xe, ye, P)
-    U = torch.from_numpy(S.Vortex().state(X, Y)).cuda()
     prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
-    ctx = fr.Context(xe, ye, P, fr.default_opts(block_precision=prec,
-                                                jv_precision=1 if args.jv_precision == "fp32" else 0))
+    if args.workload == "tgv":
+        # the 3D operator on the Taylor-Green field (64^3 hexahedra, p = 3 by default)
+        tg = S.TaylorGreen()
+        p3, n3 = args.p or 3, args.nx or 64
+        edges = S.uniform_mesh3d(n3)
+        X, Y, Z = S.point_coords3d(*edges, p3)
+        U = torch.from_numpy(tg.state(X, Y, Z)).cuda()
+        del X, Y, Z
+        ctx = fr.Context3D(*edges, p3, fr.default_opts(block_precision=prec, mu=tg.mu, prandtl=tg.prandtl,
+                                                        precond=1 if p3 <= 2 else 0, m_max=4, gmres_m=4))
+    else:
+        xe, ye = S.uniform_mesh(NX)
+        X, Y = S.point_coords(xe, ye, P)
+        U = torch.from_numpy(S.Vortex().state(X, Y)).cuda()
+        ctx = fr.Context(xe, ye, P, fr.default_opts(block_precision=prec,
+                                                    jv_precision=1 if args.jv_precision == "fp32" else 0))
     R = ctx.empty()
     fr.fr_residual(ctx, U, R)
     z = torch.from_numpy(S.random_vector(ctx.shape, 1)).cuda()
@@ -523,7 +550,8 @@ def kernel_arm(args):
     torch.cuda.synchronize()
     pr = fr.fr_profile_end(ctx)[args.kernel]
     us = pr["ms"] / max(pr["launches"], 1) * 1e3
-    print(json.dumps({"kernel": args.kernel, "block_precision": args.block_precision,
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "ndof": ctx.ndof,
+                      "block_precision": args.block_precision,
                       "jv_precision": args.jv_precision,
                       "launches": pr["launches"], "avg_us": us,
                       "tflops": pr["flops"] / pr["launches"] / (us * 1e-6) / 1e12,
