@@ -76,3 +76,34 @@ def test_defaults_and_argument_checks_without_gpu(libpath):
     assert fr.lib.fr_ctx_create(ctypes.byref(desc), 2, ctypes.byref(bad), ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
     assert fr.lib.fr_residual(None, None, None, None) == fr.FR_ERR_INVALID_ARG
     assert fr.lib.fr_last_error(None) is not None
+
+
+def test_3d_argument_checks_without_gpu(libpath):
+    """fr_ctx_create_3d validates its mesh, degree and options on the host
+    before any device call."""
+    import numpy as np
+    import paper_1904_04825_gb300 as fr
+    h = ctypes.c_void_p()
+    e3 = np.linspace(-1.0, 1.0, 3)
+    dp = e3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    desc = fr.fr_mesh3d_desc(2, 2, 2, dp, dp, dp)
+
+    def create(d, p, **kw):
+        o = fr.default_opts(**kw)
+        return fr.lib.fr_ctx_create_3d(ctypes.byref(d), p, ctypes.byref(o), ctypes.byref(h))
+    assert create(desc, 5, precond=0) == fr.FR_ERR_UNSUPPORTED          # degrees 1-4
+    assert create(desc, 0, precond=0) == fr.FR_ERR_UNSUPPORTED
+    assert create(desc, 3) == fr.FR_ERR_UNSUPPORTED                      # 320-row blocks not built
+    assert create(desc, 2, riemann=1) == fr.FR_ERR_UNSUPPORTED           # Rusanov only
+    assert create(desc, 2, jv_precision=1) == fr.FR_ERR_UNSUPPORTED
+    assert create(desc, 2, guess=2) == fr.FR_ERR_UNSUPPORTED
+    assert create(desc, 2, body_force_x=0.1) == fr.FR_ERR_UNSUPPORTED
+    assert create(desc, 2, m_max=64) == fr.FR_ERR_INVALID_ARG
+    thin = fr.fr_mesh3d_desc(2, 2, 1, dp, dp, dp)
+    assert create(thin, 2) == fr.FR_ERR_INVALID_ARG
+    down = np.array([1.0, 0.0, -1.0])
+    dd = down.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert create(fr.fr_mesh3d_desc(2, 2, 2, dp, dp, dd), 2) == fr.FR_ERR_INVALID_ARG
+    assert fr.lib.fr_ctx_create_3d(None, 2, None, ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
+    out = (ctypes.c_double * 3)()
+    assert fr.lib.fr_dissipation_rate(None, None, 1.0, out, None) == fr.FR_ERR_INVALID_ARG

@@ -180,3 +180,40 @@ def test_ssprk3_step_on_the_3d_problem():
     t1, _ = _mean(U1, prob.mesh, p)
     assert np.all(np.abs(t1 - t0) < 1e-12 * np.maximum(s0, 1.0))
     assert np.max(np.abs(U1 - U)) > 1e-6
+
+
+def _rk4_density_wave_3d(n, p, t_end=0.3, cfl=0.2):
+    """L2 density error of a density wave rho = 1 + 0.2 sin(x + y + z)
+    translated by v = (1, 1, 1) at constant pressure (an exact solution of
+    the Euler equations) after classical RK4 steps small enough that the
+    spatial error dominates."""
+    edges = S.uniform_mesh3d(n)
+    X, Y, Z = S.point_coords3d(*edges, p)
+
+    def exact(t):
+        one = np.ones_like(X)
+        return S.conserved3d(1.0 + 0.2 * np.sin((X - t) + (Y - t) + (Z - t)), one, one, one, one)
+    U = exact(0.0)
+    m, b = Mesh3D(*edges), Basis(p)
+    h = 2 * math.pi / n
+    dt0 = cfl * h / ((p + 1) ** 2 * 3.0)
+    nsteps = int(math.ceil(t_end / dt0))
+    dt = t_end / nsteps
+    f = lambda u: residual3d(u, m, p, Gas3D(), b)
+    for _ in range(nsteps):
+        k1 = f(U)
+        k2 = f(U + 0.5 * dt * k1)
+        k3 = f(U + 0.5 * dt * k2)
+        k4 = f(U + dt * k3)
+        U = U + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    w3 = np.einsum("k,j,i->kji", b.w, b.w, b.w).reshape(-1)
+    err2 = np.einsum("ep,p->", (U[:, 0] - exact(t_end)[:, 0]) ** 2, w3) * h ** 3 / 8
+    return math.sqrt(err2 / (2 * math.pi) ** 3)
+
+
+def test_spatial_order_on_a_3d_density_wave():
+    """Order p + 1 = 2 at p = 1 under h-refinement along a wave that crosses
+    all three directions, and a smaller error at p = 2 on the same mesh."""
+    e4, e8 = _rk4_density_wave_3d(4, 1), _rk4_density_wave_3d(8, 1)
+    assert math.log2(e4 / e8) > 2 - 0.3
+    assert _rk4_density_wave_3d(4, 2) < e4 / 4
