@@ -277,7 +277,7 @@ int step_ssprk3(fr_ctx* ctx, double dt, double* U, fr_step_stats* stats, void* s
  * Network 3nb -> hidden -> hidden -> nb, ReLU,
  * FP32 master weights.  Training kernels run in FP32 on the CUDA cores
  * (gradients checkable against an FP64 reference); inference runs BF16
- * operands on the tcgen05 tensor cores with FP32 accumulation.  GMRES judges the
+ * operands on the tcgen05 tensor cores with FP32 accumulation.  GMRES tests the
  * guess: a stage solved from it still stops at tol_lin * ||b||. */
 typedef struct fr_mlp fr_mlp;
 /* Create a model (device memory for up to max_batch samples). */

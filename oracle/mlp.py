@@ -1,6 +1,6 @@
 """Per-element MLP that predicts a stage solve's initial Krylov guess.
 
-Not in the paper (a learned addition around its GMRES, which still judges
+Not in the paper (a learned addition around its GMRES, which still tests
 the result: the solve converges to the same tolerance from any guess).
 
 Network: x (3 nb features of one element) -> Linear(3nb, 256) -> ReLU ->

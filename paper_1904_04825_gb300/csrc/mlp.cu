@@ -1,5 +1,5 @@
 // Per-element MLP that predicts a stage solve's initial Krylov guess (not in
-// the paper; the GMRES solve still judges the guess and converges to the
+// the paper; the GMRES solve still tests the guess and converges to the
 // same tolerance).
 //
 // Network 3nb -> 256 -> 256 -> nb, ReLU, FP32 master weights.

@@ -158,7 +158,7 @@ def test_learned_guess_in_row_stages(fr):
     """Train on stage solves captured from plain ROW2 steps (zero guess) of
     20 x 20, p = 2 vortices; then run a held-out vortex with the zero guess,
     the previous-step guess and the learned guess at tol_lin = 1e-8.  GMRES
-    judges every guess (same absolute target tol * ||b||), so the states
+    tests every guess (same absolute target tol * ||b||), so the states
     agree at the tolerance level; the guesses cut iterations.  At
     tol_lin = 1e-12 the learned-guess run matches the oracle to 1e-9."""
     import torch
