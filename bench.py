@@ -174,6 +174,20 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------ our arm --
+def combine_ranks(dist, slowest, summed, device):
+    """Whole-job figures of independent replicas: the maximum over ranks of
+    each time in `slowest`, the sum over ranks of each work count in
+    `summed`.  Every rank calls it (collective); dist None: one rank."""
+    if dist is None:
+        return list(slowest), list(summed)
+    import torch
+    t = torch.tensor(list(slowest), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor(list(summed), dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [float(x) for x in u]
+
+
 def our_arm(args):
     import numpy as np
     import torch
@@ -322,13 +336,7 @@ def our_arm(args):
     ndof = ctx.ndof
     units = float(ndof) * iters
     e2e_units = float(ndof) * e2e_iters
-    if dist is not None:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([units, e2e_units], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms, e2e_s = float(t[0]), float(t[1])
-        units, e2e_units = float(u[0]), float(u[1])
+    (ms, e2e_s), (units, e2e_units) = combine_ranks(dist, [ms, e2e_s], [units, e2e_units], dev)
 
     if rank != 0:
         if dist is not None:
@@ -681,13 +689,8 @@ def batch_arm(args):
         torch.cuda.synchronize()
         host_in, host_out = host_out, host_in
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([ms, e2e_s, ms_seq], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([units, e2e_units, units_seq], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms, e2e_s, ms_seq = (float(x) for x in t)
-        units, e2e_units, units_seq = (float(x) for x in u)
+    (ms, e2e_s, ms_seq), (units, e2e_units, units_seq) = combine_ranks(
+        dist, [ms, e2e_s, ms_seq], [units, e2e_units, units_seq], dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

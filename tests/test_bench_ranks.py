@@ -1,0 +1,60 @@
+"""Host logic of the benchmark's N > 1 path on CPU: independent replicas,
+whole-job time = the slowest rank, work = the sum over ranks, and the
+reference arm runs on rank 0 only.  Two gloo ranks, no GPU."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import json
+    import sys
+
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    # rank r took (10 + r) ms and 3 + r seconds end to end, did 100 (r + 1) units
+    slow, summed = bench.combine_ranks(dist, [10.0 + rank, 3.0 + rank], [100.0 * (rank + 1), 7.0], "cpu")
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump({"slow": slow, "summed": summed}, f)
+
+
+def test_two_gloo_ranks_combine_max_time_and_summed_work(tmp_path):
+    import json
+
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        d = json.load(open(tmp_path / f"rank{r}.json"))
+        assert d["slow"] == [11.0, 4.0]          # the slowest rank's times
+        assert d["summed"] == [300.0, 14.0]      # work of both ranks
+
+
+def test_single_rank_passes_figures_through():
+    import bench
+    assert bench.combine_ranks(None, [1.5, 2.0], [3.0], "cpu") == ([1.5, 2.0], [3.0])
+
+
+def test_reference_arm_does_no_work_off_rank_0(monkeypatch, capsys):
+    import types
+
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    def boom(*a, **k):
+        raise AssertionError("rank 1 must not run the oracle")
+    monkeypatch.setattr(bench, "run_oracle_sample", boom)
+    assert bench.reference_arm(types.SimpleNamespace(steps=2, warmup=3, gpus=2)) == 0
+    assert capsys.readouterr().out == ""
