@@ -217,3 +217,30 @@ def test_spatial_order_on_a_3d_density_wave():
     e4, e8 = _rk4_density_wave_3d(4, 1), _rk4_density_wave_3d(8, 1)
     assert math.log2(e4 / e8) > 2 - 0.3
     assert _rk4_density_wave_3d(4, 2) < e4 / 4
+
+
+def test_viscous_shear_flow_closed_form():
+    """w = A sin x with rho = 1, u = v = 0 and constant pressure: a closed
+    form of the viscous terms along z (the direction the 2D reduction does
+    not reach).  The continuous residual is R_rhow = -mu A sin x, R_E =
+    mu A^2 cos 2x and zero otherwise.  R_rho and R_rhov vanish to round-off;
+    R_rhow converges to the closed form at about order p in the maximum norm
+    (the residual is a second derivative of the interpolated state); R_rhou
+    is the BR2 broken-gradient term on the z faces and vanishes at the same
+    order; R_E, whose heat flux differentiates the chain-rule temperature
+    gradient once more, converges at about order p - 1."""
+    A, mu, p = 0.3, 0.05, 3
+    errs = []
+    for n in (8, 16):
+        ex, e2 = S.uniform_edges(n, -math.pi, math.pi), S.uniform_edges(2, -math.pi, math.pi)
+        X, Y, Z = S.point_coords3d(ex, e2, e2, p)
+        one = np.ones_like(X)
+        U = S.conserved3d(one, 0 * one, 0 * one, A * np.sin(X), 2.0 * one)
+        R = residual3d(U, Mesh3D(ex, e2, e2), p, Gas3D(mu=mu))
+        assert np.max(np.abs(R[:, [0, 2]])) < 1e-13
+        errs.append((np.max(np.abs(R[:, 3] + mu * A * np.sin(X))),
+                     np.max(np.abs(R[:, 1])),
+                     np.max(np.abs(R[:, 4] - mu * A * A * np.cos(2 * X)))))
+    order = [math.log2(errs[0][c] / errs[1][c]) for c in range(3)]
+    assert order[0] > p - 0.5 and order[1] > p - 0.5 and order[2] > p - 1.5
+    assert errs[1][0] < 0.01 * mu * A
