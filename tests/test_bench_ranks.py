@@ -58,3 +58,20 @@ def test_reference_arm_does_no_work_off_rank_0(monkeypatch, capsys):
     monkeypatch.setattr(bench, "run_oracle_sample", boom)
     assert bench.reference_arm(types.SimpleNamespace(steps=2, warmup=3, gpus=2)) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """The reference arm (the oracle on the host) prints one JSON line with
+    the keys the benchmark contract asks of it (one short oracle step)."""
+    import json
+    import types
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    assert bench.reference_arm(types.SimpleNamespace(steps=1, warmup=0, gpus=1)) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
