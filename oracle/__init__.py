@@ -21,6 +21,7 @@ step, NumPy doing only library work (matrix products, dense solves, norms):
   tableaus   ROW / ESDIRK coefficient sets (Sec. 4.2, 4.3)
   steppers   ROW, ESDIRK + pseudo-transient continuation + SER, BDF2, SSPRK3 (Sec. 4.1-4.4)
   mlp        per-element MLP forward, backward, Adam (learned initial guess)
+  vortex     exact isentropic vortex (Eq. VP_Solution) and the error norm of Sec. 5.1
 
 Parity status of each function is stated in its module docstring; every
 function listed above is pinned by a ``-m "not gpu"`` test against facts the
