@@ -42,6 +42,7 @@ UNIT = "DOF*iter/s"
 WORKLOAD = "vortex-160x160-p3-ROW3-dt0.05-gmres30-tol1e-6"
 FP64_PEAK_TFLOPS = 1.259  # 152 SMs x 4 FP64 flops/clk/SM x 2.07 GHz (nominal 1.25 TF)
 REF_NX = 24               # oracle sample mesh (same p, scheme, CFL, tolerance)
+REF_ARM_NX = 16           # smaller sample for the per-step reference arm
 
 
 def _config(extra=None):
@@ -118,8 +119,6 @@ from oracle.jfnk import Problem
 from oracle.steppers import SolverOpts, step_row
 from oracle.tableaus import ROW
 n, p, steps = {n}, {p}, {steps}
-h = 10.0 / n
-dt = {dt} * (h / (10.0 / {nx_full}))
 xe, ye = S.uniform_mesh(n)
 X, Y = S.point_coords(xe, ye, p)
 U = S.Vortex().state(X, Y)
@@ -128,45 +127,117 @@ opts = SolverOpts(tol_lin={tol}, m=30, max_restarts=20)
 out = []
 for k in range(steps):
     t0 = time.perf_counter()
-    U, st = step_row(prob, ROW[{scheme}](), dt, U, opts)
+    U, st = step_row(prob, ROW[{scheme}](), {dt}, U, opts)
     out.append((time.perf_counter() - t0, st.gmres_iters))
 print(json.dumps({{"ndof": prob.ndof, "steps": out}}))
 """
 
+# Oracle samples.  C2 sample: ROW3 steps of the vortex on a coarser mesh at
+# the benchmark's p, CFL 13.6 and tolerance (the unit is per DOF, so the rate
+# is comparable); C1: the small configuration in full (20x20 p=2, ROW2, ten
+# steps of dt = 0.05, GMRES(30) to 1e-8).
+C2_SAMPLE = {"n": REF_NX, "p": P, "scheme": SCHEME, "tol": TOL_LIN, "dt": DT * (NX / REF_NX)}
+C1_FULL = {"n": 20, "p": 2, "scheme": 2, "tol": 1e-8, "dt": 0.05}
 
-def run_oracle_sample(steps):
-    """Oracle (NumPy, one thread) ROW3 steps of the vortex on a REF_NX^2 mesh at
-    the same p, CFL and tolerance; returns (ndof, [(seconds, iters), ...])."""
+
+def _oracle_procs(sample, steps, copies):
+    """Start `copies` independent oracle processes (one host thread each)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SAMPLE.format(root=ROOT, n=REF_NX, p=P, steps=steps, dt=DT, nx_full=NX, tol=TOL_LIN,
-                                scheme=SCHEME)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["ndof"], d["steps"]
+    code = ORACLE_SAMPLE.format(root=ROOT, steps=steps, **sample)
+    return [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                             text=True, env=env) for _ in range(copies)]
+
+
+def run_oracle(sample, steps, copies=1):
+    """Run the oracle sample in `copies` concurrent single-threaded processes
+    (independent replicas, one per host core); returns (ndof, wall seconds
+    of the slowest, per-copy lists of (seconds, iters) per step)."""
+    t0 = time.perf_counter()
+    procs = _oracle_procs(sample, steps, copies)
+    runs = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        runs.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    return runs[0]["ndof"], wall, [r["steps"] for r in runs]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_baseline():
+    """The oracle on the host: the C2 sample (one ROW3 step) on one thread and
+    as one replica per host core; C1 in full on one thread and one replica per
+    core.  value / cores: the all-core C2-sample rate (units summed over the
+    replicas / wall time)."""
+    cores = host_cores()
+    res = {}
+    for name, sample, steps in (("c2_sample", C2_SAMPLE, 1), ("c1_full", C1_FULL, 10)):
+        nd, wall1, runs1 = run_oracle(sample, steps, 1)
+        it1 = sum(i for _, i in runs1[0])
+        ndN, wallN, runsN = run_oracle(sample, steps, cores)
+        itN = sum(sum(i for _, i in r) for r in runsN)
+        res[name] = {"ndof": nd, "gmres_iters": it1,
+                     "single_thread": {"seconds": wall1, "value": nd * it1 / wall1},
+                     "all_cores": {"replicas": cores, "seconds": wallN, "value": nd * itN / wallN}}
+    c2 = res["c2_sample"]
+    return {"value": c2["all_cores"]["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle (NumPy FP64, one thread per process): one ROW3 step of the {REF_NX}x{REF_NX} "
+                       f"p={P} vortex ({c2['ndof']} DOFs, CFL 13.6, tol 1e-6) as {cores} concurrent replicas "
+                       f"(one per host core); single-thread rate and the C1 run (20x20 p=2 ROW2, 10 steps of "
+                       f"0.05, tol 1e-8) in full alongside"),
+            "single_thread_value": c2["single_thread"]["value"],
+            "host": {"nproc": cores, "cpu": host_cpu_model()},
+            "runs": res}
 
 
 def reference_arm(args):
+    """The oracle as it stands, timed on the host cores: each step runs one
+    ROW3 step of the coarse vortex sample on every host core (independent
+    replicas, one thread each)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    ndof, steps = run_oracle_sample(args.warmup + args.steps)
-    timed = steps[args.warmup:]
-    secs = sum(t for t, _ in timed)
-    iters = sum(i for _, i in timed)
-    value = ndof * iters / secs
+    cores = host_cores()
+    sample = dict(C2_SAMPLE, n=REF_ARM_NX, dt=DT * (NX / REF_ARM_NX))
+    secs, units, nd = 0.0, 0.0, None
+    for k in range(args.warmup + args.steps):
+        nd, wall, runs = run_oracle(sample, 1, cores)
+        if k >= args.warmup:
+            secs += wall
+            units += sum(nd * sum(i for _, i in r) for r in runs)
+    value = units / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(len(timed), 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": _config({"reference_sample": f"oracle ROW3 steps on the {REF_NX}x{REF_NX} p=3 vortex, same CFL and tolerance"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one oracle ROW3 step of the {REF_NX}x{REF_NX} p={P} vortex "
-                                   f"({ndof} DOFs, same CFL 13.6, tol 1e-6), NumPy on 1 host thread"},
+        "config": _config({"reference_sample": f"oracle ROW3 steps on the {REF_ARM_NX}x{REF_ARM_NX} p=3 vortex, "
+                                               f"same CFL and tolerance, one replica per host core"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: one oracle ROW3 step of the {REF_ARM_NX}x{REF_ARM_NX} p={P} vortex "
+                                   f"({nd} DOFs, same CFL 13.6, tol 1e-6) on each of {cores} host cores "
+                                   f"(NumPy, one thread per process)",
+                         "host": {"nproc": cores, "cpu": host_cpu_model()}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -292,9 +363,8 @@ def our_arm(args):
                      "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None}
                  for k, v in warm.items()}
 
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, no per-launch instrumentation
     launches0 = fr.fr_kernel_launches()
-    fr.fr_profile_begin(ctx, [top])
     clocks = ClockSampler(dev)
     clocks.start()
     torch.cuda.synchronize()
@@ -313,8 +383,15 @@ def our_arm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof = fr.fr_profile_end(ctx)[top]
     launches = fr.fr_kernel_launches() - launches0
+
+    # kernel timing pass: the same number of steps again, with CUDA events
+    # around every launch of the dominant family on its launching stream
+    fr.fr_profile_begin(ctx, [top])
+    for _ in range(args.steps):
+        one_step(U)
+    torch.cuda.synchronize()
+    prof = fr.fr_profile_end(ctx)[top]
 
     # end to end through the public API from pinned host memory
     host_in = torch.from_numpy(U.cpu().numpy()).pin_memory()
@@ -387,19 +464,27 @@ def our_arm(args):
         except (OSError, ValueError):
             pass
 
+    default_line = (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt
+                    and args.jv_precision == "fp64" and args.riemann == "rusanov")
+    t_end = None
+    if world == 1 and default_line and not args.no_t_end:
+        ctx.close()
+        torch.cuda.empty_cache()
+        plain = run_t_end(T_END_PLAIN, sample_clocks=True)
+        mixed = run_t_end(T_END_MIXED, sample_clocks=True)
+        t_end = {"t_end": 10.0, "plain_fp64": plain, "mixed": mixed,
+                 "speedup": (plain["time_to_t_end_s"] / mixed["time_to_t_end_s"])
+                 if "time_to_t_end_s" in plain and "time_to_t_end_s" in mixed else None,
+                 "note": "both arms run one period of the 160x160 p=3 vortex through the public API "
+                         "(wall time from the first step to the last, host waits included); E(rho), E(u) "
+                         "by the Sec. 5.1 norm on the GPU"}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload == "vortex" and args.scheme == "row3":
-        nd, stp = run_oracle_sample(1)
-        secs = sum(t for t, _ in stp)
-        it = sum(i for _, i in stp)
-        cpu = {"value": nd * it / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle ROW3 step of the {REF_NX}x{REF_NX} p={P} vortex ({nd} DOFs, same "
-                         f"CFL 13.6 and tol 1e-6, {it} GMRES iterations, {secs:.1f} s), NumPy on 1 host thread"}
+        cpu = cpu_baseline()
 
     line = {
-        "metric": METRIC if (prec == 0 and args.workload == "vortex" and args.scheme == "row3" and not args.dt
-                             and args.jv_precision == "fp64" and args.riemann == "rusanov")
-        else f"DOF*GMRES-iters/s ({wl})",
+        "metric": METRIC if default_line else f"DOF*GMRES-iters/s ({wl})",
         "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -411,7 +496,9 @@ def our_arm(args):
                            "scheme": args.scheme.upper(), "dt": dt, "ndof": ctx.ndof,
                            "mesh": f"{ctx.nx}x{ctx.ny}" + (f"x{ctx.nz}" if args.workload == "tgv" else ""),
                            "launch_config": tuned,
-                           "time_to_t_end_s_est": ms / args.steps * 1e-3 * round(10.0 / dt) if args.workload == "vortex" else None}),
+                           "kernel_timing": "roofline.avg_launch_us from a second pass of the same number of "
+                                            "steps with CUDA events around each launch of the dominant family; "
+                                            "the timed steps run without events"}),
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roofline,
@@ -419,6 +506,7 @@ def our_arm(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                 "d2h_bytes_per_step": 8 * ndof},
+        "time_to_t_end": t_end,
     }
     print(json.dumps(line))
     if dist is not None:
@@ -426,44 +514,45 @@ def our_arm(args):
     return 0
 
 
-def t_end_arm(args):
-    """Run the vortex workload to t_end; report wall time and E(rho), the L2
-    density error against the advected exact vortex (Sec. 5.1 error norm,
-    Gauss-Legendre quadrature at the solution points)."""
-    import numpy as np
+def run_t_end(cfg, autotune=True, sample_clocks=False):
+    """Run the vortex workload to t_end through the public API and measure
+    the wall time, GMRES iterations and the Sec. 5.1 errors E(rho), E(u)
+    against the advected exact vortex (fr_vortex_error, on the GPU).
+    cfg keys: scheme, cfl or dt, t_end, nx, p, box, tol, tol_lin, gmres_m,
+    eps_fixed, block_precision, jv_precision, riemann, guess, precond_refresh."""
     import torch
     import paper_1904_04825_gb300 as fr
     import synthetic as S
 
-    torch.cuda.set_device(0)
-    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
-    kind, order = args.scheme[:-1], int(args.scheme[-1])
-    nx = args.nx or NX
-    p = args.p or P
-    L = args.box
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[cfg["block_precision"]]
+    kind, order = cfg["scheme"][:-1], int(cfg["scheme"][-1])
+    nx, p, L = cfg["nx"], cfg["p"], cfg["box"]
     box = (-L / 2, L / 2, -L / 2, L / 2)
     xe, ye = S.uniform_mesh(nx, box=box)
     X, Y = S.point_coords(xe, ye, p)
-    vort = S.Vortex()
-    U = torch.from_numpy(vort.state(X, Y, box=box)).cuda()
+    U = torch.from_numpy(S.Vortex().state(X, Y, box=box)).cuda()
+    del X, Y
     Uprev = torch.empty_like(U)
     h = L / nx
-    dt = args.dt if args.dt else args.cfl * h / (3 * math.sqrt(2) * (p + 1))
-    nsteps = int(round(args.t_end / dt))
-    dt = args.t_end / nsteps
-    tol = args.tol
-    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else args.tol_lin,
-                                                gmres_m=args.gmres_m, m_max=max(30, args.gmres_m),
+    dt = cfg.get("dt") or cfg["cfl"] * h / (3 * math.sqrt(2) * (p + 1))
+    nsteps = int(round(cfg["t_end"] / dt))
+    dt = cfg["t_end"] / nsteps
+    tol = cfg["tol"]
+    ctx = fr.Context(xe, ye, p, fr.default_opts(tol_lin=tol if kind == "row" else cfg["tol_lin"],
+                                                gmres_m=cfg["gmres_m"], m_max=max(30, cfg["gmres_m"]),
                                                 gmres_max_restarts=20,
-                                                eps_fixed=args.eps_fixed, block_precision=prec,
-                                                guess=args.guess, precond_refresh=args.precond_refresh,
-                                                jv_precision=1 if args.jv_precision == "fp32" else 0,
-                                                riemann=1 if args.riemann == "roe" else 0))
-    if not args.no_autotune:
+                                                eps_fixed=cfg["eps_fixed"], block_precision=prec,
+                                                guess=cfg["guess"], precond_refresh=cfg["precond_refresh"],
+                                                jv_precision=1 if cfg["jv_precision"] == "fp32" else 0,
+                                                riemann=1 if cfg["riemann"] == "roe" else 0))
+    if autotune:
         fr.autotune(ctx, U, 1.0 / (0.5 * dt), reps=1)
-    ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=args.tol_lin)
+    ptc = fr.default_ptc_opts(tol_nl=tol, tol_lin=cfg["tol_lin"])
     iters = 0
     bad = 0
+    clocks = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    if clocks:
+        clocks.start()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     failed = None
@@ -484,28 +573,53 @@ def t_end_arm(args):
         bad += 0 if st.converged else 1
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    clk = clocks.stop() if clocks else None
+    out = {"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": cfg["scheme"].upper(), "dt": dt,
+           "gmres_m": cfg["gmres_m"], "eps_fixed": cfg["eps_fixed"],
+           "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
+           "tol": tol, "tol_lin": (tol if kind == "row" else cfg["tol_lin"]),
+           "block_precision": cfg["block_precision"], "jv_precision": cfg["jv_precision"],
+           "riemann": cfg["riemann"], "guess": cfg["guess"],
+           "precond_refresh": cfg["precond_refresh"], "t_end": cfg["t_end"]}
     if failed:
-        print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": args.scheme.upper(), "dt": dt,
-                      "gmres_m": args.gmres_m, "eps_fixed": args.eps_fixed,
-                          "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 3), "steps": nsteps,
-                          "riemann": args.riemann, "failed": failed}))
-        return 0
-    x, w = np.polynomial.legendre.leggauss(p + 1)
-    w2 = np.outer(w, w).reshape(-1)
-    exact = vort.state(X, Y, t=args.t_end, box=box)
-    Uh = U.cpu().numpy()
-    rho = Uh[:, 0]
-    err = math.sqrt(np.sum((exact[:, 0] - rho) ** 2 * w2[None, :]) * (h * h / 4) / (L * L))
-    err_u = math.sqrt(np.sum((exact[:, 1] / exact[:, 0] - Uh[:, 1] / rho) ** 2 * w2[None, :]) * (h * h / 4) / (L * L))
-    print(json.dumps({"workload": f"vortex-{nx}x{nx}-p{p}-box{L:g}", "scheme": args.scheme.upper(), "dt": dt,
-                      "gmres_m": args.gmres_m, "eps_fixed": args.eps_fixed,
-                      "cfl": round(dt * 3 * math.sqrt(2) * (p + 1) / h, 2), "steps": nsteps,
-                      "tol": tol, "tol_lin": (tol if kind == "row" else args.tol_lin),
-                      "block_precision": args.block_precision, "jv_precision": args.jv_precision,
-                      "riemann": args.riemann, "guess": args.guess,
-                      "precond_refresh": args.precond_refresh, "t_end": args.t_end,
-                      "time_to_t_end_s": wall, "E_rho": err, "E_u": err_u, "gmres_iters": iters,
-                      "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad}))
+        out["failed"] = failed
+        ctx.close()
+        return out
+    err = fr.fr_vortex_error(ctx, U, cfg["t_end"])
+    out.update({"time_to_t_end_s": wall, "E_rho": err["rho"], "E_u": err["u"], "gmres_iters": iters,
+                "dof_iters_per_s": ctx.ndof * iters / wall, "unconverged_steps": bad})
+    if clk is not None:
+        out["clocks"] = clk
+    ctx.close()
+    return out
+
+
+def _t_end_cfg(args):
+    return {"scheme": args.scheme, "cfl": args.cfl, "dt": args.dt, "t_end": args.t_end, "nx": args.nx or NX,
+            "p": args.p or P, "box": args.box, "tol": args.tol, "tol_lin": args.tol_lin, "gmres_m": args.gmres_m,
+            "eps_fixed": args.eps_fixed, "block_precision": args.block_precision,
+            "jv_precision": args.jv_precision, "riemann": args.riemann, "guess": args.guess,
+            "precond_refresh": args.precond_refresh}
+
+
+# The two arms of the time-to-t_end comparison on the 160^2 p=3 vortex, one
+# period (t = 10): the plain FP64 method (ROW3 at CFL 13.6, FP64 blocks, zero
+# guess, FP64 FD operator, Rusanov) and the mixed form (ROW4 at CFL 50, BF16
+# blocks, previous-step guess, FP32 linear parts of the FD operator, the
+# paper's Roe flux), both with GMRES(30) to 1e-6 and element-Jacobi.
+T_END_PLAIN = {"scheme": "row3", "cfl": 13.6, "dt": None, "t_end": 10.0, "nx": NX, "p": P, "box": 10.0,
+               "tol": TOL_LIN, "tol_lin": 1e-1, "gmres_m": 30, "eps_fixed": 0.0, "block_precision": "fp64",
+               "jv_precision": "fp64", "riemann": "rusanov", "guess": 0, "precond_refresh": 0}
+T_END_MIXED = dict(T_END_PLAIN, scheme="row4", cfl=50.0, block_precision="bf16", jv_precision="fp32",
+                   riemann="roe", guess=1)
+
+
+def t_end_arm(args):
+    """Run the vortex workload to t_end; report wall time and E(rho), the L2
+    density error against the advected exact vortex (Sec. 5.1 error norm)."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(run_t_end(_t_end_cfg(args), autotune=not args.no_autotune)))
     return 0
 
 
@@ -790,6 +904,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-t-end", action="store_true",
+                    help="default run: skip the plain-vs-mixed time-to-t_end comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")

@@ -183,6 +183,32 @@ int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* opts, fr_
  * stream.  FR_ERR_UNSUPPORTED on a 2D context. */
 int fr_dissipation_rate(fr_ctx* ctx, const double* U, double rho0, double* out, void* stream);
 
+/* ---- accuracy of the isentropic vortex study (Sec. 5.1) ----------------
+ * The exact solution of Eq. VP_Solution: a free stream (rho_inf, u_inf,
+ * v_inf) with gas constant R = 1 carries, centred at (x0 + u_inf t,
+ * y0 + v_inf t) (nearest periodic image on the mesh's box),
+ *   du = -alpha/(2 pi) (y - yc) e^{phi (1 - r^2)},
+ *   dv =  alpha/(2 pi) (x - xc) e^{phi (1 - r^2)},
+ *   dT = -alpha^2 (gamma - 1)/(16 phi gamma pi^2) e^{2 phi (1 - r^2)},
+ * dS = 0, r the distance to the centre (the paper prints its square; the
+ * exponent is read as phi (1 - r^2)).  The Mach number is taken on the
+ * free-stream speed, T_inf = (u_inf^2 + v_inf^2) / (gamma mach^2). */
+typedef struct fr_vortex {
+  double alpha, phi;     /* strength and width (5, 1/2) */
+  double mach;           /* free-stream Mach number on |V| (0.5) */
+  double rho_inf, u_inf, v_inf;  /* free stream (1, 1, 1) */
+  double x0, y0;         /* centre at t = 0 (0, 0) */
+} fr_vortex;
+void fr_default_vortex(fr_vortex* v);
+/* Error(s) = sqrt( int (s_exact - s_num)^2 dV / V ) of Sec. 5.1 for
+ * s = rho, u, v, p of the conserved state U (device, ndof doubles) against
+ * the exact vortex at time t, the integral by the Gauss-Legendre rule of the
+ * solution points on every element (weights w_i w_j |J_e|), V the area of
+ * the mesh's box.  err: HOST array of 4 doubles (E(rho), E(u), E(v), E(p)).
+ * 2D Euler contexts; synchronises the stream. */
+int fr_vortex_error(fr_ctx* ctx, const double* U, const fr_vortex* vortex, double t, double* err,
+                    void* stream);
+
 /* Free the context and its device memory. NULL is accepted. */
 int fr_ctx_destroy(fr_ctx* ctx);
 /* Message of the last failing call on ctx ("" if none); static string for ctx == NULL. */
@@ -332,15 +358,19 @@ int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
  *    (about 365 KB, held on every GPU that loads the library until the
  *    process exits).  It limits the mesh to 2 <= nx, ny <= 4096; larger
  *    meshes are rejected with FR_ERR_INVALID_ARG.  p must be 2, 3 or 4.
- *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the current device
+ *    (this allocates nothing).  The first lookup on a device also loads the
+ *    library's device code there: make the first call on each device before
+ *    any stream capture.
  *  - Every call uses the same array and leaves its contents behind; calls
  *    that overlap on the GPU (other streams, other host threads) race.
  *    Serialise them on one stream.
  *  - mesh: HOST edge arrays (copied on `stream`); opts may be NULL
- *    (defaults; gamma, eps_rel, eps_fixed and riemann are used; the product
- *    is always the FP64 Euler one).  U, R0, z, y: device,
- *    ndof doubles as for fr_jv.  Errors are reported by fr_last_error(NULL). */
+ *    (defaults; gamma, eps_rel, eps_fixed and riemann are used).  The
+ *    product is the periodic FP64 Euler one: mesh->wall_y != 0,
+ *    opts->mu > 0 or opts->jv_precision != 0 return FR_ERR_UNSUPPORTED.
+ *    U, R0, z, y: device, ndof doubles as for fr_jv.  Errors are reported
+ *    by fr_last_error(NULL). */
 int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opts, const double* U,
                   const double* R0, const double* z, double shift, double* y, void* stream);
 

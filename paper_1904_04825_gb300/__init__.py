@@ -77,6 +77,12 @@ class fr_ptc_opts(ctypes.Structure):
                 ("reject_above", ctypes.c_double)]
 
 
+class fr_vortex(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("phi", ctypes.c_double), ("mach", ctypes.c_double),
+                ("rho_inf", ctypes.c_double), ("u_inf", ctypes.c_double), ("v_inf", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+
+
 class fr_gmres_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("converged", ctypes.c_int), ("relres", ctypes.c_double)]
@@ -103,6 +109,8 @@ def _load():
         "fr_ctx_create_3d": (I, [ctypes.POINTER(fr_mesh3d_desc), I, ctypes.POINTER(fr_opts),
                                  ctypes.POINTER(ctypes.c_void_p)]),
         "fr_dissipation_rate": (I, [P, P, D, ctypes.POINTER(ctypes.c_double), V]),
+        "fr_default_vortex": (None, [ctypes.POINTER(fr_vortex)]),
+        "fr_vortex_error": (I, [P, P, ctypes.POINTER(fr_vortex), D, ctypes.POINTER(ctypes.c_double), V]),
         "fr_ctx_destroy": (I, [P]),
         "fr_last_error": (ctypes.c_char_p, [P]),
         "fr_ndof": (ctypes.c_longlong, [P]),
@@ -185,6 +193,20 @@ def _ptr(t):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _sized(t, n: int, name: str = "tensor"):
+    """_ptr after checking that t holds exactly n elements: the library takes
+    the length from the mesh and trusts the pointer, so a shorter tensor would
+    be read or written past its end."""
+    if t is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return _ptr(t)
+
+
+def _vec(ctx, t, name: str = "vector"):
+    """Pointer to a state-shaped float64 CUDA tensor of exactly ctx.ndof elements."""
+    return _sized(t, ctx.ndof, name)
 
 
 def _stream(stream):
@@ -272,25 +294,42 @@ class Context3D(Context):
 def fr_dissipation_rate(ctx: Context3D, U, rho0: float = 1.0, stream=None):
     """(eps1, eps3, kinetic energy) of the Taylor-Green study for the 3D state U."""
     out = (ctypes.c_double * 3)()
-    ctx.check(lib.fr_dissipation_rate(ctx.handle, _ptr(U), rho0, out, _stream(stream)))
+    ctx.check(lib.fr_dissipation_rate(ctx.handle, _vec(ctx, U, "U"), rho0, out, _stream(stream)))
     return out[0], out[1], out[2]
 
 
+def default_vortex(**kw) -> fr_vortex:
+    v = fr_vortex()
+    lib.fr_default_vortex(ctypes.byref(v))
+    for k, val in kw.items():
+        setattr(v, k, val)
+    return v
+
+
+def fr_vortex_error(ctx: Context, U, t: float, vortex: fr_vortex | None = None, stream=None):
+    """E(rho), E(u), E(v), E(p) of the state U against the exact isentropic vortex at time t."""
+    v = vortex if vortex is not None else default_vortex()
+    out = (ctypes.c_double * 4)()
+    ctx.check(lib.fr_vortex_error(ctx.handle, _vec(ctx, U), ctypes.byref(v), float(t), out, _stream(stream)))
+    return {"rho": out[0], "u": out[1], "v": out[2], "p": out[3]}
+
+
 def fr_residual(ctx: Context, U, R, stream=None):
-    return ctx.check(lib.fr_residual(ctx.handle, _ptr(U), _ptr(R), _stream(stream)))
+    return ctx.check(lib.fr_residual(ctx.handle, _vec(ctx, U, "U"), _vec(ctx, R, "R"), _stream(stream)))
 
 
 def fr_jv(ctx: Context, U, R0, z, shift, y, stream=None):
-    return ctx.check(lib.fr_jv(ctx.handle, _ptr(U), _ptr(R0), _ptr(z), float(shift), _ptr(y),
+    return ctx.check(lib.fr_jv(ctx.handle, _vec(ctx, U, "U"), _vec(ctx, R0, "R0"), _vec(ctx, z, "z"), float(shift),
+                               _vec(ctx, y, "y"),
                                _stream(stream)))
 
 
 def ejacobi_factor(ctx: Context, U, R0, shift, stream=None):
-    return ctx.check(lib.ejacobi_factor(ctx.handle, _ptr(U), _ptr(R0), float(shift), _stream(stream)))
+    return ctx.check(lib.ejacobi_factor(ctx.handle, _vec(ctx, U, "U"), _vec(ctx, R0, "R0"), float(shift), _stream(stream)))
 
 
 def ejacobi_apply(ctx: Context, r, z, stream=None):
-    return ctx.check(lib.ejacobi_apply(ctx.handle, _ptr(r), _ptr(z), _stream(stream)))
+    return ctx.check(lib.ejacobi_apply(ctx.handle, _vec(ctx, r, "r"), _vec(ctx, z, "z"), _stream(stream)))
 
 
 @dataclass
@@ -305,7 +344,8 @@ class GmresInfo:
 def gmres_solve(ctx: Context, U, R0, shift, b, x, m=30, rtol=1e-8, max_restarts=20, stream=None,
                 allow_not_converged=True) -> GmresInfo:
     info = fr_gmres_info()
-    rc = lib.gmres_solve(ctx.handle, _ptr(U), _ptr(R0), float(shift), _ptr(b), _ptr(x), int(m),
+    rc = lib.gmres_solve(ctx.handle, _vec(ctx, U, "U"), _vec(ctx, R0, "R0"), float(shift), _vec(ctx, b, "b"),
+                         _vec(ctx, x, "x"), int(m),
                          float(rtol), int(max_restarts), ctypes.byref(info), _stream(stream))
     ctx.check(rc, allow=(FR_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return GmresInfo(info.iters, info.restarts, bool(info.converged), info.relres, rc)
@@ -329,7 +369,7 @@ def _stats(st, rc):
 
 def step_row(ctx: Context, scheme: int, dt: float, U, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
     st = fr_step_stats()
-    rc = lib.step_row(ctx.handle, int(scheme), float(dt), _ptr(U), ctypes.byref(st), _stream(stream))
+    rc = lib.step_row(ctx.handle, int(scheme), float(dt), _vec(ctx, U, "U"), ctypes.byref(st), _stream(stream))
     ctx.check(rc, allow=allow)
     return _stats(st, rc)
 
@@ -337,7 +377,7 @@ def step_row(ctx: Context, scheme: int, dt: float, U, stream=None, allow=(FR_ERR
 def step_esdirk(ctx: Context, scheme: int, dt: float, U, ptc: fr_ptc_opts | None = None, stream=None,
                 allow=(FR_ERR_NOT_CONVERGED,)):
     st = fr_step_stats()
-    rc = lib.step_esdirk(ctx.handle, int(scheme), float(dt), _ptr(U),
+    rc = lib.step_esdirk(ctx.handle, int(scheme), float(dt), _vec(ctx, U, "U"),
                          ctypes.byref(ptc) if ptc is not None else None, ctypes.byref(st),
                          _stream(stream))
     ctx.check(rc, allow=allow)
@@ -347,7 +387,7 @@ def step_esdirk(ctx: Context, scheme: int, dt: float, U, ptc: fr_ptc_opts | None
 def step_bdf2(ctx: Context, dt: float, U, U_prev, first_step: bool, ptc: fr_ptc_opts | None = None,
               stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
     st = fr_step_stats()
-    rc = lib.step_bdf2(ctx.handle, float(dt), _ptr(U), _ptr(U_prev), int(bool(first_step)),
+    rc = lib.step_bdf2(ctx.handle, float(dt), _vec(ctx, U, "U"), _vec(ctx, U_prev, "U_prev"), int(bool(first_step)),
                        ctypes.byref(ptc) if ptc is not None else None, ctypes.byref(st),
                        _stream(stream))
     ctx.check(rc, allow=allow)
@@ -356,7 +396,7 @@ def step_bdf2(ctx: Context, dt: float, U, U_prev, first_step: bool, ptc: fr_ptc_
 
 def step_ssprk3(ctx: Context, dt: float, U, stream=None):
     st = fr_step_stats()
-    rc = lib.step_ssprk3(ctx.handle, float(dt), _ptr(U), ctypes.byref(st), _stream(stream))
+    rc = lib.step_ssprk3(ctx.handle, float(dt), _vec(ctx, U, "U"), ctypes.byref(st), _stream(stream))
     ctx.check(rc)
     return _stats(st, rc)
 
@@ -396,11 +436,20 @@ def fr_jv_noalloc(x_edges, y_edges, p: int, U, R0, z, shift, y, opts: fr_opts | 
     desc = fr_mesh_desc(len(xe) - 1, len(ye) - 1,
                         xe.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         ye.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    n = (len(xe) - 1) * (len(ye) - 1) * 4 * (int(p) + 1) ** 2
     rc = lib.fr_jv_noalloc(ctypes.byref(desc), int(p), ctypes.byref(opts) if opts is not None else None,
-                           _ptr(U), _ptr(R0), _ptr(z), float(shift), _ptr(y), _stream(stream))
+                           _sized(U, n, "U"), _sized(R0, n, "R0"), _sized(z, n, "z"), float(shift),
+                           _sized(y, n, "y"), _stream(stream))
     if rc != FR_OK:
         raise FrError(rc, lib.fr_last_error(None).decode())
     return rc
+
+
+def _fsized(t, n: int, name: str = "tensor"):
+    """_fptr after checking that t holds exactly n elements."""
+    if t is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return _fptr(t)
 
 
 def _fptr(t):
@@ -454,13 +503,15 @@ class MLP:
         return a
 
     def forward(self, X, Y, bf16=False):
-        return self.check(lib.fr_mlp_forward(self.handle, _fptr(X), int(X.shape[0]), _fptr(Y), int(bool(bf16)),
-                                             _stream(None)))
+        M = int(X.shape[0])
+        return self.check(lib.fr_mlp_forward(self.handle, _fsized(X, M * self.sizes[0], "X"), M,
+                                             _fsized(Y, M * self.sizes[3], "Y"), int(bool(bf16)), _stream(None)))
 
     def backward(self, X, T):
         loss = ctypes.c_double()
-        self.check(lib.fr_mlp_backward(self.handle, _fptr(X), _fptr(T), int(X.shape[0]), ctypes.byref(loss),
-                                       _stream(None)))
+        M = int(X.shape[0])
+        self.check(lib.fr_mlp_backward(self.handle, _fsized(X, M * self.sizes[0], "X"),
+                                       _fsized(T, M * self.sizes[3], "T"), M, ctypes.byref(loss), _stream(None)))
         return loss.value
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -488,6 +539,11 @@ def fr_attach_guess_model(ctx: Context, model):
 
 
 def fr_set_stage_capture(ctx: Context, X, T, max_samples, elem_stride):
+    nb = 4 * ctx.np
+    if X is not None and X.numel() < int(max_samples) * 3 * nb:
+        raise ValueError(f"X holds {X.numel()} floats, fewer than max_samples * 3 nb = {int(max_samples) * 3 * nb}")
+    if T is not None and T.numel() < int(max_samples) * nb:
+        raise ValueError(f"T holds {T.numel()} floats, fewer than max_samples * nb = {int(max_samples) * nb}")
     return ctx.check(lib.fr_set_stage_capture(ctx.handle, _fptr(X) if X is not None else None,
                                               _fptr(T) if T is not None else None, int(max_samples),
                                               int(elem_stride)))
@@ -498,7 +554,8 @@ def fr_stage_capture_count(ctx: Context) -> int:
 
 
 def fr_stage_features(ctx: Context, b, bl, yl, X, stream=None):
-    return ctx.check(lib.fr_stage_features(ctx.handle, _ptr(b), _ptr(bl), _ptr(yl), _fptr(X), _stream(stream)))
+    return ctx.check(lib.fr_stage_features(ctx.handle, _vec(ctx, b, "b"), _vec(ctx, bl, "bl"), _vec(ctx, yl, "yl"),
+                                              _fsized(X, ctx.ne * 12 * ctx.np, "X"), _stream(stream)))
 
 
 def fr_reset_history(ctx: Context):
@@ -529,7 +586,7 @@ def autotune(ctx: Context, U, shift: float, reps: int = 2, stream=None):
     """Pick the fastest launch configuration for GMRES cycles at U; returns
     (vec_blocks, tile_variant, ms per cycle chosen, ms per cycle on entry)."""
     best, dflt = ctypes.c_double(), ctypes.c_double()
-    ctx.check(lib.fr_autotune(ctx.handle, _ptr(U), float(shift), int(reps), ctypes.byref(best),
+    ctx.check(lib.fr_autotune(ctx.handle, _vec(ctx, U, "U"), float(shift), int(reps), ctypes.byref(best),
                               ctypes.byref(dflt), _stream(stream)))
     vb, tv = get_launch_config(ctx)
     return vb, tv, best.value, dflt.value

@@ -27,6 +27,8 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->hx);
   cudaFree(c->hy);
   cudaFree(c->hz);
+  cudaFree(c->xo);
+  cudaFree(c->yo);
   cudaFree(c->diss);
   cudaFree(c->blocks);
   cudaFree(c->tb);
@@ -103,6 +105,16 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   delete[] hx;
   delete[] hy;
   FRK_TRY(rc);
+  c->box[0] = mesh->x_edges[0];
+  c->box[1] = mesh->x_edges[mesh->nx];
+  c->box[2] = mesh->y_edges[0];
+  c->box[3] = mesh->y_edges[mesh->ny];
+  c->volume = (c->box[1] - c->box[0]) * (c->box[3] - c->box[2]);
+  FRK_TRY(dalloc(c, &c->xo, mesh->nx));
+  FRK_TRY(dalloc(c, &c->yo, mesh->ny));
+  FRK_CUDA(c, cudaMemcpy(c->xo, mesh->x_edges, mesh->nx * sizeof(double), cudaMemcpyHostToDevice));
+  FRK_CUDA(c, cudaMemcpy(c->yo, mesh->y_edges, mesh->ny * sizeof(double), cudaMemcpyHostToDevice));
+  FRK_TRY(dalloc(c, &c->diss, 4));
   const size_t n = (size_t)c->ndof;
   const int m = o->m_max;
   FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * c->nb * c->nb));
@@ -437,6 +449,39 @@ extern "C" int fr_dissipation_rate(fr_ctx* ctx, const double* U, double rho0, do
   out[0] = 2.0 * ctx->opts.mu / rho0 * ctx->h_scal[0] / V;
   out[1] = -ctx->h_scal[1] / (rho0 * V);
   out[2] = ctx->h_scal[2] / (rho0 * V);
+  return FR_OK;
+}
+
+extern "C" void fr_default_vortex(fr_vortex* v) {
+  if (!v) return;
+  v->alpha = 5.0;
+  v->phi = 0.5;
+  v->mach = 0.5;
+  v->rho_inf = 1.0;
+  v->u_inf = 1.0;
+  v->v_inf = 1.0;
+  v->x0 = 0.0;
+  v->y0 = 0.0;
+}
+
+extern "C" int fr_vortex_error(fr_ctx* ctx, const double* U, const fr_vortex* vortex, double t, double* err,
+                               void* stream) {
+  if (!ctx || !err) return FR_ERR_INVALID_ARG;
+  FRK_TRY(check_vec(ctx, U, "U"));
+  if (!vortex) return set_error(ctx, FR_ERR_INVALID_ARG, "fr_vortex_error: vortex is NULL");
+  if (ctx->dim3 || ctx->viscous)
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "fr_vortex_error: 2D Euler contexts only");
+  if (!(vortex->phi > 0.0) || !(vortex->mach > 0.0) || !(vortex->rho_inf > 0.0) || !std::isfinite(vortex->alpha) ||
+      !std::isfinite(vortex->u_inf) || !std::isfinite(vortex->v_inf) || !std::isfinite(vortex->x0) ||
+      !std::isfinite(vortex->y0) || !std::isfinite(t) ||
+      !(vortex->u_inf * vortex->u_inf + vortex->v_inf * vortex->v_inf > 0.0))
+    return set_error(ctx, FR_ERR_INVALID_ARG,
+                     "fr_vortex_error: phi, mach, rho_inf and the free-stream speed must be > 0, all finite");
+  cudaStream_t s = as_stream(stream);
+  FRK_TRY(launch_vortex_error(ctx, U, vortex, t, ctx->diss, s));
+  FRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->diss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FRK_CUDA(ctx, cudaStreamSynchronize(s));
+  for (int k = 0; k < 4; ++k) err[k] = std::sqrt(ctx->h_scal[k] / ctx->volume);
   return FR_OK;
 }
 

@@ -113,6 +113,9 @@ struct fr_ctx {
   frk::Tables tab{};
   double* hx = nullptr;      // [nx] element widths (device)
   double* hy = nullptr;      // [ny] element heights (device)
+  double* xo = nullptr;      // 2D: [nx] left edges of the element columns (device)
+  double* yo = nullptr;      // 2D: [ny] bottom edges of the element rows (device)
+  double box[4] = {};        // 2D: x_edges[0], x_edges[nx], y_edges[0], y_edges[ny]
   int wall_y = 0;            // isothermal no-slip walls at the y ends (viscous runs)
   int viscous = 0;           // Navier-Stokes (BR2) residual instead of Euler
   double* tb = nullptr;      // viscous: face traces (q, grad q) of every element
@@ -248,6 +251,10 @@ int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
                        const int* done, cudaStream_t s);
 int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s);
 int launch_f3_dissipation(fr_ctx* ctx, const double* U, double* out, cudaStream_t s);
+// vortex.cu: quadrature sums of (s_exact - s_num)^2 |J| w_i w_j for s = rho, u, v, p
+// against the exact isentropic vortex into out[0..3]
+int launch_vortex_error(fr_ctx* ctx, const double* U, const fr_vortex* vx, double t, double* out,
+                        cudaStream_t s);
 // blocks.cu: invert staged FP64 blocks (column-major M[c][row], dshift added to
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);

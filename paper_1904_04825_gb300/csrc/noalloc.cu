@@ -7,8 +7,6 @@
 // holds that array until the process exits.  All calls share it and it keeps
 // the last call's contents; calls that overlap on the GPU (two streams, two
 // host threads) race on it.
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace frk {
@@ -27,34 +25,24 @@ constexpr size_t kScratchDoubles = ((kOffCount + 1 + 31) / 32) * 32;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_setup_mutex;
-
 __global__ void k_widths(double* scratch, int nx, int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nx) scratch[kOffHX + i] = scratch[kOffXE + i + 1] - scratch[kOffXE + i];
   if (i < ny) scratch[kOffHY + i] = scratch[kOffYE + i + 1] - scratch[kOffYE + i];
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the first call on a device does this).
-int scratch_for_device(int dev, double** out) {
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_static_error("fr_jv_noalloc: device index out of range");
-    return FR_ERR_INVALID_ARG;
+// Device address of the scratch array on the current device, looked up on
+// every call (the lookup allocates nothing, and a cached address would go
+// stale after a device reset).  The first lookup on a device loads the
+// library's device code there.
+int scratch_for_device(double** out) {
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_static_error("fr_jv_noalloc: cudaGetSymbolAddress failed");
+    return FR_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    double* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_static_error("fr_jv_noalloc: cudaGetSymbolAddress failed");
-      return FR_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return FR_OK;
 }
 
@@ -117,15 +105,20 @@ extern "C" int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opt
     set_static_error("fr_jv_noalloc: bad gamma, eps_rel or riemann");
     return FR_ERR_INVALID_ARG;
   }
-  o.jv_precision = 0;  // the FP32-linear-parts product needs per-context caches
-  o.mu = 0.0;          // Euler residual
+  // The product here is the periodic Euler one: a viscous or walled mesh, or
+  // the FP32-linear-parts product (which needs per-context caches), would be
+  // a different operator than fr_jv on a context made from the same inputs.
+  if (mesh->wall_y || o.mu > 0.0 || o.jv_precision != 0) {
+    set_static_error("fr_jv_noalloc: only the periodic Euler FP64 product (wall_y = 0, mu = 0, jv_precision = 0)");
+    return FR_ERR_UNSUPPORTED;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     set_static_error("fr_jv_noalloc: cudaGetDevice failed");
     return FR_ERR_CUDA;
   }
   double* sp = nullptr;
-  const int rc = scratch_for_device(dev, &sp);
+  const int rc = scratch_for_device(&sp);
   if (rc != FR_OK) return rc;
 
   // A host-side view of the scratch with the fields the launchers use.

@@ -55,7 +55,7 @@ def test_reference_arm_does_no_work_off_rank_0(monkeypatch, capsys):
 
     def boom(*a, **k):
         raise AssertionError("rank 1 must not run the oracle")
-    monkeypatch.setattr(bench, "run_oracle_sample", boom)
+    monkeypatch.setattr(bench, "run_oracle", boom)
     assert bench.reference_arm(types.SimpleNamespace(steps=2, warmup=3, gpus=2)) == 0
     assert capsys.readouterr().out == ""
 
@@ -75,3 +75,23 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_reports_one_and_all_cores(monkeypatch):
+    """cpu_baseline runs the C2 sample and C1 in full, each on one thread and
+    as one replica per host core, and reports the all-core C2 rate as value
+    (oracle runs replaced by a stand-in that returns fixed timings)."""
+    import bench
+    calls = []
+
+    def fake(sample, steps, copies=1):
+        calls.append((sample["n"], steps, copies))
+        return 100, 2.0, [[(1.0, 5)] * steps for _ in range(copies)]
+    monkeypatch.setattr(bench, "run_oracle", fake)
+    monkeypatch.setattr(bench, "host_cores", lambda: 4)
+    cb = bench.cpu_baseline()
+    assert sorted(calls) == sorted([(bench.REF_NX, 1, 1), (bench.REF_NX, 1, 4), (20, 10, 1), (20, 10, 4)])
+    assert cb["cores"] == 4 and cb["kind"] == "oracle" and cb["host"]["nproc"] == 4
+    assert cb["value"] == 4 * 100 * 5 / 2.0
+    assert cb["single_thread_value"] == 100 * 5 / 2.0
+    assert cb["runs"]["c1_full"]["all_cores"]["value"] == 4 * 100 * 50 / 2.0

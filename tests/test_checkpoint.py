@@ -58,9 +58,10 @@ def test_damaged_or_foreign_files_are_rejected(tmp_path):
     edges, U = _state()
     pre = str(tmp_path / "c")
     ck.save(pre, U, t=1.0, step=1, scheme="ROW3", p=3, edges=edges)
-    raw = bytearray(open(pre + ".bin", "rb").read())
+    payload = str(tmp_path / json.load(open(pre + ".json"))["payload"])
+    raw = bytearray(open(payload, "rb").read())
     raw[100] ^= 1
-    open(pre + ".bin", "wb").write(bytes(raw))
+    open(payload, "wb").write(bytes(raw))
     with pytest.raises(ValueError, match="SHA-256"):
         ck.load(pre, device=None)
     h = json.load(open(pre + ".json"))
@@ -70,3 +71,39 @@ def test_damaged_or_foreign_files_are_rejected(tmp_path):
         ck.load(pre, device=None)
     with pytest.raises(TypeError):
         ck.save(pre, U.astype(np.float32), t=0.0, step=0, scheme="ROW3", p=3, edges=edges)
+
+
+def test_interrupted_save_leaves_the_previous_checkpoint_loadable(tmp_path, monkeypatch):
+    """A save that dies after writing its payload (here: the header rename
+    fails) or while writing it leaves the earlier checkpoint at the same
+    prefix intact and loadable; a completed save removes the old payload."""
+    ck = _ckpt()
+    edges, U = _state()
+    pre = str(tmp_path / "c")
+    ck.save(pre, U, t=1.0, step=10, scheme="ROW3", p=3, edges=edges)
+    first_payload = json.load(open(pre + ".json"))["payload"]
+    real_replace = os.replace
+
+    def dies_on_header(src, dst):
+        if dst.endswith(".json"):
+            raise OSError("interrupted")
+        return real_replace(src, dst)
+    monkeypatch.setattr(ck.os, "replace", dies_on_header)
+    with pytest.raises(OSError):
+        ck.save(pre, U * 2.0, t=2.0, step=20, scheme="ROW3", p=3, edges=edges)
+    U1, _, h1 = ck.load(pre, device=None)
+    assert h1["step"] == 10 and np.array_equal(U1, U)
+
+    def dies_in_payload(src, dst):
+        raise OSError("interrupted")
+    monkeypatch.setattr(ck.os, "replace", dies_in_payload)
+    with pytest.raises(OSError):
+        ck.save(pre, U * 3.0, t=3.0, step=30, scheme="ROW3", p=3, edges=edges)
+    U1, _, h1 = ck.load(pre, device=None)
+    assert h1["step"] == 10 and np.array_equal(U1, U)
+
+    monkeypatch.setattr(ck.os, "replace", real_replace)
+    ck.save(pre, U * 4.0, t=4.0, step=40, scheme="ROW3", p=3, edges=edges)
+    U4, _, h4 = ck.load(pre, device=None)
+    assert h4["step"] == 40 and np.array_equal(U4, U * 4.0)
+    assert not os.path.exists(str(tmp_path / first_payload))

@@ -107,3 +107,45 @@ def test_3d_argument_checks_without_gpu(libpath):
     assert fr.lib.fr_ctx_create_3d(None, 2, None, ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
     out = (ctypes.c_double * 3)()
     assert fr.lib.fr_dissipation_rate(None, None, 1.0, out, None) == fr.FR_ERR_INVALID_ARG
+
+
+def test_wrong_length_tensors_rejected_before_any_library_call(libpath):
+    """The library takes vector lengths from the mesh and trusts the pointers,
+    so the binding checks every tensor's length first (a shorter tensor would
+    be read or written past its end).  Runs on the host: the check raises
+    before any call into the library."""
+    import types
+
+    import numpy as np
+    import torch
+
+    import paper_1904_04825_gb300 as fr
+    ne, np_ = 4, 9
+    ctx = types.SimpleNamespace(handle=None, ndof=ne * 4 * np_, ne=ne, np=np_,
+                                check=lambda rc, allow=(): rc)
+    good = torch.zeros(ctx.ndof, dtype=torch.float64)
+    short = torch.zeros(ctx.ndof - 1, dtype=torch.float64)
+    # the first tensor argument is the wrong one (later ones would fail the
+    # CUDA-tensor check on this GPU-less host)
+    calls = [
+        lambda: fr.fr_residual(ctx, short, good),
+        lambda: fr.fr_jv(ctx, short, good, good, 0.0, good),
+        lambda: fr.ejacobi_factor(ctx, short, None, 1.0),
+        lambda: fr.ejacobi_apply(ctx, short, good),
+        lambda: fr.gmres_solve(ctx, short, good, 0.0, good, good),
+        lambda: fr.step_row(ctx, 3, 0.1, short),
+        lambda: fr.step_esdirk(ctx, 3, 0.1, short),
+        lambda: fr.step_bdf2(ctx, 0.1, short, good, False),
+        lambda: fr.step_ssprk3(ctx, 0.1, short),
+        lambda: fr.fr_vortex_error(ctx, short, 0.0),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
+    xe = np.linspace(0.0, 1.0, 3)   # 2 x 2 elements, p = 2: 144 values
+    s2 = torch.zeros(143, dtype=torch.float64)
+    g2 = torch.zeros(144, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        fr.fr_jv_noalloc(xe, xe, 2, s2, g2, g2, 0.0, g2)
+    with pytest.raises(ValueError):       # degree 3 needs 256 values
+        fr.fr_jv_noalloc(xe, xe, 3, g2, g2, g2, 0.0, g2)
