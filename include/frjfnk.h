@@ -460,6 +460,18 @@ enum {
   FR_KF_COUNT = 8
 };
 
+/* Test hook (no counterpart in the paper) for the bounded waits of the
+ * element-Jacobi apply, whose CTAs wait on shared-memory barriers for the
+ * bulk copies of the blocks: polls = the poll limit of every such wait
+ * (0 = the default, 2^22); skip_first_copy = 1 makes CTA 0 of every later
+ * apply launch leave its first element's copies unissued, so that its wait
+ * runs out.  The CTA then flags the context, waits (bounded) for the copies
+ * it did issue and leaves; the GMRES cycle that launched it returns
+ * FR_ERR_TIMEOUT (as gmres_solve and the steppers do whenever a bounded wait
+ * gave up).  Nothing faults.  A context that reported FR_ERR_TIMEOUT keeps
+ * reporting it: destroy it. */
+int fr_set_wait_test(fr_ctx* ctx, unsigned polls, int skip_first_copy);
+
 /* Number of kernels this library has launched in this process. */
 long long fr_kernel_launches(void);
 

@@ -126,6 +126,7 @@ def _load():
                           ctypes.POINTER(fr_step_stats), V]),
         "step_ssprk3": (I, [P, D, P, ctypes.POINTER(fr_step_stats), V]),
         "fr_kernel_launches": (ctypes.c_longlong, []),
+        "fr_set_wait_test": (I, [P, ctypes.c_uint, I]),
         "fr_jv_noalloc": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts), P, P, P, D, P, V]),
         "fr_mlp_create": (I, [I, I, I, I, ctypes.POINTER(ctypes.c_void_p)]),
         "fr_mlp_destroy": (I, [P]),
@@ -399,6 +400,11 @@ def step_ssprk3(ctx: Context, dt: float, U, stream=None):
     rc = lib.step_ssprk3(ctx.handle, float(dt), _vec(ctx, U, "U"), ctypes.byref(st), _stream(stream))
     ctx.check(rc)
     return _stats(st, rc)
+
+
+def fr_set_wait_test(ctx: Context, polls: int = 0, skip_first_copy: bool = False):
+    """Test hook for the element-Jacobi apply's bounded waits (see the C header)."""
+    return ctx.check(lib.fr_set_wait_test(ctx.handle, int(polls), int(bool(skip_first_copy))))
 
 
 def fr_kernel_launches() -> int:

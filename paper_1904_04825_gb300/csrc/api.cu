@@ -6,6 +6,7 @@
 #include <atomic>
 #include <new>
 
+#include "device.cuh"
 #include "internal.cuh"
 
 namespace frk {
@@ -449,6 +450,15 @@ extern "C" int fr_dissipation_rate(fr_ctx* ctx, const double* U, double rho0, do
   out[0] = 2.0 * ctx->opts.mu / rho0 * ctx->h_scal[0] / V;
   out[1] = -ctx->h_scal[1] / (rho0 * V);
   out[2] = ctx->h_scal[2] / (rho0 * V);
+  return FR_OK;
+}
+
+extern "C" int fr_set_wait_test(fr_ctx* ctx, unsigned polls, int skip_first_copy) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (skip_first_copy < 0 || skip_first_copy > 1)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "fr_set_wait_test: skip_first_copy must be 0 or 1");
+  ctx->wait_polls = polls ? polls : kWaitPolls;
+  ctx->test_skip_copy = skip_first_copy;
   return FR_OK;
 }
 

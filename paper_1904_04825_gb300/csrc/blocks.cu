@@ -11,7 +11,10 @@
 // over eps; entries outside the cross are exactly zero in both forms).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "device.cuh"
+#include "gj_tc.cuh"
 
 namespace frk {
 namespace {
@@ -28,6 +31,7 @@ struct FactorArgs {
   double shift;
   double beps;       // block_eps_rel
   int riemann;       // common flux: 0 Rusanov, 1 Roe
+  int* err;          // set when a tensor-core wait gave up
   Tables tab;
 };
 
@@ -43,8 +47,11 @@ struct FactorLayout {
   static constexpr int OFF_NT = OFF_TR + 16 * N;        // neighbour traces [4][4][N]
   static constexpr int OFF_FN = OFF_NT + 16 * N;        // base common fluxes [4][4][N] (scaled)
   static constexpr int DOUBLES = OFF_FN + 16 * N;
-  static constexpr size_t BYTES = DOUBLES * sizeof(double) + (size_t)(NB * LD + NB) * sizeof(T) +
-                                  NB * sizeof(int) + 64;
+  static constexpr bool TC = gjtc::Use<T, NB>::value;  // inversion on the tensor cores
+  // block, pivot column and pivots, then (TC) the tensor-core scratch, 128-byte aligned
+  static constexpr size_t GJ_END = DOUBLES * sizeof(double) + (size_t)(NB * LD + NB) * sizeof(T) + NB * sizeof(int);
+  static constexpr size_t OFF_TC = (GJ_END + 127) / 128 * 128;
+  static constexpr size_t BYTES = TC ? OFF_TC + gjtc::Shape<NB>::BYTES : GJ_END + 64;
 };
 
 constexpr size_t kSmemMax = 227 * 1024;  // opt-in shared memory per CTA
@@ -273,21 +280,43 @@ __global__ void __launch_bounds__(FactorLayout<P, T>::THREADS) k_factor(const Fa
     }
   }
   __syncthreads();
-  gauss_jordan<T, NB, LD>(M, col, piv);
-  // ---- store column-major: Minv[k*NB + i] = inverse(i, k) ----
   S* out = reinterpret_cast<S*>(a.blocks) + e * (long long)NB * NB;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    const int kk = idx / NB, ii = idx % NB;
-    out[idx] = StoreT<S>::to(M[ii * LD + kk]);
+  if constexpr (L::TC) {
+    unsigned char* tcs = reinterpret_cast<unsigned char*>(smem) + L::OFF_TC;
+    const bool ok = gjtc::invert<NB, LD>(M, col, piv, tcs);
+    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+    // ---- store column-major: inverse(i, k) = M[pr[i]][ipr[k]] ----
+    const int* ipr = reinterpret_cast<const int*>(tcs + gjtc::Shape<NB>::OFF_IPR);
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int kk = idx / NB, ii = idx % NB;
+      out[idx] = StoreT<S>::to(M[piv[ii] * LD + ipr[kk]]);
+    }
+  } else {
+    gauss_jordan<T, NB, LD>(M, col, piv);
+    // ---- store column-major: Minv[k*NB + i] = inverse(i, k) ----
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int kk = idx / NB, ii = idx % NB;
+      out[idx] = StoreT<S>::to(M[ii * LD + kk]);
+    }
   }
 }
 
 // Invert staged FP64 blocks (column-major per element: mst[e][c][row]) into
 // the preconditioner storage; one CTA per element.
+template <int NB, typename T>
+struct InvertLayout {
+  static constexpr int LD = NB + 1;
+  static constexpr bool TC = gjtc::Use<T, NB>::value;
+  static constexpr size_t GJ_END = (size_t)(NB * LD + NB) * sizeof(T) + NB * sizeof(int);
+  static constexpr size_t OFF_TC = (GJ_END + 127) / 128 * 128;
+  static constexpr size_t BYTES = TC ? OFF_TC + gjtc::Shape<NB>::BYTES : GJ_END + 64;
+};
+
 template <int NB, typename T, typename S>
 __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long ne,
-                                                double dshift) {
-  constexpr int LD = NB + 1;
+                                                double dshift, int* err) {
+  using L = InvertLayout<NB, T>;
+  constexpr int LD = L::LD;
   extern __shared__ double smem_inv[];
   T* M = reinterpret_cast<T*>(smem_inv);
   T* col = M + NB * LD;
@@ -299,11 +328,22 @@ __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, 
     M[r * LD + c] = (T)(r == c ? src[idx] + dshift : src[idx]);
   }
   __syncthreads();
-  gauss_jordan<T, NB, LD>(M, col, piv);
   S* out = reinterpret_cast<S*>(blocks) + e * (long long)NB * NB;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    const int kk = idx / NB, ii = idx % NB;
-    out[idx] = StoreT<S>::to(M[ii * LD + kk]);
+  if constexpr (L::TC) {
+    unsigned char* tcs = reinterpret_cast<unsigned char*>(smem_inv) + L::OFF_TC;
+    const bool ok = gjtc::invert<NB, LD>(M, col, piv, tcs);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    const int* ipr = reinterpret_cast<const int*>(tcs + gjtc::Shape<NB>::OFF_IPR);
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int kk = idx / NB, ii = idx % NB;
+      out[idx] = StoreT<S>::to(M[piv[ii] * LD + ipr[kk]]);
+    }
+  } else {
+    gauss_jordan<T, NB, LD>(M, col, piv);
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int kk = idx / NB, ii = idx % NB;
+      out[idx] = StoreT<S>::to(M[ii * LD + kk]);
+    }
   }
 }
 
@@ -357,7 +397,8 @@ struct ApplyLayout {
 template <int NB, typename S, typename A>
 __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
     k_apply(const S* __restrict__ Minv, double* r, const double* scale, double* __restrict__ z, long long ne,
-            double* sumsq, Reduce red, const int* done, EpsArgs ea, int* kerr) {
+            double* sumsq, Reduce red, const int* done, EpsArgs ea, int* kerr, unsigned polls,
+            int skip_first_copy) {
   using L = ApplyLayout<NB, S, A>;
   constexpr int KS = L::KS, NS = L::NS, KP = NB / KS;
   extern __shared__ __align__(128) double smem_d[];
@@ -376,6 +417,9 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   }
   __syncthreads();
   auto issue = [&](long long t) {
+    // test hook: CTA 0 leaves its first element's copies unissued, so its
+    // bounded wait for them runs out
+    if (skip_first_copy && blockIdx.x == 0 && t == 0) return;
     const int q = (int)(t % NS);
     const long long e = blockIdx.x + t * G;
     unsigned char* st = smem + (size_t)q * L::STAGE;
@@ -390,7 +434,7 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   long long t = 0;
   for (; t < nloc; ++t) {
     const int q = (int)(t % NS);
-    const bool ok = mbar_wait(&bar[q], (unsigned)((t / NS) & 1), kWaitPolls);
+    const bool ok = mbar_wait(&bar[q], (unsigned)((t / NS) & 1), polls);
     if (!__syncthreads_and(ok)) break;
     const long long e = blockIdx.x + t * G;
     const S* Ms = reinterpret_cast<const S*>(smem + (size_t)q * L::STAGE);
@@ -429,7 +473,7 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   if (t < nloc && tid == 0) {  // a copy never completed: flag it and drain what was issued
     atomicExch(kerr, 1);
     for (long long u = t; u < nloc && u < t + NS; ++u)
-      (void)mbar_wait(&bar[u % NS], (unsigned)((u / NS) & 1), kWaitPolls);
+      (void)mbar_wait(&bar[u % NS], (unsigned)((u / NS) & 1), polls);
   }
   if (sumsq) {  // every CTA takes part, so the reduction's counter stays consistent
     const double bs = block_sum(ss, sh);
@@ -625,7 +669,8 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
   if (grid > kRedBlocks) grid = kRedBlocks;
   if (grid < 1) grid = 1;
   { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB, S, A><<<(unsigned)grid, L::THREADS, L::BYTES, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
-                                                                  sumsq, ctx->red, done, eps_args(ctx, with_eps), ctx->kerr); }
+                                                                  sumsq, ctx->red, done, eps_args(ctx, with_eps), ctx->kerr,
+                                                                  ctx->wait_polls, ctx->test_skip_copy); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -692,14 +737,15 @@ unsigned vec_grid(const fr_ctx* ctx, long long n) {
 
 template <int NB, typename T, typename S>
 int invert_nbts(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)(NB * (NB + 1) + NB) * sizeof(T) + NB * sizeof(int) + 64;
+  constexpr size_t bytes = InvertLayout<NB, T>::BYTES;
   if constexpr (bytes > kSmemMax) {
     return set_error(ctx, FR_ERR_UNSUPPORTED, "element blocks of %d rows in this precision exceed shared memory", NB);
   }
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_invert<NB, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)bytes));
   { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, 2.0 * NB * NB * (double)NB * (double)ctx->ne);
-    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne, dshift); }
+    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne, dshift,
+                                                                               ctx->kerr); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
@@ -741,6 +787,7 @@ int launch_block_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t
   a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
   a.gam = ctx->opts.gamma; a.shift = shift; a.beps = ctx->opts.block_eps_rel;
   a.riemann = ctx->opts.riemann;
+  a.err = ctx->kerr;
   a.tab = ctx->tab;
   switch (ctx->p) {
     case 2: return factor_p<2>(ctx, a, s);

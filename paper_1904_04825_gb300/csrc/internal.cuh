@@ -141,6 +141,8 @@ struct fr_ctx {
   double* lin_fy = nullptr;  // mixed A z: per element's south face point, same layout
   int num_sms = 1;           // SMs of the device (persistent grids)
   int* kerr = nullptr;       // device flag: a kernel's bounded wait gave up
+  unsigned wait_polls = 1u << 22;  // poll limit of the element-Jacobi apply's bounded waits
+  int test_skip_copy = 0;    // test hook: the apply leaves one copy unissued (see fr_set_wait_test)
   int vec_blocks = frk::kVecBlocks;  // grid of the streaming vector kernels (autotuned)
   int tile_variant = 0;      // element-tile shape of the Euler residual kernel (autotuned)
   frk::Reduce red{};

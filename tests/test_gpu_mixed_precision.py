@@ -1,10 +1,13 @@
 """Reduced-precision element-Jacobi blocks (FP32 inversion, FP32 or BF16
 storage) against the FP64 oracle.
 
-The preconditioner's own error is stated against the oracle's FP64 blocks:
-FP32 Gauss-Jordan leaves about n u_32 cond(M) (n = 64, u_32 = 6e-8) relative
-error in M^-1 r, bound 1e-4; BF16 storage rounds every entry to 8 bits
-(u_bf16 = 3.9e-3), bound 3e-2.  The converged linear solves and the
+The preconditioner's own error is stated against the oracle's FP64 blocks.
+The FP32-class inversion runs its trailing updates on the tensor cores with
+every operand split into two TF32 halves (about 22 bits of it, an effective
+unit roundoff of 2^-23 = 1.2e-7, twice that of FP32); it leaves about
+n u cond(M) relative error in M^-1 r, bound 2e-4 (measured 1.0e-4 on the
+walled channel's blocks of condition 4e5); BF16 storage rounds every entry
+to 8 bits (u_bf16 = 3.9e-3), bound 3e-2.  The converged linear solves and the
 end-of-run state do not depend on the preconditioner: with tol_lin = 1e-12
 they match the FP64 oracle to 1e-9 like the FP64 path."""
 import numpy as np
@@ -19,7 +22,7 @@ from oracle.tableaus import ROW
 
 pytestmark = pytest.mark.gpu
 
-PREC_TOL = {1: 1e-4, 2: 3e-2}
+PREC_TOL = {1: 2e-4, 2: 3e-2}
 
 
 @pytest.fixture(scope="module")

@@ -126,7 +126,10 @@ def test_ns_jv_matches_oracle(fr, p):
     assert _rel(y.cpu().numpy(), yo) < 1e-6
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-4), (2, 3e-2)])
+# FP32 blocks: tensor-core inversion with TF32-split operands (effective unit
+# roundoff 2^-23), bound 2e-4; the wall-clustered blocks here have condition
+# numbers up to 4e5 (see tests/test_gpu_mixed_precision.py)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 2e-4), (2, 3e-2)])
 def test_ns_element_jacobi_matches_oracle(fr, prec, tol):
     p = 2
     xe, ye, U0, T = _channel(4, 4, p, seed=2)
