@@ -77,7 +77,7 @@ template <> struct Tile<6, 0> { static constexpr int TX = 2, TY = 2; };
 template <> struct Tile<6, 1> { static constexpr int TX = 5, TY = 1; };
 
 template <int P, int MODE, int TV, int RM>
-__global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
+__global__ void __launch_bounds__(256, 4) k_residual(const ResArgs a) {
   constexpr int N = P + 1, NP = N * N;
   constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
   constexpr int NXF = (TX + 1) * TY * N;  // points on the tile's x-faces (normal +x)
@@ -87,9 +87,13 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
   __shared__ double sF[NE][4][NP];
   __shared__ double sG[NE][4][NP];
   __shared__ double str[NE][4][4][N];       // own traces [face W,E,S,N][var][k]
+  __shared__ double shx[2][TY][4][N];       // outside traces on the tile's west / east faces
+  __shared__ double shy[2][TX][4][N];       // outside traces on the tile's south / north faces
   __shared__ double sfx[TY][TX + 1][4][N];  // common flux f_n on x-face xf of tile row ly
   __shared__ double sfy[TX][TY + 1][4][N];  // common flux g_n on y-face yf of tile column lx
   __shared__ double sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+  constexpr int NOWN = NE * 4 * N;           // own-trace work items
+  constexpr int NHALO = 2 * (TX + TY) * N;   // outside-trace work items
 
   if (a.done && *a.done) return;
   if (threadIdx.x < N * N) sDt[threadIdx.x / N][threadIdx.x % N] = a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
@@ -135,42 +139,63 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
     }
   }
   __syncthreads();
-  // ---- 2a: own solution traces on the four faces of every tile element ----
-  for (int idx = threadIdx.x; idx < NE * 4 * N; idx += blockDim.x) {
-    const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
-    if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
-    const int off = face < 2 ? N * k : k;
-    const int stride = face < 2 ? 1 : N;
-    const double* c = (face == 0 || face == 2) ? slm : slp;
+  // ---- 2a: own solution traces on the four faces of every tile element,
+  //      then (separate work items, starting on a warp boundary when NOWN is
+  //      a multiple of 32, so the FP64 work does not diverge) the outside
+  //      neighbours' traces on the tile's boundary faces, from global memory ----
+  for (int idx = threadIdx.x; idx < NOWN + NHALO; idx += blockDim.x) {
+    if (idx < NOWN) {
+      const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
+      if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
+      const int off = face < 2 ? N * k : k;
+      const int stride = face < 2 ? 1 : N;
+      const double* c = (face == 0 || face == 2) ? slm : slp;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) str[e2][face][v][k] = trace_sum<N>(&sq[e2][v][off], stride, c);
+      for (int v = 0; v < 4; ++v) str[e2][face][v][k] = trace_sum<N>(&sq[e2][v][off], stride, c);
+    } else {
+      const int h = idx - NOWN, seg = h / N, k = h % N;
+      long long nb;
+      int off, stride;
+      const double* c;
+      double* dst;
+      if (seg < 2 * TY) {  // west (side 0) / east (side 1) boundary of tile row fy
+        const int side = seg / TY, fy = seg % TY;
+        if (fy >= ay) continue;
+        const int gx = side == 0 ? (ix0 + a.nx - 1) % a.nx : (ix0 + ax) % a.nx;
+        nb = (long long)gx + (long long)a.nx * (iy0 + fy);
+        off = N * k;
+        stride = 1;
+        c = side == 0 ? slp : slm;  // the west neighbour's east trace, the east one's west trace
+        dst = &shx[side][fy][0][k];
+      } else {             // south (side 0) / north (side 1) boundary of tile column fx
+        const int s2 = seg - 2 * TY, side = s2 / TX, fx = s2 % TX;
+        if (fx >= ax) continue;
+        const int gy = side == 0 ? (iy0 + a.ny - 1) % a.ny : (iy0 + ay) % a.ny;
+        nb = (long long)(ix0 + fx) + (long long)a.nx * gy;
+        off = k;
+        stride = N;
+        c = side == 0 ? slp : slm;
+        dst = &shy[side][fx][0][k];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        dst[v * N] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + off, stride, c, eps);
+    }
   }
   __syncthreads();
-  // ---- 2b: one Rusanov flux per face point; faces on the tile boundary take
-  //      the outside neighbour's trace from global memory ----
+  // ---- 2b: one Rusanov flux per face point, both traces from shared memory ----
   for (int idx = threadIdx.x; idx < NXF + NYF; idx += blockDim.x) {
     double qm[4], qp[4], fc[4];
     if (idx < NXF) {
       const int k = idx % N, rr = idx / N, xf = rr % (TX + 1), fy = rr / (TX + 1);
       if (fy >= ay || xf > ax) continue;
       const int gy = iy0 + fy;
-      if (xf >= 1) {
+      const double* pm = xf >= 1 ? &str[xf - 1 + TX * fy][1][0][k] : &shx[0][fy][0][k];
+      const double* pp = xf < ax ? &str[xf + TX * fy][0][0][k] : &shx[1][fy][0][k];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) qm[v] = str[xf - 1 + TX * fy][1][v][k];
-      } else {
-        const long long nb = (long long)((ix0 + a.nx - 1) % a.nx) + (long long)a.nx * gy;
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          qm[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slp, eps);
-      }
-      if (xf < ax) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) qp[v] = str[xf + TX * fy][0][v][k];
-      } else {
-        const long long nb = (long long)((ix0 + ax) % a.nx) + (long long)a.nx * gy;
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + N * k, 1, slm, eps);
+      for (int v = 0; v < 4; ++v) {
+        qm[v] = pm[v * N];
+        qp[v] = pp[v * N];
       }
       riemann_flux(RM, qm, qp, 0, a.gam, fc);
 #pragma unroll
@@ -189,23 +214,12 @@ __global__ void __launch_bounds__(256) k_residual(const ResArgs a) {
       const int k = i2 % N, rr = i2 / N, yf = rr % (TY + 1), fx = rr / (TY + 1);
       if (fx >= ax || yf > ay) continue;
       const int gx = ix0 + fx;
-      if (yf >= 1) {
+      const double* pm = yf >= 1 ? &str[fx + TX * (yf - 1)][3][0][k] : &shy[0][fx][0][k];
+      const double* pp = yf < ay ? &str[fx + TX * yf][2][0][k] : &shy[1][fx][0][k];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) qm[v] = str[fx + TX * (yf - 1)][3][v][k];
-      } else {
-        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + a.ny - 1) % a.ny);
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          qm[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slp, eps);
-      }
-      if (yf < ay) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) qp[v] = str[fx + TX * yf][2][v][k];
-      } else {
-        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + ay) % a.ny);
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          qp[v] = trace_global<N, PERTURB>(a.U, a.z, nb * 4 * NP + v * NP + k, N, slm, eps);
+      for (int v = 0; v < 4; ++v) {
+        qm[v] = pm[v * N];
+        qp[v] = pp[v * N];
       }
       riemann_flux(RM, qm, qp, 1, a.gam, fc);
 #pragma unroll
@@ -269,6 +283,9 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
   constexpr int NYF = (TY + 1) * TX * N;
   __shared__ float sdF[NE][4][NP], sdG[NE][4][NP], sz[NE][4][NP];
   __shared__ float strz[NE][4][4][N];         // own traces of z [face W,E,S,N][var][k]
+  __shared__ float shzx[2][TY][4][N];         // outside traces of z on the tile's west / east faces
+  __shared__ float shzy[2][TX][4][N];         // outside traces of z on the tile's south / north faces
+  constexpr int NOWN = NE * 4 * N, NHALO = 2 * (TX + TY) * N;
   __shared__ float sfx[TY][TX + 1][4][N];     // df on x-faces
   __shared__ float sfy[TX][TY + 1][4][N];     // df on y-faces
   __shared__ float sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
@@ -308,19 +325,49 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
     }
   }
   __syncthreads();
-  // ---- 2a: own traces of z (FP32) ----
-  for (int idx = threadIdx.x; idx < NE * 4 * N; idx += blockDim.x) {
-    const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
-    if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
-    const int off = face < 2 ? N * k : k;
-    const int stride = face < 2 ? 1 : N;
-    const float* c = (face == 0 || face == 2) ? slm : slp;
+  // ---- 2a: own traces of z (FP32), then the outside neighbours' traces of z
+  //      on the tile's boundary faces (separate work items, from global memory) ----
+  for (int idx = threadIdx.x; idx < NOWN + NHALO; idx += blockDim.x) {
+    if (idx < NOWN) {
+      const int e2 = idx / (4 * N), face = (idx / N) % 4, k = idx % N;
+      if ((e2 % TX) >= ax || (e2 / TX) >= ay) continue;
+      const int off = face < 2 ? N * k : k;
+      const int stride = face < 2 ? 1 : N;
+      const float* c = (face == 0 || face == 2) ? slm : slp;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      float s2 = c[0] * sz[e2][v][off];
+      for (int v = 0; v < 4; ++v) {
+        float s2 = c[0] * sz[e2][v][off];
 #pragma unroll
-      for (int q = 1; q < N; ++q) s2 = fmaf(c[q], sz[e2][v][off + q * stride], s2);
-      strz[e2][face][v][k] = s2;
+        for (int q = 1; q < N; ++q) s2 = fmaf(c[q], sz[e2][v][off + q * stride], s2);
+        strz[e2][face][v][k] = s2;
+      }
+    } else {
+      const int h = idx - NOWN, seg = h / N, k = h % N;
+      long long nb;
+      int off, stride;
+      const double* c;
+      float* dst;
+      if (seg < 2 * TY) {
+        const int side = seg / TY, fy = seg % TY;
+        if (fy >= ay) continue;
+        const int gx = side == 0 ? (ix0 + a.nx - 1) % a.nx : (ix0 + ax) % a.nx;
+        nb = (long long)gx + (long long)a.nx * (iy0 + fy);
+        off = N * k;
+        stride = 1;
+        c = side == 0 ? a.tab.lp : a.tab.lm;
+        dst = &shzx[side][fy][0][k];
+      } else {
+        const int s2 = seg - 2 * TY, side = s2 / TX, fx = s2 % TX;
+        if (fx >= ax) continue;
+        const int gy = side == 0 ? (iy0 + a.ny - 1) % a.ny : (iy0 + ay) % a.ny;
+        nb = (long long)(ix0 + fx) + (long long)a.nx * gy;
+        off = k;
+        stride = N;
+        c = side == 0 ? a.tab.lp : a.tab.lm;
+        dst = &shzy[side][fx][0][k];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dst[v * N] = (float)trace_sum<N>(a.z + nb * 4 * NP + v * NP + off, stride, c);
     }
   }
   __syncthreads();
@@ -337,20 +384,12 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
       const int gy = iy0 + fy;
       const long long ep = (long long)((ix0 + xf) % a.nx) + (long long)a.nx * gy;  // element east of the face
       cache = a.lin_fx + (ep * N + k) * 12;
-      if (xf >= 1) {
+      const float* pm = xf >= 1 ? &strz[xf - 1 + TX * fy][1][0][k] : &shzx[0][fy][0][k];
+      const float* pp = xf < ax ? &strz[xf + TX * fy][0][0][k] : &shzx[1][fy][0][k];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) tzm[v] = strz[xf - 1 + TX * fy][1][v][k];
-      } else {
-        const long long nb = (long long)((ix0 + a.nx - 1) % a.nx) + (long long)a.nx * gy;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzm[v] = (float)trace_sum<N>(a.z + nb * 4 * NP + v * NP + N * k, 1, a.tab.lp);
-      }
-      if (xf < ax) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzp[v] = strz[xf + TX * fy][0][v][k];
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzp[v] = (float)trace_sum<N>(a.z + ep * 4 * NP + v * NP + N * k, 1, a.tab.lm);
+      for (int v = 0; v < 4; ++v) {
+        tzm[v] = pm[v * N];
+        tzp[v] = pp[v * N];
       }
       dir = 0; sx0 = fy; sx1 = xf; sx3 = k; sx2 = 0;
     } else {
@@ -360,20 +399,12 @@ __global__ void __launch_bounds__(256) k_jv32(const ResArgs a) {
       const int gx = ix0 + fx;
       const long long ep = (long long)gx + (long long)a.nx * ((iy0 + yf) % a.ny);  // element north of the face
       cache = a.lin_fy + (ep * N + k) * 12;
-      if (yf >= 1) {
+      const float* pm = yf >= 1 ? &strz[fx + TX * (yf - 1)][3][0][k] : &shzy[0][fx][0][k];
+      const float* pp = yf < ay ? &strz[fx + TX * yf][2][0][k] : &shzy[1][fx][0][k];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) tzm[v] = strz[fx + TX * (yf - 1)][3][v][k];
-      } else {
-        const long long nb = (long long)gx + (long long)a.nx * ((iy0 + a.ny - 1) % a.ny);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzm[v] = (float)trace_sum<N>(a.z + nb * 4 * NP + v * NP + k, N, a.tab.lp);
-      }
-      if (yf < ay) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzp[v] = strz[fx + TX * yf][2][v][k];
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) tzp[v] = (float)trace_sum<N>(a.z + ep * 4 * NP + v * NP + k, N, a.tab.lm);
+      for (int v = 0; v < 4; ++v) {
+        tzm[v] = pm[v * N];
+        tzp[v] = pp[v * N];
       }
       dir = 1; sx0 = fx; sx1 = yf; sx3 = k; sx2 = 0;
     }
