@@ -310,15 +310,17 @@ def our_arm(args):
               + ("" if p <= 2 else "-noprecond"))
     else:
         ch = S.Channel()
-        xe = np.linspace(0.0, ch.lx, 257)
-        ye = S.channel_y_edges(128, first=1e-3, ratio=1.15)
-        X, Y = S.point_coords(xe, ye, P)
+        cnx, cny = args.nx or 256, args.ny or 128
+        xe = np.linspace(0.0, ch.lx, cnx + 1)
+        ye = S.channel_y_edges(cny, first=1e-3, ratio=1.15)
+        p = args.p or P
+        X, Y = S.point_coords(xe, ye, p)
         U0 = ch.state(X, Y, seed=0)
-        p, dt, wall = P, (args.dt or 1e-3), True
+        dt, wall = (args.dt or 1e-3), True
         opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=30, gmres_max_restarts=20, block_precision=prec,
                                mu=ch.mu, prandtl=ch.prandtl, body_force_x=ch.body_force,
                                wall_temperature=ch.temperature)
-        wl = f"channel-256x128-p3-Re1000-M0.2-{args.scheme.upper()}-dt{dt:g}"
+        wl = f"channel-{cnx}x{cny}-p{p}-Re1000-M0.2-{args.scheme.upper()}-dt{dt:g}"
     if prec:
         wl += f"-{args.block_precision}blocks"
     if args.jv_precision == "fp32":
@@ -840,6 +842,130 @@ def batch_arm(args):
     return 0
 
 
+def guess_arm(args):
+    """The learned initial guess at its workload: the stretched viscous
+    channel (Re 1000, M 0.2, walls clustered to a first cell of 1e-3 with
+    ratio 1.15) on a 384 x 192 mesh at p = 4 (7.4 M DOFs, 100 x 100 element
+    blocks), ROW3 steps of dt with GMRES(30) to tol_lin = 1e-8.
+
+    Training data: for each training seed s, the seeded perturbed channel
+    state, one ROW3 step (which leaves the previous-step history) and a
+    second step whose four stage solves are captured (features and targets
+    of every 61st element, the offset rotating per stage).  The per-element
+    MLP (300 -> 256 -> 256 -> 100) is trained by the library's FP32
+    forward / backward / Adam kernels on random minibatches.  Evaluation:
+    held-out seeds, two steps each with the zero guess, the previous-step
+    guess and the learned guess (BF16 tensor-core inference); reported are
+    the GMRES iterations and the wall time of the second step (the first has
+    no history), all at the same absolute tolerance tol_lin * ||b||."""
+    import numpy as np
+    import torch
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    torch.cuda.set_device(0)
+    prec = {"fp64": 0, "fp32": 1, "bf16": 2}[args.block_precision]
+    nx, ny, p = args.nx or 384, args.ny or 192, args.p or 4
+    dt = args.dt or 1e-3
+    ch = S.Channel()
+    xe = np.linspace(0.0, ch.lx, nx + 1)
+    ye = S.channel_y_edges(ny, first=1e-3, ratio=1.15)
+    X, Y = S.point_coords(xe, ye, p)
+    nb = 4 * (p + 1) ** 2
+    ne = nx * ny
+    stride = 61
+
+    def opts(mode):
+        return fr.default_opts(tol_lin=1e-8, gmres_m=30, gmres_max_restarts=60, block_precision=prec,
+                               mu=ch.mu, prandtl=ch.prandtl, body_force_x=ch.body_force,
+                               wall_temperature=ch.temperature, guess=mode)
+
+    def state(seed):
+        return torch.from_numpy(ch.state(X, Y, seed=seed)).cuda()
+
+    ctx = {m: fr.Context(xe, ye, p, opts(m), wall_y=True) for m in (0, 1, 2)}
+    train = list(range(1, args.train_seeds + 1))
+    per_seed = 4 * ((ne + stride - 1) // stride)
+    cap = per_seed * len(train)
+    Xc = torch.empty((cap, 3 * nb), dtype=torch.float32, device="cuda")
+    Tc = torch.empty((cap, nb), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    n = 0
+    gen_iters = 0
+    c1 = ctx[1]
+    for s in train:
+        U = state(s)
+        fr.fr_reset_history(c1)
+        gen_iters += fr.step_row(c1, 3, dt, U).gmres_iters
+        fr.fr_set_stage_capture(c1, Xc[n:], Tc[n:], per_seed, stride)
+        gen_iters += fr.step_row(c1, 3, dt, U).gmres_iters
+        n += fr.fr_stage_capture_count(c1)
+        fr.fr_set_stage_capture(c1, None, None, 0, 1)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    rng = np.random.default_rng(0)
+    sizes = [3 * nb, 256, 256, nb]
+    model = fr.MLP(3 * nb, 256, nb, max_batch=max(8192, ne))
+    flat = []
+    for a, b in zip(sizes[:-1], sizes[1:]):   # He-uniform weights, zero biases
+        lim = math.sqrt(6.0 / a)
+        flat.append(rng.uniform(-lim, lim, a * b).astype(np.float32))
+        flat.append(np.zeros(b, np.float32))
+    model.set_params(np.concatenate(flat))
+    bs = 8192
+    Yb = torch.empty((bs, nb), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    losses = []
+    iters = args.train_iters
+    for it in range(iters):
+        idx = torch.from_numpy(rng.integers(0, n, bs)).cuda()
+        xb, tb = Xc[idx].contiguous(), Tc[idx].contiguous()
+        model.forward(xb, Yb)
+        losses.append(model.backward(xb, tb))
+        model.adam(1e-3 if it < iters * 2 // 3 else 3e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # loss of predicting no change, for scale
+    Tz = Tc[:n]
+    zero_loss = float((Tz.double() ** 2).sum(dim=1).mean() / 2 / nb)
+    del Xc, Tc
+    fr.fr_attach_guess_model(ctx[2], model)
+
+    evals = list(range(10001, 10001 + args.eval_seeds))
+    res = {m: {"iters": 0, "seconds": 0.0, "unconverged": 0} for m in (0, 1, 2)}
+    for s in evals:
+        for m in (0, 1, 2):
+            c = ctx[m]
+            U = state(s)
+            fr.fr_reset_history(c)
+            fr.step_row(c, 3, dt, U)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st = fr.step_row(c, 3, dt, U)
+            torch.cuda.synchronize()
+            res[m]["seconds"] += time.perf_counter() - t1
+            res[m]["iters"] += st.gmres_iters
+            res[m]["unconverged"] += 0 if st.converged else 1
+    tried, used = fr.fr_guess_stats(ctx[2])
+    names = {0: "zero", 1: "previous_step", 2: "learned"}
+    out = {"workload": f"learned-guess-channel-{nx}x{ny}-p{p}-ROW3-dt{dt:g}-tol1e-8-{args.block_precision}blocks",
+           "ndof": ctx[0].ndof, "train_seeds": [train[0], train[-1]], "stage_solves_captured": 4 * len(train),
+           "samples": n, "elem_stride": stride, "generation_s": gen_s, "generation_gmres_iters": gen_iters,
+           "train_iters": iters, "minibatch": bs, "train_s": train_s,
+           "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-50:])),
+           "loss_zero_prediction": zero_loss,
+           "eval_seeds": [evals[0], evals[-1]],
+           "second_step": {names[m]: {"gmres_iters_per_step": res[m]["iters"] / len(evals),
+                                      "seconds_per_step": res[m]["seconds"] / len(evals),
+                                      "unconverged": res[m]["unconverged"]} for m in (0, 1, 2)},
+           "learned_guess_kept": [int(used), int(tried)]}
+    print(json.dumps(out))
+    for c in ctx.values():
+        c.close()
+    return 0
+
+
 def mlp_kernel_arm(args):
     """The per-element guess MLP at the size of its largest workload: one
     inference (BF16 tensor cores, FP32 accumulate) or one training step
@@ -913,7 +1039,10 @@ def main():
                     help="common inviscid flux (roe: the paper's; Euler only)")
     ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: linear parts of the FD operator in FP32 (Euler only)")
-    ap.add_argument("--workload", choices=["vortex", "channel", "batch", "tgv"], default="vortex")
+    ap.add_argument("--workload", choices=["vortex", "channel", "batch", "tgv", "guess"], default="vortex")
+    ap.add_argument("--train-seeds", type=int, default=500, help="--workload guess: training seeds (4 stage solves each)")
+    ap.add_argument("--eval-seeds", type=int, default=50, help="--workload guess: held-out seeds")
+    ap.add_argument("--train-iters", type=int, default=3000, help="--workload guess: Adam steps")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])
@@ -932,6 +1061,7 @@ def main():
     ap.add_argument("--gmres-m", type=int, default=30, help="--t-end: GMRES restart length (<= 63; the paper's 60)")
     ap.add_argument("--eps-fixed", type=float, default=0.0, help="--t-end: fixed FD step (the paper's 1e-8)")
     ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--ny", type=int, default=None, help="--workload channel: cells across the channel")
     ap.add_argument("--p", type=int, default=None)
     args = ap.parse_args()
     if args.scheme is None and args.workload != "batch":
@@ -946,6 +1076,8 @@ def main():
         return t_end_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "guess":
+        return guess_arm(args)
     return our_arm(args)
 
 
