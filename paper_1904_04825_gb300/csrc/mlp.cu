@@ -19,6 +19,7 @@
 #include <new>
 
 #include "device.cuh"
+#include "umma_ws.cuh"
 
 struct fr_mlp {
   int n[4] = {0, 0, 0, 0};  // layer widths: in, hidden, hidden, out
@@ -37,6 +38,12 @@ struct fr_mlp {
   __nv_bfloat16* W16[3] = {};     // BF16 weights [n[l+1]][kp[l]], zero-padded columns
   int kp[3] = {0, 0, 0};          // padded widths of the layer inputs
   int* derr = nullptr;            // device flag: a bounded wait of the GEMM gave up
+  // TMA tensor maps of the inference operands (input rows, hidden rows, weights)
+  // for the weight-stationary GEMM; ws = 1 when every layer's weights fit in
+  // shared memory and the maps were built
+  CUtensorMap amap[3] = {};       // layer l input: X16 (l = 0), H16[l-1]
+  CUtensorMap wmap[3] = {};
+  int ws = 0;
   int* herr = nullptr;            // pinned host copy, refreshed after every inference
   double* loss = nullptr;   // device scalar
   int step = 0;
@@ -421,6 +428,51 @@ int refresh_bf16(fr_mlp* m, cudaStream_t s) {
   return FR_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D BF16 row-major [rows][ld] (cols <= ld valid), boxes of 64 columns x box_rows
+// rows, 128-byte swizzle, zero fill outside
+bool make_map(CUtensorMap* map, const void* base, long long rows, int cols, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)umws::BK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor maps of the weight-stationary inference (all three layers, or none)
+void build_maps(fr_mlp* m) {
+  m->ws = 0;
+  for (int l = 0; l < 3; ++l)
+    if (!umws::fits(m->n[l + 1], m->kp[l])) return;
+  for (int l = 0; l < 3; ++l) {
+    const void* in = l == 0 ? (const void*)m->X16 : (const void*)m->H16[l - 1];
+    if (!make_map(&m->amap[l], in, m->max_batch, m->kp[l], m->kp[l], umws::BM)) return;
+    if (!make_map(&m->wmap[l], m->W16[l], m->n[l + 1], m->kp[l], m->kp[l], umws::npad_of(m->n[l + 1]))) return;
+  }
+  m->ws = 1;
+}
+
 void free_mlp(fr_mlp* m) {
   if (!m) return;
   cudaFree(m->P); cudaFree(m->G); cudaFree(m->Mo); cudaFree(m->Vo);
@@ -496,6 +548,7 @@ extern "C" int fr_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, f
     if (e == cudaSuccess) e = cudaMemset(g_mlp_red[dev].counter, 0, sizeof(unsigned));
   }
   if (e != cudaSuccess) return fail(e);
+  build_maps(m);
   *out = m;
   return FR_OK;
 }
@@ -567,6 +620,36 @@ extern "C" int fr_mlp_forward(fr_mlp* m, const float* X, int M, float* Y, int bf
     }
     count_launch();
     k_f2bf_pad<<<grid_for((long long)M * m->kp[0]), 256, 0, s>>>(X, m->X16, M, m->n[0], m->kp[0]);
+    if (m->ws) {
+      // weight-stationary persistent GEMMs: one CTA per SM (at most one per 128-row tile)
+      static int sms = 0;
+      if (sms == 0) {
+        int dev = 0;
+        MLP_CUDA(m, cudaGetDevice(&dev));
+        MLP_CUDA(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MLP_CUDA(m, cudaFuncSetAttribute(umws::k_umma_ws<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)umws::kSmemLimit));
+        MLP_CUDA(m, cudaFuncSetAttribute(umws::k_umma_ws<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)umws::kSmemLimit));
+      }
+      const int tiles = (M + umws::BM - 1) / umws::BM;
+      const unsigned grid = (unsigned)std::min(tiles, sms);
+      for (int l = 0; l < 3; ++l) {
+        const int N = m->n[l + 1];
+        const size_t smem = umws::smem_bytes(N, m->kp[l]);
+        count_launch();
+        if (l < 2)
+          umws::k_umma_ws<true, true><<<grid, umws::THREADS, smem, s>>>(m->amap[l], m->wmap[l], M, N, m->kp[l],
+                                                                        m->P + off_b(m, l), m->H16[l], m->kp[l + 1],
+                                                                        m->derr);
+        else
+          umws::k_umma_ws<false, false><<<grid, umws::THREADS, smem, s>>>(m->amap[l], m->wmap[l], M, N, m->kp[l],
+                                                                          m->P + off_b(m, l), Y, N, m->derr);
+      }
+      MLP_CUDA(m, cudaGetLastError());
+      MLP_CUDA(m, cudaMemcpyAsync(m->herr, m->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      return FR_OK;
+    }
     const __nv_bfloat16* in = m->X16;
     for (int l = 0; l < 3; ++l) {
       const int N = m->n[l + 1];
