@@ -785,6 +785,15 @@ def batch_arm(args):
     clk = clocks.stop()
     launches = fr.fr_kernel_launches() - launches0
     ms_seq, units_seq = timed(seq_step, args.steps)
+    # the same batch with per-instance cycle kernels (no batched launches)
+    nodes_batched = B.cycle_kernels()
+    B.set_batched(False)
+    for _ in range(2):
+        batch_step()   # recaptures the cycle graphs
+    nodes_per_instance = B.cycle_kernels()
+    ms_pi, units_pi = timed(batch_step, args.steps)
+    B.set_batched(True)
+    batch_step()
 
     # end to end: every state from pinned host memory and back, each step
     host_in = [torch.from_numpy(u.cpu().numpy()).pin_memory() for u in Ub]
@@ -829,6 +838,10 @@ def batch_arm(args):
         "sequential": {"value": units_seq / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps,
                        "note": "same instances, one single-instance step call after another"},
         "speedup_vs_sequential": (units / ms) / (units_seq / ms_seq),
+        "per_instance_cycles": {"value": units_pi / (ms_pi * 1e-3), "ms_per_step": ms_pi / args.steps,
+                                "cycle_graph_kernels": nodes_per_instance,
+                                "note": "same batch, every instance enqueuing its own cycle kernels"},
+        "cycle_graph_kernels": nodes_batched,
         "gpu_launches": launches, "clocks": clk,
         "roofline": None,
         "roofline_note": "kernels run inside CUDA graphs; per-kernel event timing does not apply",
@@ -857,7 +870,8 @@ def guess_arm(args):
     held-out seeds, two steps each with the zero guess, the previous-step
     guess and the learned guess (BF16 tensor-core inference); reported are
     the GMRES iterations and the wall time of the second step (the first has
-    no history), all at the same absolute tolerance tol_lin * ||b||."""
+    no history), all at the same absolute tolerance tol_lin * ||b||
+    (--guess-tol)."""
     import numpy as np
     import torch
     import paper_1904_04825_gb300 as fr
@@ -875,8 +889,10 @@ def guess_arm(args):
     ne = nx * ny
     stride = 61
 
+    tol = args.guess_tol
+
     def opts(mode):
-        return fr.default_opts(tol_lin=1e-8, gmres_m=30, gmres_max_restarts=60, block_precision=prec,
+        return fr.default_opts(tol_lin=tol, gmres_m=30, gmres_max_restarts=60, block_precision=prec,
                                mu=ch.mu, prandtl=ch.prandtl, body_force_x=ch.body_force,
                                wall_temperature=ch.temperature, guess=mode)
 
@@ -903,6 +919,15 @@ def guess_arm(args):
         fr.fr_set_stage_capture(c1, None, None, 0, 1)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+    # floor of the stage solves: one GMRES(30) solve of the first stage's
+    # system at a seeded state, 20 restarts, target 1e-12 (relres at exit)
+    U = state(train[0])
+    R0 = c1.empty()
+    fr.fr_residual(c1, U, R0)
+    shift = 1.0 / (0.435866521508459 * dt)
+    fr.ejacobi_factor(c1, U, R0, shift)
+    xg = torch.zeros_like(U)
+    floor = fr.gmres_solve(c1, U, R0, shift, R0, xg, m=30, rtol=1e-12, max_restarts=20)
 
     rng = np.random.default_rng(0)
     sizes = [3 * nb, 256, 256, nb]
@@ -949,9 +974,10 @@ def guess_arm(args):
             res[m]["unconverged"] += 0 if st.converged else 1
     tried, used = fr.fr_guess_stats(ctx[2])
     names = {0: "zero", 1: "previous_step", 2: "learned"}
-    out = {"workload": f"learned-guess-channel-{nx}x{ny}-p{p}-ROW3-dt{dt:g}-tol1e-8-{args.block_precision}blocks",
+    out = {"workload": f"learned-guess-channel-{nx}x{ny}-p{p}-ROW3-dt{dt:g}-tol{tol:g}-{args.block_precision}blocks",
            "ndof": ctx[0].ndof, "train_seeds": [train[0], train[-1]], "stage_solves_captured": 4 * len(train),
            "samples": n, "elem_stride": stride, "generation_s": gen_s, "generation_gmres_iters": gen_iters,
+           "stage_solve_floor": {"relres": floor.relres, "iters": floor.iters, "target": 1e-12},
            "train_iters": iters, "minibatch": bs, "train_s": train_s,
            "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-50:])),
            "loss_zero_prediction": zero_loss,
@@ -1043,6 +1069,7 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=500, help="--workload guess: training seeds (4 stage solves each)")
     ap.add_argument("--eval-seeds", type=int, default=50, help="--workload guess: held-out seeds")
     ap.add_argument("--train-iters", type=int, default=3000, help="--workload guess: Adam steps")
+    ap.add_argument("--guess-tol", type=float, default=1e-8, help="--workload guess: GMRES tolerance tol_lin")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])

@@ -392,6 +392,19 @@ int fr_batch_create(int count, const fr_mesh_desc* meshes, const int* degrees, c
                     fr_batch** out);
 int fr_batch_destroy(fr_batch* batch);
 const char* fr_batch_last_error(const fr_batch* batch);
+/* Launch structure of the batch's GMRES cycles.  on = 1 (the default): when
+ * every instance is a 2D Euler context of degree 2..4 with element-Jacobi
+ * blocks and the FP64 FD operator, each Arnoldi iteration of all instances
+ * runs as one batched launch per kernel (per degree for the block apply
+ * and the FD operator): the grid holds the CTAs of every instance, each CTA
+ * finds its instance from a device table of per-instance arguments and CTA
+ * ranges, and instances whose cycle is done skip their work on the device.
+ * Every instance keeps the CTA partition of its own launches, so results
+ * equal those of single-instance steps.  on = 0: every instance enqueues its
+ * own cycle kernels on its stream.  Changing it drops the captured graphs. */
+int fr_batch_set_batched(fr_batch* batch, int on);
+/* Kernel nodes of the largest captured cycle graph (0 before the first step). */
+int fr_batch_cycle_kernels(const fr_batch* batch, long long* kernels);
 /* Context of instance k (owned by the batch; NULL when out of range), for
  * fr_residual, fr_set_launch_config, fr_autotune and friends. */
 fr_ctx* fr_batch_member(fr_batch* batch, int k);

@@ -149,6 +149,8 @@ def _load():
         "fr_batch_destroy": (I, [P]),
         "fr_batch_last_error": (ctypes.c_char_p, [P]),
         "fr_batch_member": (P, [P, I]),
+        "fr_batch_set_batched": (I, [P, I]),
+        "fr_batch_cycle_kernels": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
         "fr_batch_step_row": (I, [P, I, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fr_step_stats), V]),
         "fr_batch_step_esdirk": (I, [P, I, D, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(fr_ptc_opts), I,
                                      ctypes.POINTER(fr_step_stats), V]),
@@ -652,6 +654,19 @@ class Batch:
         if rc != FR_OK and rc not in allow:
             raise FrError(rc, lib.fr_batch_last_error(self.handle).decode())
         return [_stats(st[k], rc) for k in range(len(self.members))]
+
+    def set_batched(self, on: bool):
+        """Batched Arnoldi launches over all instances (True, the default) or
+        per-instance cycle kernels (False)."""
+        rc = lib.fr_batch_set_batched(self.handle, int(bool(on)))
+        if rc != FR_OK:
+            raise FrError(rc, lib.fr_batch_last_error(self.handle).decode())
+
+    def cycle_kernels(self) -> int:
+        """Kernel nodes of the largest captured GMRES-cycle graph."""
+        n = ctypes.c_longlong()
+        lib.fr_batch_cycle_kernels(self.handle, ctypes.byref(n))
+        return int(n.value)
 
     def step_row(self, scheme: int, dt: float, Us, stream=None, allow=(FR_ERR_NOT_CONVERGED,)):
         ptrs = self._states(Us)

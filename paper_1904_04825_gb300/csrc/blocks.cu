@@ -395,10 +395,10 @@ struct ApplyLayout {
 // A wait that gives up sets *kerr, waits (bounded) for the copies it issued
 // and leaves.
 template <int NB, typename S, typename A>
-__global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
-    k_apply(const S* __restrict__ Minv, double* r, const double* scale, double* __restrict__ z, long long ne,
-            double* sumsq, Reduce red, const int* done, EpsArgs ea, int* kerr, unsigned polls,
-            int skip_first_copy) {
+__device__ __forceinline__ void apply_body(const S* __restrict__ Minv, double* r, const double* scale,
+                                           double* __restrict__ z, long long ne, double* sumsq, const Reduce& red,
+                                           const int* done, const EpsArgs& ea, int* kerr, unsigned polls,
+                                           int skip_first_copy, int bid, int nblk) {
   using L = ApplyLayout<NB, S, A>;
   constexpr int KS = L::KS, NS = L::NS, KP = NB / KS;
   extern __shared__ __align__(128) double smem_d[];
@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sh + 32);
   if (done && *done) return;
   const int tid = threadIdx.x, i = tid % NB, ks = tid / NB;  // ks == KS: padding thread
-  const long long G = gridDim.x;
-  const long long nloc = ne > (long long)blockIdx.x ? (ne - 1 - blockIdx.x) / G + 1 : 0;
+  const long long G = nblk;
+  const long long nloc = ne > (long long)bid ? (ne - 1 - bid) / G + 1 : 0;
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   auto issue = [&](long long t) {
     // test hook: CTA 0 leaves its first element's copies unissued, so its
     // bounded wait for them runs out
-    if (skip_first_copy && blockIdx.x == 0 && t == 0) return;
+    if (skip_first_copy && bid == 0 && t == 0) return;
     const int q = (int)(t % NS);
-    const long long e = blockIdx.x + t * G;
+    const long long e = bid + t * G;
     unsigned char* st = smem + (size_t)q * L::STAGE;
     mbar_arrive_expect_tx(&bar[q], L::MB + L::RB);
     bulk_g2s(st, Minv + e * NB * NB, L::MB, &bar[q]);
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
     const int q = (int)(t % NS);
     const bool ok = mbar_wait(&bar[q], (unsigned)((t / NS) & 1), polls);
     if (!__syncthreads_and(ok)) break;
-    const long long e = blockIdx.x + t * G;
+    const long long e = bid + t * G;
     const S* Ms = reinterpret_cast<const S*>(smem + (size_t)q * L::STAGE);
     const double* rsrc = reinterpret_cast<const double*>(smem + (size_t)q * L::STAGE + L::MB);
     if (ks == 0) {
@@ -477,12 +477,55 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
   }
   if (sumsq) {  // every CTA takes part, so the reduction's counter stays consistent
     const double bs = block_sum(ss, sh);
-    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-    if (last_block(red.counter)) {
-      finish_sums(red, 1, sumsq);
+    if (threadIdx.x == 0) red.partials[(size_t)bid * kMaxVec] = bs;
+    if (last_block(red.counter, nblk)) {
+      finish_sums(red, 1, sumsq, nblk);
       if (threadIdx.x == 0) write_eps(ea, *sumsq);
     }
   }
+}
+
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
+    k_apply(const S* __restrict__ Minv, double* r, const double* scale, double* __restrict__ z, long long ne,
+            double* sumsq, Reduce red, const int* done, EpsArgs ea, int* kerr, unsigned polls,
+            int skip_first_copy) {
+  apply_body<NB, S, A>(Minv, r, scale, z, ne, sumsq, red, done, ea, kerr, polls, skip_first_copy, blockIdx.x,
+                       gridDim.x);
+}
+
+}  // namespace
+
+// Per-instance arguments of the batched apply (Arnoldi iteration j: r = V_j,
+// scale = 1/||v_j|| = invh[j]).
+struct BatchApply {
+  const void* Minv;
+  double* V;
+  long long n;
+  const double* invh;
+  double* z;
+  long long ne;
+  double* sumsq;
+  Reduce red;
+  const int* done;
+  EpsArgs ea;
+  int* kerr;
+  unsigned polls;
+  int skip;
+};
+
+namespace {
+
+// z = M^-1 v_j of every instance (of one block size) in one grid; instance k
+// owns blocks [start[k], start[k+1]), the partition of its own launch.
+template <int NB, typename S, typename A>
+__global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
+    kb_apply(const BatchApply* __restrict__ tab, const int* __restrict__ start, int ninst, int j) {
+  const int k = batch_instance(start, ninst, blockIdx.x);
+  const BatchApply& t = tab[k];
+  const int bid = blockIdx.x - start[k], nblk = start[k + 1] - start[k];
+  apply_body<NB, S, A>(reinterpret_cast<const S*>(t.Minv), t.V + (size_t)j * t.n, t.invh + j, t.z, t.ne, t.sumsq,
+                       t.red, t.done, t.ea, t.kerr, t.polls, t.skip, bid, nblk);
 }
 
 // z_e = M_e^-1 (s r_e) for blocks whose rows are not 16-byte multiples (3D
@@ -641,6 +684,27 @@ unsigned apply_grid(long long ne) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// persistent grid of the staged apply: resident CTAs per SM x SMs, at most
+// one CTA per element (the function attributes are set once per process)
+template <int NB, typename S, typename A>
+int apply_grid_nbs(fr_ctx* ctx, long long* grid_out) {
+  using L = ApplyLayout<NB, S, A>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    FRK_CUDA(ctx, cudaFuncSetAttribute(k_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    FRK_CUDA(ctx, cudaFuncSetAttribute(kb_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    int occ = 0;
+    FRK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<NB, S, A>, L::THREADS, L::BYTES));
+    per_sm = occ > 0 ? occ : 1;
+  }
+  long long grid = (long long)per_sm * ctx->num_sms;
+  if (grid > ctx->ne) grid = ctx->ne;
+  if (grid > kRedBlocks) grid = kRedBlocks;
+  if (grid < 1) grid = 1;
+  *grid_out = grid;
+  return FR_OK;
+}
+
 template <int NB, typename S, typename A>
 int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* sumsq,
               const int* done, cudaStream_t s, bool with_eps) {
@@ -657,17 +721,8 @@ int apply_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, double* su
   // the staged apply copies r with the bulk-copy engine: 16-byte aligned rows
   if (reinterpret_cast<uintptr_t>(r) % 16 != 0)
     return set_error(ctx, FR_ERR_INVALID_ARG, "ejacobi_apply: r must be 16-byte aligned");
-  static int per_sm = 0;  // resident CTAs per SM (function attribute set once per process)
-  if (per_sm == 0) {
-    FRK_CUDA(ctx, cudaFuncSetAttribute(k_apply<NB, S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
-    int occ = 0;
-    FRK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<NB, S, A>, L::THREADS, L::BYTES));
-    per_sm = occ > 0 ? occ : 1;
-  }
-  long long grid = (long long)per_sm * ctx->num_sms;
-  if (grid > ctx->ne) grid = ctx->ne;
-  if (grid > kRedBlocks) grid = kRedBlocks;
-  if (grid < 1) grid = 1;
+  long long grid = 0;
+  FRK_TRY((apply_grid_nbs<NB, S, A>(ctx, &grid)));
   { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf); k_apply<NB, S, A><<<(unsigned)grid, L::THREADS, L::BYTES, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
                                                                   sumsq, ctx->red, done, eps_args(ctx, with_eps), ctx->kerr,
                                                                   ctx->wait_polls, ctx->test_skip_copy); }
@@ -835,6 +890,62 @@ int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
     case 144: return solupdate_nb<144>(ctx, x, s);
     case 196: return solupdate_nb<196>(ctx, x, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
+  }
+}
+
+}  // namespace frk
+
+namespace frk {
+
+size_t batch_apply_bytes() { return sizeof(BatchApply); }
+
+unsigned apply_grid_of(fr_ctx* ctx) {
+  long long g = 1;
+  int rc = FR_OK;
+  const int prec = ctx->opts.block_precision;
+  switch (ctx->nb) {
+    case 36: rc = prec == 1 ? apply_grid_nbs<36, float, float>(ctx, &g) : prec == 2 ? apply_grid_nbs<36, __nv_bfloat16, float>(ctx, &g) : apply_grid_nbs<36, double, double>(ctx, &g); break;
+    case 64: rc = prec == 1 ? apply_grid_nbs<64, float, float>(ctx, &g) : prec == 2 ? apply_grid_nbs<64, __nv_bfloat16, float>(ctx, &g) : apply_grid_nbs<64, double, double>(ctx, &g); break;
+    case 100: rc = prec == 1 ? apply_grid_nbs<100, float, float>(ctx, &g) : prec == 2 ? apply_grid_nbs<100, __nv_bfloat16, float>(ctx, &g) : apply_grid_nbs<100, double, double>(ctx, &g); break;
+    default: return 0;
+  }
+  return rc == FR_OK ? (unsigned)g : 0u;
+}
+
+int fill_batch_apply(fr_ctx* ctx, BatchApply* t) {
+  t->Minv = ctx->blocks;
+  t->V = ctx->V;
+  t->n = ctx->ndof;
+  t->invh = ctx->gd.invh;
+  t->z = ctx->z;
+  t->ne = ctx->ne;
+  t->sumsq = ctx->scal + S_NZ2;
+  t->red = ctx->red;
+  t->done = ctx->gd.done;
+  t->ea = eps_args(ctx, true);
+  t->kerr = ctx->kerr;
+  t->polls = ctx->wait_polls;
+  t->skip = ctx->test_skip_copy;
+  return FR_OK;
+}
+
+namespace {
+template <int NB, typename S, typename A>
+int batch_apply_nbs(const BatchApply* tab, const int* start, int ninst, int nblocks, int j, cudaStream_t s) {
+  using L = ApplyLayout<NB, S, A>;
+  count_launch();
+  kb_apply<NB, S, A><<<nblocks, L::THREADS, L::BYTES, s>>>(tab, start, ninst, j);
+  return cudaGetLastError() == cudaSuccess ? FR_OK : FR_ERR_CUDA;
+}
+}  // namespace
+
+int launch_batch_apply(int nb, int prec, const BatchApply* tab, const int* start, int ninst, int nblocks, int j,
+                       cudaStream_t s) {
+  switch (nb) {
+    case 36: return prec == 1 ? batch_apply_nbs<36, float, float>(tab, start, ninst, nblocks, j, s) : prec == 2 ? batch_apply_nbs<36, __nv_bfloat16, float>(tab, start, ninst, nblocks, j, s) : batch_apply_nbs<36, double, double>(tab, start, ninst, nblocks, j, s);
+    case 64: return prec == 1 ? batch_apply_nbs<64, float, float>(tab, start, ninst, nblocks, j, s) : prec == 2 ? batch_apply_nbs<64, __nv_bfloat16, float>(tab, start, ninst, nblocks, j, s) : batch_apply_nbs<64, double, double>(tab, start, ninst, nblocks, j, s);
+    case 100: return prec == 1 ? batch_apply_nbs<100, float, float>(tab, start, ninst, nblocks, j, s) : prec == 2 ? batch_apply_nbs<100, __nv_bfloat16, float>(tab, start, ninst, nblocks, j, s) : batch_apply_nbs<100, double, double>(tab, start, ninst, nblocks, j, s);
+    default: return FR_ERR_UNSUPPORTED;
   }
 }
 

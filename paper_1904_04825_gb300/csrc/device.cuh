@@ -68,26 +68,29 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Called by every thread of every block after thread 0 wrote its partials.
-// Returns true in the last block to arrive.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
+// Returns true in the last of the nblk blocks of the reduction to arrive
+// (nblk < 0: the whole grid).
+__device__ __forceinline__ bool last_block(unsigned* counter, int nblk = -1) {
   __shared__ bool am_last;
+  const unsigned nb = nblk < 0 ? gridDim.x : (unsigned)nblk;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == nb - 1);
   }
   __syncthreads();
   return am_last;
 }
 
 // In the last block: out[i] = sum over blocks b (fixed order) of partials[b][i],
-// i < nvec.  Each warp sums one value with its lanes striding over the blocks
-// through four independent accumulators.  Resets the counter.
-__device__ __forceinline__ void finish_sums(const Reduce& red, int nvec, double* out) {
+// i < nvec, over the nblk blocks of the reduction (nblk < 0: the whole grid).
+// Each warp sums one value with its lanes striding over the blocks through
+// four independent accumulators.  Resets the counter.
+__device__ __forceinline__ void finish_sums(const Reduce& red, int nvec, double* out, int nblk = -1) {
   __threadfence();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int G = (int)gridDim.x;
+  const int G = nblk < 0 ? (int)gridDim.x : nblk;
   for (int i = wid; i < nvec; i += nw) {
     const double* p = red.partials + i;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -103,6 +106,18 @@ __device__ __forceinline__ void finish_sums(const Reduce& red, int nvec, double*
     if (lane == 0) out[i] = s;
   }
   if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// Batched launches: the CTAs of all instances in one grid; instance k owns
+// blocks [start[k], start[k+1]).  Returns k for block b (binary search).
+__device__ __forceinline__ int batch_instance(const int* __restrict__ start, int ninst, int b) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // eps and 1/eps of the FD product from the finished ||z||^2 (one thread).

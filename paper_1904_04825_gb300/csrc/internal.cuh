@@ -59,6 +59,17 @@ struct GmresDev {
   int ldh;          // m_max + 1
 };
 
+// Per-instance arguments of the batched Arnoldi-step kernels (the basis of
+// the instance, its GMRES state, its reduction scratch and ||w||^2 slot).
+struct BatchKrylov {
+  double* V;        // basis, ldv = n
+  long long n;
+  GmresDev gd;
+  Reduce red;
+  double* nw2;      // ||w||^2 of the current Arnoldi vector
+  double eta2;      // second Gram-Schmidt pass when ||w_new||^2 < eta2 ||w_old||^2
+};
+
 // Device scalars (sums of squares) used by the FD step and GMRES.
 enum Scal { S_NU2 = 0, S_NZ2, S_NW2, S_NB2, S_NR2, S_NF2, S_NX2, S_EPS, S_IEPS, S_GB2, S_GU2, S_GR1, S_GR2, S_ST0, S_ST1, S_ST2, S_ST3, S_COUNT };  // S_ST*: one GMRES cycle status
 
@@ -238,6 +249,30 @@ int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, con
 // tolerance; a cycle that finds it set does no work (for replayed graphs).
 int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
                         double* x, int m, double rtol, double* status, int* fin, cudaStream_t s);
+// the cycle's parts (batches enqueue the Arnoldi iterations of all instances
+// as batched launches between them)
+int gmres_cycle_prologue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                         double* x, int m, double rtol, int* fin, cudaStream_t s);
+int gmres_cycle_epilogue(fr_ctx* ctx, double* x, double* status, int* fin, cudaStream_t s);
+// batched Arnoldi-step kernels (krylov.cu, blocks.cu, residual.cu); the
+// instance tables and CTA partitions are device arrays
+BatchKrylov batch_krylov_args(fr_ctx* ctx);
+unsigned vec_grid_of(const fr_ctx* ctx);
+int launch_batch_gs_givens(const BatchKrylov* tab, const int* start, int ninst, int nblocks, int j, cudaStream_t s);
+// apply: the per-instance launch grid of the block apply (blocks.cu) and the
+// batched apply of the instances of one block size nb
+struct BatchApply;
+unsigned apply_grid_of(fr_ctx* ctx);
+int fill_batch_apply(fr_ctx* ctx, BatchApply* out);
+int launch_batch_apply(int nb, int prec, const BatchApply* tab, const int* start, int ninst, int nblocks, int j,
+                       cudaStream_t s);
+size_t batch_apply_bytes();
+// residual: A z of Arnoldi iteration j into V_{j+1} for the instances of one degree
+int fill_batch_residual(fr_ctx* ctx, const double* U, const double* R0, double shift, void* out);
+size_t batch_residual_bytes();
+unsigned residual_grid_of(const fr_ctx* ctx);
+int launch_batch_residual(int p, int riemann, const void* tab, const int* start, int ninst, int nblocks, int j,
+                          cudaStream_t s);
 // tables.cu
 void build_tables(int p, Tables* t);
 // ns.cu (viscous path): mode 0 R, 1 A z, 2 b - A z; block formation + inversion

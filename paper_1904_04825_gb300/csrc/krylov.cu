@@ -65,15 +65,15 @@ __global__ void k_lincomb(double* out, long long len, const Lincomb lc, double* 
 // thread (NC x UR independent accumulation chains hide the FMA latency).
 template <int NC>
 __device__ __forceinline__ void dots_chunk(const double* const* ptr, const double* __restrict__ w,
-                                           long long n, double* acc) {
+                                           long long n, double* acc, int bid, int nblk) {
   constexpr int UR = NC >= 8 ? 1 : (NC >= 4 ? 2 : 4);
   double a[NC][UR];
 #pragma unroll
   for (int i = 0; i < NC; ++i)
 #pragma unroll
     for (int u = 0; u < UR; ++u) a[i][u] = 0.0;
-  const long long S = (long long)gridDim.x * blockDim.x;
-  for (long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
+  const long long S = (long long)nblk * blockDim.x;
+  for (long long r0 = (long long)bid * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
     double wr[UR];
 #pragma unroll
     for (int u = 0; u < UR; ++u) wr[u] = (r0 + u * S < n) ? w[r0 + u * S] : 0.0;
@@ -95,10 +95,10 @@ __device__ __forceinline__ void dots_chunk(const double* const* ptr, const doubl
 // out[i] = <V_i, w> for i < nvec, and out[nvec] = <w, w> when with_self,
 // in chunks of up to 8 values per sweep.  Skipped when the cycle is done or
 // when `gate` points at a zero flag.
-__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long long ldv, int nvec,
-                                              const double* __restrict__ w, long long n, double* out,
-                                              int with_self, Reduce red, const int* done,
-                                              const int* gate) {
+__device__ __forceinline__ void dots_body(const double* __restrict__ V, long long ldv, int nvec,
+                                          const double* __restrict__ w, long long n, double* out,
+                                          int with_self, const Reduce& red, const int* done,
+                                          const int* gate, int bid, int nblk) {
   __shared__ double sred[8][kThreads / 32];
   if ((done && *done) || (gate && !*gate)) return;
   const int total = nvec + (with_self ? 1 : 0);
@@ -113,14 +113,14 @@ __global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long
     }
     double acc[8];
     switch (nc) {
-      case 1: dots_chunk<1>(ptr, w, n, acc); break;
-      case 2: dots_chunk<2>(ptr, w, n, acc); break;
-      case 3: dots_chunk<3>(ptr, w, n, acc); break;
-      case 4: dots_chunk<4>(ptr, w, n, acc); break;
-      case 5: dots_chunk<5>(ptr, w, n, acc); break;
-      case 6: dots_chunk<6>(ptr, w, n, acc); break;
-      case 7: dots_chunk<7>(ptr, w, n, acc); break;
-      default: dots_chunk<8>(ptr, w, n, acc); break;
+      case 1: dots_chunk<1>(ptr, w, n, acc, bid, nblk); break;
+      case 2: dots_chunk<2>(ptr, w, n, acc, bid, nblk); break;
+      case 3: dots_chunk<3>(ptr, w, n, acc, bid, nblk); break;
+      case 4: dots_chunk<4>(ptr, w, n, acc, bid, nblk); break;
+      case 5: dots_chunk<5>(ptr, w, n, acc, bid, nblk); break;
+      case 6: dots_chunk<6>(ptr, w, n, acc, bid, nblk); break;
+      case 7: dots_chunk<7>(ptr, w, n, acc, bid, nblk); break;
+      default: dots_chunk<8>(ptr, w, n, acc, bid, nblk); break;
     }
     // Warp sums of the (up to) 8 values by recursive halving: each exchange
     // sends half of the values still held to the partner lane and keeps the
@@ -155,11 +155,18 @@ __global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long
     if ((int)threadIdx.x < nc) {
       double t = 0.0;
       for (int q = 0; q < nw; ++q) t += sred[threadIdx.x][q];
-      red.partials[(size_t)blockIdx.x * kMaxVec + c0 + threadIdx.x] = t;
+      red.partials[(size_t)bid * kMaxVec + c0 + threadIdx.x] = t;
     }
     __syncthreads();
   }
-  if (last_block(red.counter)) finish_sums(red, total, out);
+  if (last_block(red.counter, nblk)) finish_sums(red, total, out, nblk);
+}
+
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ V, long long ldv, int nvec,
+                                              const double* __restrict__ w, long long n, double* out,
+                                              int with_self, Reduce red, const int* done,
+                                              const int* gate) {
+  dots_body(V, ldv, nvec, w, n, out, with_self, red, done, gate, blockIdx.x, gridDim.x);
 }
 
 // w -= sum_i h_i V_i as one FMA chain per row (exactly nvec FP64 FMAs); optional sum of
@@ -176,10 +183,11 @@ struct Reorth {
   double* h2;
 };
 
-__global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const double* __restrict__ V,
-                                                long long ldv, int nvec, const double* h,
-                                                long long n, double* sumsq, Reduce red,
-                                                const int* done, const int* gate, Reorth ro) {
+__device__ __forceinline__ void update_body(double* __restrict__ w, const double* __restrict__ V,
+                                            long long ldv, int nvec, const double* h,
+                                            long long n, double* sumsq, const Reduce& red,
+                                            const int* done, const int* gate, const Reorth& ro,
+                                            int bid, int nblk) {
   __shared__ double sh[32];
   __shared__ double hs[kMaxVec];
   if ((done && *done) || (gate && !*gate)) return;
@@ -188,8 +196,8 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
   // four rows per thread in flight: four independent FMA chains of length nvec
   constexpr int UR = 4;
   double ss[UR] = {0.0, 0.0, 0.0, 0.0};
-  const long long S = (long long)gridDim.x * blockDim.x;
-  for (long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
+  const long long S = (long long)nblk * blockDim.x;
+  for (long long r0 = (long long)bid * blockDim.x + threadIdx.x; r0 < n; r0 += UR * S) {
     double v[UR];
 #pragma unroll
     for (int u = 0; u < UR; ++u) v[u] = (r0 + u * S < n) ? w[r0 + u * S] : 0.0;
@@ -210,9 +218,9 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
   }
   if (sumsq) {
     const double bs = block_sum((ss[0] + ss[1]) + (ss[2] + ss[3]), sh);
-    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
-    if (last_block(red.counter)) {
-      finish_sums(red, 1, sumsq);
+    if (threadIdx.x == 0) red.partials[(size_t)bid * kMaxVec] = bs;
+    if (last_block(red.counter, nblk)) {
+      finish_sums(red, 1, sumsq, nblk);
       if (ro.self2 && threadIdx.x == 0) {
         const int need = (*sumsq < ro.eta2 * *ro.self2) ? 1 : 0;
         *ro.rflag = need;
@@ -221,6 +229,13 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const do
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ w, const double* __restrict__ V,
+                                                long long ldv, int nvec, const double* h,
+                                                long long n, double* sumsq, Reduce red,
+                                                const int* done, const int* gate, Reorth ro) {
+  update_body(w, V, ldv, nvec, h, n, sumsq, red, done, gate, ro, blockIdx.x, gridDim.x);
 }
 
 // start of a cycle: beta = ||r||, g = beta e_1, done if beta <= rtol ||b||
@@ -245,8 +260,7 @@ __global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, 
 }
 
 // Hessenberg column j, Givens rotations, residual estimate, convergence
-__global__ void k_givens(GmresDev gd, int j, const double* nw2) {
-  if (threadIdx.x != 0) return;
+__device__ __forceinline__ void givens_body(const GmresDev& gd, int j, const double* nw2) {
   if (*gd.done) return;
   double* Hj = gd.H + (size_t)j * gd.ldh;
   for (int i = 0; i <= j; ++i) Hj[i] = gd.h1[i] + gd.h2[i];
@@ -271,6 +285,11 @@ __global__ void k_givens(GmresDev gd, int j, const double* nw2) {
   *gd.res = res;
   gd.invh[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
   if (res <= *gd.target || hn == 0.0 || !(res == res)) *gd.done = 1;
+}
+
+__global__ void k_givens(GmresDev gd, int j, const double* nw2) {
+  if (threadIdx.x != 0) return;
+  givens_body(gd, j, nw2);
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k)
@@ -317,7 +336,64 @@ __global__ void k_fill(double* dst, double v, long long n) {
     dst[i] = v;
 }
 
+// ---- batched Arnoldi-step kernels: the CTAs of every instance in one grid,
+// instance k owning blocks [start[k], start[k+1]) (the same partition as its
+// single-instance launch, so every reduction sums in the same order) ----
+__global__ void __launch_bounds__(256) kb_dots(const BatchKrylov* __restrict__ tab, const int* __restrict__ start,
+                                               int ninst, int j, int second) {
+  const int k = batch_instance(start, ninst, blockIdx.x);
+  const BatchKrylov& t = tab[k];
+  const int bid = blockIdx.x - start[k], nblk = start[k + 1] - start[k];
+  const long long n = t.n;
+  dots_body(t.V, n, j + 1, t.V + (size_t)(j + 1) * n, n, second ? t.gd.h2 : t.gd.h1, second ? 0 : 1, t.red,
+            t.gd.done, second ? t.gd.rflag + j : nullptr, bid, nblk);
+}
+
+__global__ void __launch_bounds__(256) kb_update(const BatchKrylov* __restrict__ tab, const int* __restrict__ start,
+                                                 int ninst, int j, int second) {
+  const int k = batch_instance(start, ninst, blockIdx.x);
+  const BatchKrylov& t = tab[k];
+  const int bid = blockIdx.x - start[k], nblk = start[k + 1] - start[k];
+  const long long n = t.n;
+  const Reorth none{nullptr, 0.0, nullptr, nullptr};
+  const Reorth first{t.gd.h1 + (j + 1), t.eta2, t.gd.rflag + j, t.gd.h2};
+  update_body(t.V + (size_t)(j + 1) * n, t.V, n, j + 1, second ? t.gd.h2 : t.gd.h1, n, t.nw2, t.red, t.gd.done,
+              second ? t.gd.rflag + j : nullptr, second ? none : first, bid, nblk);
+}
+
+__global__ void kb_givens(const BatchKrylov* __restrict__ tab, int j) {
+  if (threadIdx.x != 0) return;
+  const BatchKrylov& t = tab[blockIdx.x];
+  givens_body(t.gd, j, t.nw2);
+}
+
 }  // namespace
+
+BatchKrylov batch_krylov_args(fr_ctx* ctx) {
+  BatchKrylov t;
+  t.V = ctx->V;
+  t.n = ctx->ndof;
+  t.gd = ctx->gd;
+  t.red = ctx->red;
+  t.nw2 = ctx->scal + S_NW2;
+  t.eta2 = ctx->opts.reorth_eta * ctx->opts.reorth_eta;
+  return t;
+}
+
+unsigned vec_grid_of(const fr_ctx* ctx) { return vgrid(ctx, ctx->ndof); }
+
+// The Gram-Schmidt passes and the Givens step of Arnoldi iteration j of every
+// instance of a batch: tab / start describe the instances (device arrays),
+// nblocks = start[ninst].
+int launch_batch_gs_givens(const BatchKrylov* tab, const int* start, int ninst, int nblocks, int j, cudaStream_t s) {
+  count_launches(5);
+  kb_dots<<<nblocks, kThreads, 0, s>>>(tab, start, ninst, j, 0);
+  kb_update<<<nblocks, kThreads, 0, s>>>(tab, start, ninst, j, 0);
+  kb_dots<<<nblocks, kThreads, 0, s>>>(tab, start, ninst, j, 1);
+  kb_update<<<nblocks, kThreads, 0, s>>>(tab, start, ninst, j, 1);
+  kb_givens<<<ninst, 32, 0, s>>>(tab, j);
+  return cudaGetLastError() == cudaSuccess ? FR_OK : FR_ERR_CUDA;
+}
 
 EpsArgs eps_args(fr_ctx* ctx, bool on) {
   EpsArgs ea{ctx->scal + S_NU2, ctx->opts.eps_rel, ctx->opts.eps_fixed, on ? ctx->scal + S_EPS : nullptr};
@@ -359,21 +435,40 @@ int launch_fill(fr_ctx* ctx, double* dst, double v, cudaStream_t s) {
 // One whole GMRES cycle enqueued without any host synchronisation (for CUDA
 // graph capture): r = b - A x (exactly b for x = 0), m Arnoldi iterations
 // that stop on the device, the solution update, and the status
-// [k, |g_k|, target, ||b||] written to status (device, 4 doubles).
+// [k, |g_k|, target, ||b||] written to status (device, 4 doubles).  The three
+// parts are also enqueued separately by batches, whose Arnoldi iterations
+// run as batched launches over all instances.
+int gmres_cycle_prologue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
+                         double* x, int m, double rtol, int* fin, cudaStream_t s) {
+  double* sc = ctx->scal;
+  FRK_TRY(launch_linearize(ctx, U, s));
+  FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
+  FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
+  FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
+  FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, ctx->V, shift, sc + S_EPS, fin, s));
+  FRK_TRY(launch_sumsq(ctx, ctx->V, sc + S_NR2, s));
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(ctx->gd, sc + S_NR2, sc + S_NB2, rtol, m, fin); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+int gmres_cycle_epilogue(fr_ctx* ctx, double* x, double* status, int* fin, cudaStream_t s) {
+  GmresDev& gd = ctx->gd;
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
+  FRK_LAUNCHED(ctx);
+  FRK_TRY(launch_solution_update(ctx, x, s));
+  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, ctx->scal + S_NB2, status, fin, ctx->kerr); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
 int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,
                         double* x, int m, double rtol, double* status, int* fin, cudaStream_t s) {
   const long long n = ctx->ndof;
   double* sc = ctx->scal;
   GmresDev& gd = ctx->gd;
   double* V = ctx->V;
-  FRK_TRY(launch_linearize(ctx, U, s));
-  FRK_TRY(launch_sumsq(ctx, U, sc + S_NU2, s));
-  FRK_TRY(launch_sumsq(ctx, b, sc + S_NB2, s));
-  FRK_TRY(launch_sumsq(ctx, x, sc + S_NZ2, s, true));
-  FRK_TRY(launch_residual(ctx, 2, U, x, R0, b, V, shift, sc + S_EPS, fin, s));
-  FRK_TRY(launch_sumsq(ctx, V, sc + S_NR2, s));
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_cycle_init<<<1, 32, 0, s>>>(gd, sc + S_NR2, sc + S_NB2, rtol, m, fin); }
-  FRK_LAUNCHED(ctx);
+  FRK_TRY(gmres_cycle_prologue(ctx, U, R0, shift, b, x, m, rtol, fin, s));
   for (int j = 0; j < m; ++j) {
     double* vj = V + (size_t)j * n;
     double* w = V + (size_t)(j + 1) * n;
@@ -388,12 +483,7 @@ int gmres_cycle_enqueue(fr_ctx* ctx, const double* U, const double* R0, double s
     { ProfScope ps_(ctx, FR_KF_OTHER, s); k_givens<<<1, 32, 0, s>>>(gd, j, sc + S_NW2); }
     FRK_LAUNCHED(ctx);
   }
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_backsub<<<1, 32, 0, s>>>(gd); }
-  FRK_LAUNCHED(ctx);
-  FRK_TRY(launch_solution_update(ctx, x, s));
-  { ProfScope ps_(ctx, FR_KF_OTHER, s); k_status<<<1, 32, 0, s>>>(gd, sc + S_NB2, status, fin, ctx->kerr); }
-  FRK_LAUNCHED(ctx);
-  return FR_OK;
+  return gmres_cycle_epilogue(ctx, x, status, fin, s);
 }
 
 int gmres_impl(fr_ctx* ctx, const double* U, const double* R0, double shift, const double* b,

@@ -77,7 +77,7 @@ template <> struct Tile<6, 0> { static constexpr int TX = 2, TY = 2; };
 template <> struct Tile<6, 1> { static constexpr int TX = 5, TY = 1; };
 
 template <int P, int MODE, int TV, int RM>
-__global__ void __launch_bounds__(256, 4) k_residual(const ResArgs a) {
+__device__ __forceinline__ void residual_body(const ResArgs& a, double* __restrict__ out, int bid) {
   constexpr int N = P + 1, NP = N * N;
   constexpr int TX = Tile<P, TV>::TX, TY = Tile<P, TV>::TY, NE = TX * TY;
   constexpr int NXF = (TX + 1) * TY * N;  // points on the tile's x-faces (normal +x)
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256, 4) k_residual(const ResArgs a) {
   }
 
   const int tiles_x = (a.nx + TX - 1) / TX;
-  const int ix0 = (int)(blockIdx.x % tiles_x) * TX, iy0 = (int)(blockIdx.x / tiles_x) * TY;
+  const int ix0 = (int)(bid % tiles_x) * TX, iy0 = (int)(bid / tiles_x) * TY;
   const int ax = min(TX, a.nx - ix0), ay = min(TY, a.ny - iy0);  // active tile extent
   const int el = threadIdx.x / NP, t = threadIdx.x % NP;
   const int lx = el % TX, ly = el / TX;
@@ -257,13 +257,30 @@ __global__ void __launch_bounds__(256, 4) k_residual(const ResArgs a) {
     const double R = -fma(sx, dF, sy * dG);
     const long long o = base + v * NP;
     if (MODE == 0) {
-      a.out[o] = R;
+      out[o] = R;
     } else {
       const double zo = a.z[o];
       const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
-      a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
+      out[o] = MODE == 2 ? a.b[o] - Az : Az;
     }
   }
+}
+
+template <int P, int MODE, int TV, int RM>
+__global__ void __launch_bounds__(256, 4) k_residual(const ResArgs a) {
+  residual_body<P, MODE, TV, RM>(a, a.out, blockIdx.x);
+}
+
+// A z of Arnoldi iteration j of every instance (of one degree) in one grid:
+// instance k owns the tiles [start[k], start[k+1]); its table entry holds
+// the basis in `out`, and A z is written to V_{j+1}.
+template <int P, int RM>
+__global__ void __launch_bounds__(256, 4) kb_residual(const ResArgs* __restrict__ tab, const int* __restrict__ start,
+                                                      int ninst, int j) {
+  const int k = batch_instance(start, ninst, blockIdx.x);
+  const ResArgs& a = tab[k];
+  const long long ndof = a.ne * 4 * (P + 1) * (P + 1);
+  residual_body<P, 1, 0, RM>(a, a.out + (size_t)(j + 1) * ndof, blockIdx.x - start[k]);
 }
 
 // A z with FP32 linear parts (jv_precision 1).  R(U+eps z) - R(U) is the
@@ -505,6 +522,53 @@ int launch_residual(fr_ctx* ctx, int mode, const double* U, const double* z, con
     case 6: return launch_p<6>(ctx, mode, a, s);
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "degree %d not compiled", ctx->p);
   }
+}
+
+size_t batch_residual_bytes() { return sizeof(ResArgs); }
+
+// tiles of the residual launch (tile variant 0, the one the batched launch uses)
+unsigned residual_grid_of(const fr_ctx* ctx) {
+  int tx = 1, ty = 1;
+  switch (ctx->p) {
+    case 2: tx = Tile<2, 0>::TX; ty = Tile<2, 0>::TY; break;
+    case 3: tx = Tile<3, 0>::TX; ty = Tile<3, 0>::TY; break;
+    case 4: tx = Tile<4, 0>::TX; ty = Tile<4, 0>::TY; break;
+    default: return 0;
+  }
+  return (unsigned)(((ctx->nx + tx - 1) / tx) * ((ctx->ny + ty - 1) / ty));
+}
+
+// table entry of the batched A z: A = shift I - dR/dU at U, z = the
+// context's preconditioned vector, output base = the Krylov basis
+int fill_batch_residual(fr_ctx* ctx, const double* U, const double* R0, double shift, void* out) {
+  if (ctx->dim3 || ctx->viscous || ctx->opts.jv_precision != 0 || ctx->p < 2 || ctx->p > 4) return FR_ERR_UNSUPPORTED;
+  ResArgs a{};
+  a.U = U; a.z = ctx->z; a.R0 = R0; a.b = nullptr; a.out = ctx->V;
+  a.hx = ctx->hx; a.hy = ctx->hy; a.eps2 = ctx->scal + S_EPS; a.done = ctx->gd.done;
+  a.ne = ctx->ne; a.nx = ctx->nx; a.ny = ctx->ny;
+  a.gam = ctx->opts.gamma; a.shift = shift;
+  a.eps_rel = ctx->opts.eps_rel; a.eps_fixed = ctx->opts.eps_fixed;
+  a.lin_fg = ctx->lin_fg; a.lin_fx = ctx->lin_fx; a.lin_fy = ctx->lin_fy;
+  a.riemann = ctx->opts.riemann;
+  a.tab = ctx->tab;
+  *reinterpret_cast<ResArgs*>(out) = a;
+  return FR_OK;
+}
+
+int launch_batch_residual(int p, int riemann, const void* tab, const int* start, int ninst, int nblocks, int j,
+                          cudaStream_t s) {
+  const ResArgs* t = reinterpret_cast<const ResArgs*>(tab);
+  count_launch();
+  switch (p) {
+    case 2: riemann ? kb_residual<2, 1><<<nblocks, Tile<2, 0>::TX * Tile<2, 0>::TY * 9, 0, s>>>(t, start, ninst, j)
+                    : kb_residual<2, 0><<<nblocks, Tile<2, 0>::TX * Tile<2, 0>::TY * 9, 0, s>>>(t, start, ninst, j); break;
+    case 3: riemann ? kb_residual<3, 1><<<nblocks, Tile<3, 0>::TX * Tile<3, 0>::TY * 16, 0, s>>>(t, start, ninst, j)
+                    : kb_residual<3, 0><<<nblocks, Tile<3, 0>::TX * Tile<3, 0>::TY * 16, 0, s>>>(t, start, ninst, j); break;
+    case 4: riemann ? kb_residual<4, 1><<<nblocks, Tile<4, 0>::TX * Tile<4, 0>::TY * 25, 0, s>>>(t, start, ninst, j)
+                    : kb_residual<4, 0><<<nblocks, Tile<4, 0>::TX * Tile<4, 0>::TY * 25, 0, s>>>(t, start, ninst, j); break;
+    default: return FR_ERR_UNSUPPORTED;
+  }
+  return cudaGetLastError() == cudaSuccess ? FR_OK : FR_ERR_CUDA;
 }
 
 int launch_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {

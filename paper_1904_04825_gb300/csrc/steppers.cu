@@ -515,6 +515,12 @@ struct fr_batch {
   int* fin_dev = nullptr;         // [count] stage solve finished (reset per stage)
   cudaGraphExec_t exec[6] = {};
   long long nodes[6] = {};
+  // batched Arnoldi iterations: instance tables and CTA partitions (device),
+  // one group per degree 2..4 for the apply and the FD operator
+  unsigned char* tab_dev = nullptr;
+  size_t tab_bytes = 0;
+  int batched = 0;          // 1: the cycles use the batched launches
+  int use_batched = 1;      // set to 0 to capture per-instance cycles
   std::vector<const double*> keyU;
   std::vector<int> keyCfg;  // vec_blocks, tile_variant of every instance
   double key_dt = 0.0;
@@ -556,6 +562,7 @@ void free_batch(fr_batch* B) {
   if (B->main) cudaStreamDestroy(B->main);
   cudaFree(B->status_dev);
   cudaFree(B->fin_dev);
+  cudaFree(B->tab_dev);
   cudaFreeHost(B->status_host);
   delete B;
 }
@@ -574,6 +581,92 @@ int join_all(fr_batch* B) {
   return FR_OK;
 }
 
+// Layout of the batched-iteration tables in tab_dev (host mirror in tab):
+// [BatchKrylov x K][vec starts K+1] then per degree g = 2, 3, 4:
+// [BatchApply x n_g][apply starts n_g+1][ResArgs x n_g][tile starts n_g+1].
+struct BatchPlan {
+  size_t off_kry = 0, off_vstart = 0;
+  size_t off_app[3] = {}, off_astart[3] = {}, off_res[3] = {}, off_rstart[3] = {};
+  int n[3] = {}, nb[3] = {};
+  int app_blocks[3] = {}, res_blocks[3] = {}, vec_blocks = 0;
+  size_t bytes = 0;
+};
+
+size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// whether every instance can take the batched Arnoldi launches: 2D Euler,
+// degree 2..4, element-Jacobi on, the FP64 FD operator
+bool batchable(const fr_batch* B) {
+  for (const fr_ctx* c : B->m)
+    if (c->dim3 || c->viscous || c->p < 2 || c->p > 4 || !c->opts.precond || c->opts.jv_precision != 0)
+      return false;
+  return true;
+}
+
+BatchPlan plan_of(const fr_batch* B) {
+  BatchPlan P;
+  const int K = (int)B->m.size();
+  for (const fr_ctx* c : B->m) P.n[c->p - 2] += 1;
+  size_t o = 0;
+  P.off_kry = o; o = align16(o + (size_t)K * sizeof(BatchKrylov));
+  P.off_vstart = o; o = align16(o + (size_t)(K + 1) * sizeof(int));
+  for (int g = 0; g < 3; ++g) {
+    P.nb[g] = 4 * (g + 3) * (g + 3);
+    P.off_app[g] = o; o = align16(o + (size_t)P.n[g] * batch_apply_bytes());
+    P.off_astart[g] = o; o = align16(o + (size_t)(P.n[g] + 1) * sizeof(int));
+    P.off_res[g] = o; o = align16(o + (size_t)P.n[g] * batch_residual_bytes());
+    P.off_rstart[g] = o; o = align16(o + (size_t)(P.n[g] + 1) * sizeof(int));
+  }
+  P.bytes = o;
+  return P;
+}
+
+// fill the tables for A = shift I - dR/dU at the states U (host mirror, then
+// one copy; called outside graph capture)
+int fill_tables(fr_batch* B, BatchPlan* P, double shift, double* const* U) {
+  const int K = (int)B->m.size();
+  std::vector<unsigned char> h(P->bytes, 0);
+  BatchKrylov* kry = reinterpret_cast<BatchKrylov*>(h.data() + P->off_kry);
+  int* vstart = reinterpret_cast<int*>(h.data() + P->off_vstart);
+  int fill[3] = {0, 0, 0};
+  int acc_a[3] = {0, 0, 0}, acc_r[3] = {0, 0, 0};
+  int accv = 0;
+  for (int k = 0; k < K; ++k) {
+    fr_ctx* c = B->m[k];
+    kry[k] = batch_krylov_args(c);
+    vstart[k] = accv;
+    accv += (int)vec_grid_of(c);
+    const int g = c->p - 2, q = fill[g]++;
+    int* astart = reinterpret_cast<int*>(h.data() + P->off_astart[g]);
+    int* rstart = reinterpret_cast<int*>(h.data() + P->off_rstart[g]);
+    BATCH_TRY(B, k, fill_batch_apply(c, reinterpret_cast<BatchApply*>(h.data() + P->off_app[g] + q * batch_apply_bytes())));
+    BATCH_TRY(B, k, fill_batch_residual(c, U[k], c->buf[B_R0], shift,
+                                        h.data() + P->off_res[g] + q * batch_residual_bytes()));
+    const unsigned ga = apply_grid_of(c), gr = residual_grid_of(c);
+    if (ga == 0 || gr == 0) return batch_err(B, FR_ERR_UNSUPPORTED, "batched launch grid");
+    astart[q] = acc_a[g];
+    acc_a[g] += (int)ga;
+    rstart[q] = acc_r[g];
+    acc_r[g] += (int)gr;
+  }
+  vstart[K] = accv;
+  P->vec_blocks = accv;
+  for (int g = 0; g < 3; ++g) {
+    reinterpret_cast<int*>(h.data() + P->off_astart[g])[P->n[g]] = acc_a[g];
+    reinterpret_cast<int*>(h.data() + P->off_rstart[g])[P->n[g]] = acc_r[g];
+    P->app_blocks[g] = acc_a[g];
+    P->res_blocks[g] = acc_r[g];
+  }
+  if (!B->tab_dev || B->tab_bytes < P->bytes) {
+    cudaFree(B->tab_dev);
+    B->tab_dev = nullptr;
+    BATCH_CUDA(B, cudaMalloc(&B->tab_dev, P->bytes));
+    B->tab_bytes = P->bytes;
+  }
+  BATCH_CUDA(B, cudaMemcpy(B->tab_dev, h.data(), P->bytes, cudaMemcpyHostToDevice));
+  return FR_OK;
+}
+
 // capture the graph of one GMRES cycle of stage i for all instances
 int capture_cycle(fr_batch* B, int i, const RowTab& t, double dt, double* const* U) {
   const double shift = 1.0 / (t.gamma * dt);
@@ -586,14 +679,61 @@ int capture_cycle(fr_batch* B, int i, const RowTab& t, double dt, double* const*
     masks[k] = B->m[k]->prof.mask;
     B->m[k]->prof.mask = 0;
   }
+  // batched Arnoldi iterations when every instance allows them: the tables
+  // are filled before the capture (a plain copy)
+  B->batched = B->use_batched && batchable(B);
+  BatchPlan P;
+  if (B->batched) {
+    P = plan_of(B);
+    FRK_TRY(fill_tables(B, &P, shift, U));
+  }
   BATCH_CUDA(B, cudaStreamBeginCapture(B->main, cudaStreamCaptureModeRelaxed));
   int rc = fork_all(B);
-  for (size_t k = 0; k < B->m.size() && rc == FR_OK; ++k) {
-    fr_ctx* c = B->m[k];
-    const double* b = (i == 0) ? c->buf[B_R0] : (i > 0 ? c->buf[B_RHS] : nullptr);
-    rc = gmres_cycle_enqueue(c, U[k], c->buf[B_R0], shift, b, c->buf[B_Y0 + i], c->opts.gmres_m,
-                             c->opts.tol_lin, B->status_dev + 4 * k, B->fin_dev + k, B->st[k]);
-    if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
+  const int K = (int)B->m.size();
+  if (!B->batched) {
+    for (int k = 0; k < K && rc == FR_OK; ++k) {
+      fr_ctx* c = B->m[k];
+      const double* b = (i == 0) ? c->buf[B_R0] : (i > 0 ? c->buf[B_RHS] : nullptr);
+      rc = gmres_cycle_enqueue(c, U[k], c->buf[B_R0], shift, b, c->buf[B_Y0 + i], c->opts.gmres_m,
+                               c->opts.tol_lin, B->status_dev + 4 * k, B->fin_dev + k, B->st[k]);
+      if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
+    }
+  } else {
+    // per instance: r = b - A x and the cycle set-up; then every Arnoldi
+    // iteration of all instances as batched launches on the main stream
+    // (instances whose cycle is done skip their CTAs' work on the device);
+    // then per instance: back substitution, solution update, status
+    for (int k = 0; k < K && rc == FR_OK; ++k) {
+      fr_ctx* c = B->m[k];
+      const double* b = (i == 0) ? c->buf[B_R0] : (i > 0 ? c->buf[B_RHS] : nullptr);
+      rc = gmres_cycle_prologue(c, U[k], c->buf[B_R0], shift, b, c->buf[B_Y0 + i], c->opts.gmres_m,
+                                c->opts.tol_lin, B->fin_dev + k, B->st[k]);
+      if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
+    }
+    if (rc == FR_OK) rc = join_all(B);
+    const int m = B->m[0]->opts.gmres_m, prec = B->m[0]->opts.block_precision, rm = B->m[0]->opts.riemann;
+    unsigned char* T = B->tab_dev;
+    for (int j = 0; j < m && rc == FR_OK; ++j) {
+      for (int g = 0; g < 3 && rc == FR_OK; ++g)
+        if (P.n[g])
+          rc = launch_batch_apply(P.nb[g], prec, reinterpret_cast<const BatchApply*>(T + P.off_app[g]),
+                                  reinterpret_cast<const int*>(T + P.off_astart[g]), P.n[g], P.app_blocks[g], j,
+                                  B->main);
+      for (int g = 0; g < 3 && rc == FR_OK; ++g)
+        if (P.n[g])
+          rc = launch_batch_residual(g + 2, rm, T + P.off_res[g], reinterpret_cast<const int*>(T + P.off_rstart[g]),
+                                     P.n[g], P.res_blocks[g], j, B->main);
+      if (rc == FR_OK)
+        rc = launch_batch_gs_givens(reinterpret_cast<const BatchKrylov*>(T + P.off_kry),
+                                    reinterpret_cast<const int*>(T + P.off_vstart), K, P.vec_blocks, j, B->main);
+      if (rc != FR_OK) rc = batch_err(B, rc, "batched Arnoldi launch failed");
+    }
+    if (rc == FR_OK) rc = fork_all(B);
+    for (int k = 0; k < K && rc == FR_OK; ++k) {
+      fr_ctx* c = B->m[k];
+      rc = gmres_cycle_epilogue(c, c->buf[B_Y0 + i], B->status_dev + 4 * k, B->fin_dev + k, B->st[k]);
+      if (rc != FR_OK) rc = batch_err(B, rc, fr_last_error(c));
+    }
   }
   if (rc == FR_OK) rc = join_all(B);
   if (rc == FR_OK && cudaMemcpyAsync(B->status_host, B->status_dev, B->m.size() * 4 * sizeof(double),
@@ -669,6 +809,23 @@ extern "C" int fr_batch_destroy(fr_batch* B) {
 }
 
 extern "C" const char* fr_batch_last_error(const fr_batch* B) { return B ? B->err : "invalid batch"; }
+
+extern "C" int fr_batch_set_batched(fr_batch* B, int on) {
+  if (!B || on < 0 || on > 1) return FR_ERR_INVALID_ARG;
+  if (B->use_batched != on) {
+    B->use_batched = on;
+    for (auto& e : B->exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  }
+  return FR_OK;
+}
+
+extern "C" int fr_batch_cycle_kernels(const fr_batch* B, long long* kernels) {
+  if (!B || !kernels) return FR_ERR_INVALID_ARG;
+  *kernels = 0;
+  for (long long n : B->nodes) *kernels = n > *kernels ? n : *kernels;
+  return FR_OK;
+}
 
 extern "C" fr_ctx* fr_batch_member(fr_batch* B, int k) {
   if (!B || k < 0 || k >= (int)B->m.size()) return nullptr;

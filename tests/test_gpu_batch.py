@@ -241,3 +241,33 @@ def test_seeded_batch_instances_run(fr):
     for s, U in zip(st, Ub):
         u = U.cpu().numpy()
         assert s.converged and np.isfinite(u).all() and u[:, 0].min() > 0.0
+
+
+def test_batched_arnoldi_launches_equal_per_instance_cycles(fr):
+    """The batched Arnoldi launches (one grid per kernel over all instances)
+    reproduce the per-instance cycle kernels bit for bit (each instance keeps
+    its own CTA partition, so every reduction sums in the same order), with
+    far fewer kernel nodes per cycle graph."""
+    inst = _instances()
+    opts = fr.default_opts(tol_lin=1e-10, gmres_max_restarts=40)
+    meshes = [(xe, ye) for xe, ye, _, _ in inst]
+    degs = [p for _, _, p, _ in inst]
+    res, nodes = {}, {}
+    for on in (True, False):
+        B = fr.Batch(meshes, degs, opts)
+        B.set_batched(on)
+        Us = [_t(U0) for *_, U0 in inst]
+        its = []
+        for _ in range(2):
+            its.append([s.gmres_iters for s in B.step_row(4, 0.1, Us)])
+        res[on] = ([U.cpu().numpy() for U in Us], its)
+        nodes[on] = B.cycle_kernels()
+        B.close()
+    assert res[True][1] == res[False][1]
+    for a, b in zip(res[True][0], res[False][0]):
+        assert np.array_equal(a, b)
+    m = opts.gmres_m
+    # per Arnoldi iteration: 7 kernels per instance, against one apply and one
+    # FD operator per degree present plus four Gram-Schmidt and one Givens launch
+    assert nodes[False] >= 7 * m * len(inst)
+    assert nodes[True] <= (2 * len(set(degs)) + 5) * m + 20 * len(inst)
