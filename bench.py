@@ -929,6 +929,15 @@ def guess_arm(args):
     xg = torch.zeros_like(U)
     floor = fr.gmres_solve(c1, U, R0, shift, R0, xg, m=30, rtol=1e-12, max_restarts=20)
 
+    # target normalisation: train on T / sigma (sigma = RMS of the captured
+    # targets), so that the network's outputs and losses are of order one
+    sigma = 1.0
+    if args.normalize_targets:
+        sigma = float(torch.sqrt((Tc[:n].double() ** 2).mean()))
+        if sigma > 0.0:
+            Tc[:n] /= sigma
+        else:
+            sigma = 1.0
     rng = np.random.default_rng(0)
     sizes = [3 * nb, 256, 256, nb]
     model = fr.MLP(3 * nb, 256, nb, max_batch=max(8192, ne))
@@ -951,9 +960,16 @@ def guess_arm(args):
         model.adam(1e-3 if it < iters * 2 // 3 else 3e-4)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    # loss of predicting no change, for scale
+    # loss of predicting no change, for scale (in the units trained on)
     Tz = Tc[:n]
     zero_loss = float((Tz.double() ** 2).sum(dim=1).mean() / 2 / nb)
+    if sigma != 1.0:
+        # the network was trained on targets / sigma: scaling the last layer
+        # by sigma makes it predict the targets themselves
+        flat = model.get_params()
+        o3 = 3 * nb * 256 + 256 + 256 * 256 + 256
+        flat[o3:] *= sigma
+        model.set_params(flat)
     del Xc, Tc
     fr.fr_attach_guess_model(ctx[2], model)
 
@@ -980,7 +996,7 @@ def guess_arm(args):
            "stage_solve_floor": {"relres": floor.relres, "iters": floor.iters, "target": 1e-12},
            "train_iters": iters, "minibatch": bs, "train_s": train_s,
            "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-50:])),
-           "loss_zero_prediction": zero_loss,
+           "loss_zero_prediction": zero_loss, "target_rms": sigma if args.normalize_targets else None,
            "eval_seeds": [evals[0], evals[-1]],
            "second_step": {names[m]: {"gmres_iters_per_step": res[m]["iters"] / len(evals),
                                       "seconds_per_step": res[m]["seconds"] / len(evals),
@@ -1070,6 +1086,8 @@ def main():
     ap.add_argument("--eval-seeds", type=int, default=50, help="--workload guess: held-out seeds")
     ap.add_argument("--train-iters", type=int, default=3000, help="--workload guess: Adam steps")
     ap.add_argument("--guess-tol", type=float, default=1e-8, help="--workload guess: GMRES tolerance tol_lin")
+    ap.add_argument("--normalize-targets", type=int, default=1, choices=[0, 1],
+                    help="--workload guess: train on targets scaled to unit RMS (the last layer is rescaled after)")
     ap.add_argument("--count", type=int, default=64, help="--workload batch: number of instances")
     ap.add_argument("--scheme", default=None,
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])

@@ -259,48 +259,74 @@ __global__ void k_cycle_init(GmresDev gd, const double* nr2, const double* nb2, 
   gd.invh[0] = beta > 0.0 ? 1.0 / beta : 0.0;
 }
 
-// Hessenberg column j, Givens rotations, residual estimate, convergence
+// Hessenberg column j, Givens rotations, residual estimate, convergence.
+// One warp: the lanes bring the column's Gram-Schmidt coefficients and the
+// earlier rotations into shared memory together (one round of independent
+// loads instead of a chain of dependent ones), lane 0 applies the rotations
+// in order, and the lanes write the column back.
 __device__ __forceinline__ void givens_body(const GmresDev& gd, int j, const double* nw2) {
+  __shared__ double hs[kMaxVec + 1], cs_s[kMaxVec], sn_s[kMaxVec];
   if (*gd.done) return;
-  double* Hj = gd.H + (size_t)j * gd.ldh;
-  for (int i = 0; i <= j; ++i) Hj[i] = gd.h1[i] + gd.h2[i];
-  const double hn = sqrt(*nw2);
-  Hj[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = gd.cs[i] * Hj[i] + gd.sn[i] * Hj[i + 1];
-    Hj[i + 1] = -gd.sn[i] * Hj[i] + gd.cs[i] * Hj[i + 1];
-    Hj[i] = t;
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i <= j; i += 32) hs[i] = gd.h1[i] + gd.h2[i];
+  for (int i = lane; i < j; i += 32) {
+    cs_s[i] = gd.cs[i];
+    sn_s[i] = gd.sn[i];
   }
-  const double den = hypot(Hj[j], Hj[j + 1]);
-  const double c = den > 0.0 ? Hj[j] / den : 1.0;
-  const double s = den > 0.0 ? Hj[j + 1] / den : 0.0;
-  gd.cs[j] = c;
-  gd.sn[j] = s;
-  Hj[j] = den;
-  Hj[j + 1] = 0.0;
-  gd.g[j + 1] = -s * gd.g[j];
-  gd.g[j] = c * gd.g[j];
-  *gd.k = j + 1;
-  const double res = fabs(gd.g[j + 1]);
-  *gd.res = res;
-  gd.invh[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-  if (res <= *gd.target || hn == 0.0 || !(res == res)) *gd.done = 1;
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = sqrt(*nw2);
+    hs[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs_s[i] * hs[i] + sn_s[i] * hs[i + 1];
+      hs[i + 1] = -sn_s[i] * hs[i] + cs_s[i] * hs[i + 1];
+      hs[i] = t;
+    }
+    const double den = hypot(hs[j], hs[j + 1]);
+    const double c = den > 0.0 ? hs[j] / den : 1.0;
+    const double s = den > 0.0 ? hs[j + 1] / den : 0.0;
+    gd.cs[j] = c;
+    gd.sn[j] = s;
+    hs[j] = den;
+    hs[j + 1] = 0.0;
+    gd.g[j + 1] = -s * gd.g[j];
+    gd.g[j] = c * gd.g[j];
+    *gd.k = j + 1;
+    const double res = fabs(gd.g[j + 1]);
+    *gd.res = res;
+    gd.invh[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (res <= *gd.target || hn == 0.0 || !(res == res)) *gd.done = 1;
+  }
+  __syncwarp();
+  double* Hj = gd.H + (size_t)j * gd.ldh;
+  for (int i = lane; i <= j + 1; i += 32) Hj[i] = hs[i];
 }
 
 __global__ void k_givens(GmresDev gd, int j, const double* nw2) {
-  if (threadIdx.x != 0) return;
   givens_body(gd, j, nw2);
 }
 
-// y = H(0:k,0:k)^{-1} g(0:k)
+// y = H(0:k,0:k)^{-1} g(0:k); one warp loads the triangle, lane 0 solves
 __global__ void k_backsub(GmresDev gd) {
-  if (threadIdx.x != 0) return;
+  __shared__ double Hs[kMaxVec][kMaxVec];
+  __shared__ double ys[kMaxVec];
   const int k = *gd.k;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = gd.g[i];
-    for (int l = i + 1; l < k; ++l) s -= gd.H[(size_t)l * gd.ldh + i] * gd.y[l];
-    gd.y[i] = s / gd.H[(size_t)i * gd.ldh + i];
+  const int lane = threadIdx.x & 31;
+  for (int idx = lane; idx < k * k; idx += 32) {
+    const int l = idx / k, i = idx % k;   // column l, row i
+    if (i <= l) Hs[l][i] = gd.H[(size_t)l * gd.ldh + i];
   }
+  for (int i = lane; i < k; i += 32) ys[i] = gd.g[i];
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = ys[i];
+      for (int l = i + 1; l < k; ++l) s -= Hs[l][i] * ys[l];
+      ys[i] = s / Hs[i][i];
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) gd.y[i] = ys[i];
 }
 
 // cycle status for the host: [k, |g_k|, rtol ||b||, ||b||]; marks the
@@ -362,7 +388,6 @@ __global__ void __launch_bounds__(256) kb_update(const BatchKrylov* __restrict__
 }
 
 __global__ void kb_givens(const BatchKrylov* __restrict__ tab, int j) {
-  if (threadIdx.x != 0) return;
   const BatchKrylov& t = tab[blockIdx.x];
   givens_body(t.gd, j, t.nw2);
 }

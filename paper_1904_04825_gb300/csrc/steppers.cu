@@ -581,14 +581,16 @@ int join_all(fr_batch* B) {
   return FR_OK;
 }
 
-// Layout of the batched-iteration tables in tab_dev (host mirror in tab):
-// [BatchKrylov x K][vec starts K+1] then per degree g = 2, 3, 4:
-// [BatchApply x n_g][apply starts n_g+1][ResArgs x n_g][tile starts n_g+1].
+// Layout of the batched-iteration tables in tab_dev, per degree g = 2, 3, 4
+// (the instances of one degree form a group whose Arnoldi iterations run as
+// one chain of batched launches on a stream of its own):
+// [BatchKrylov x n_g][vec starts n_g+1][BatchApply x n_g][apply starts n_g+1]
+// [ResArgs x n_g][tile starts n_g+1].
 struct BatchPlan {
-  size_t off_kry = 0, off_vstart = 0;
+  size_t off_kry[3] = {}, off_vstart[3] = {};
   size_t off_app[3] = {}, off_astart[3] = {}, off_res[3] = {}, off_rstart[3] = {};
   int n[3] = {}, nb[3] = {};
-  int app_blocks[3] = {}, res_blocks[3] = {}, vec_blocks = 0;
+  int app_blocks[3] = {}, res_blocks[3] = {}, vec_blocks[3] = {};
   size_t bytes = 0;
 };
 
@@ -607,11 +609,12 @@ BatchPlan plan_of(const fr_batch* B) {
   BatchPlan P;
   const int K = (int)B->m.size();
   for (const fr_ctx* c : B->m) P.n[c->p - 2] += 1;
+  (void)K;
   size_t o = 0;
-  P.off_kry = o; o = align16(o + (size_t)K * sizeof(BatchKrylov));
-  P.off_vstart = o; o = align16(o + (size_t)(K + 1) * sizeof(int));
   for (int g = 0; g < 3; ++g) {
     P.nb[g] = 4 * (g + 3) * (g + 3);
+    P.off_kry[g] = o; o = align16(o + (size_t)P.n[g] * sizeof(BatchKrylov));
+    P.off_vstart[g] = o; o = align16(o + (size_t)(P.n[g] + 1) * sizeof(int));
     P.off_app[g] = o; o = align16(o + (size_t)P.n[g] * batch_apply_bytes());
     P.off_astart[g] = o; o = align16(o + (size_t)(P.n[g] + 1) * sizeof(int));
     P.off_res[g] = o; o = align16(o + (size_t)P.n[g] * batch_residual_bytes());
@@ -626,17 +629,14 @@ BatchPlan plan_of(const fr_batch* B) {
 int fill_tables(fr_batch* B, BatchPlan* P, double shift, double* const* U) {
   const int K = (int)B->m.size();
   std::vector<unsigned char> h(P->bytes, 0);
-  BatchKrylov* kry = reinterpret_cast<BatchKrylov*>(h.data() + P->off_kry);
-  int* vstart = reinterpret_cast<int*>(h.data() + P->off_vstart);
   int fill[3] = {0, 0, 0};
-  int acc_a[3] = {0, 0, 0}, acc_r[3] = {0, 0, 0};
-  int accv = 0;
+  int acc_a[3] = {0, 0, 0}, acc_r[3] = {0, 0, 0}, acc_v[3] = {0, 0, 0};
   for (int k = 0; k < K; ++k) {
     fr_ctx* c = B->m[k];
-    kry[k] = batch_krylov_args(c);
-    vstart[k] = accv;
-    accv += (int)vec_grid_of(c);
     const int g = c->p - 2, q = fill[g]++;
+    reinterpret_cast<BatchKrylov*>(h.data() + P->off_kry[g])[q] = batch_krylov_args(c);
+    reinterpret_cast<int*>(h.data() + P->off_vstart[g])[q] = acc_v[g];
+    acc_v[g] += (int)vec_grid_of(c);
     int* astart = reinterpret_cast<int*>(h.data() + P->off_astart[g]);
     int* rstart = reinterpret_cast<int*>(h.data() + P->off_rstart[g]);
     BATCH_TRY(B, k, fill_batch_apply(c, reinterpret_cast<BatchApply*>(h.data() + P->off_app[g] + q * batch_apply_bytes())));
@@ -649,9 +649,9 @@ int fill_tables(fr_batch* B, BatchPlan* P, double shift, double* const* U) {
     rstart[q] = acc_r[g];
     acc_r[g] += (int)gr;
   }
-  vstart[K] = accv;
-  P->vec_blocks = accv;
   for (int g = 0; g < 3; ++g) {
+    reinterpret_cast<int*>(h.data() + P->off_vstart[g])[P->n[g]] = acc_v[g];
+    P->vec_blocks[g] = acc_v[g];
     reinterpret_cast<int*>(h.data() + P->off_astart[g])[P->n[g]] = acc_a[g];
     reinterpret_cast<int*>(h.data() + P->off_rstart[g])[P->n[g]] = acc_r[g];
     P->app_blocks[g] = acc_a[g];
@@ -713,20 +713,22 @@ int capture_cycle(fr_batch* B, int i, const RowTab& t, double dt, double* const*
     if (rc == FR_OK) rc = join_all(B);
     const int m = B->m[0]->opts.gmres_m, prec = B->m[0]->opts.block_precision, rm = B->m[0]->opts.riemann;
     unsigned char* T = B->tab_dev;
+    // the groups' launches in order on the main stream, iteration by iteration
     for (int j = 0; j < m && rc == FR_OK; ++j) {
-      for (int g = 0; g < 3 && rc == FR_OK; ++g)
-        if (P.n[g])
-          rc = launch_batch_apply(P.nb[g], prec, reinterpret_cast<const BatchApply*>(T + P.off_app[g]),
-                                  reinterpret_cast<const int*>(T + P.off_astart[g]), P.n[g], P.app_blocks[g], j,
-                                  B->main);
-      for (int g = 0; g < 3 && rc == FR_OK; ++g)
-        if (P.n[g])
+      for (int g = 0; g < 3 && rc == FR_OK; ++g) {
+        if (!P.n[g]) continue;
+        rc = launch_batch_apply(P.nb[g], prec, reinterpret_cast<const BatchApply*>(T + P.off_app[g]),
+                                reinterpret_cast<const int*>(T + P.off_astart[g]), P.n[g], P.app_blocks[g], j,
+                                B->main);
+        if (rc == FR_OK)
           rc = launch_batch_residual(g + 2, rm, T + P.off_res[g], reinterpret_cast<const int*>(T + P.off_rstart[g]),
                                      P.n[g], P.res_blocks[g], j, B->main);
-      if (rc == FR_OK)
-        rc = launch_batch_gs_givens(reinterpret_cast<const BatchKrylov*>(T + P.off_kry),
-                                    reinterpret_cast<const int*>(T + P.off_vstart), K, P.vec_blocks, j, B->main);
-      if (rc != FR_OK) rc = batch_err(B, rc, "batched Arnoldi launch failed");
+        if (rc == FR_OK)
+          rc = launch_batch_gs_givens(reinterpret_cast<const BatchKrylov*>(T + P.off_kry[g]),
+                                      reinterpret_cast<const int*>(T + P.off_vstart[g]), P.n[g], P.vec_blocks[g], j,
+                                      B->main);
+        if (rc != FR_OK) rc = batch_err(B, rc, "batched Arnoldi launch failed");
+      }
     }
     if (rc == FR_OK) rc = fork_all(B);
     for (int k = 0; k < K && rc == FR_OK; ++k) {

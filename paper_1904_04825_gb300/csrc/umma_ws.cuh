@@ -12,10 +12,11 @@
 //    accumulation) for every slice into one of two accumulators in tensor
 //    memory (tile parity), frees the stage with tcgen05.commit and, after a
 //    tile's last slice, hands the accumulator to the epilogue;
-//  * warps 2..5 read the accumulator with tcgen05.ld (warp w owns lanes
-//    32 (w mod 4) ..), add the bias, apply ReLU, convert and store the rows,
-//    and give the accumulator back; so the epilogue of one tile overlaps the
-//    MMAs of the next.
+//  * warps 2..9 read the accumulator with tcgen05.ld (warp w owns lanes
+//    32 (w mod 4) ..; two warps per lane quarter, each half of the columns),
+//    add the bias (staged in shared memory), apply ReLU, convert and store
+//    the rows, and give the accumulator back; so the epilogue of one tile
+//    overlaps the MMAs of the next.
 // Operands are K-major with the 128-byte swizzle: 8-row x 128-byte atoms
 // (64 BF16 values of K per row), 1024 bytes between 8-row groups; the K
 // steps of 16 inside an atom advance the descriptor's start address by 32
@@ -33,7 +34,7 @@
 namespace frk {
 namespace umws {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
+constexpr int BM = 128, BK = 64, STAGES = 4, EPI_WARPS = 8, THREADS = 64 + 32 * EPI_WARPS;
 constexpr unsigned A_STAGE = BM * BK * 2;  // 16 KB per stage
 constexpr unsigned TMEM_COLS = 512;        // two accumulators of up to 256 columns
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -41,9 +42,10 @@ constexpr size_t kSmemLimit = 227 * 1024;
 __host__ __device__ inline int npad_of(int n) { return (n + 15) / 16 * 16; }
 __host__ __device__ inline int nkb_of(int kp) { return (kp + BK - 1) / BK; }  // 64-wide column blocks of K
 __host__ __device__ inline size_t w_bytes(int n, int kp) { return (size_t)nkb_of(kp) * npad_of(n) * 128; }
-// shared memory: W (1024-aligned blocks), the A ring, barriers and the tensor-memory slot
+// shared memory: W (1024-aligned blocks), the A ring, the bias row, barriers
+// and the tensor-memory slot
 __host__ __device__ inline size_t smem_bytes(int n, int kp) {
-  return w_bytes(n, kp) + (size_t)STAGES * A_STAGE + 256 + 1024;  // + alignment slack
+  return w_bytes(n, kp) + (size_t)STAGES * A_STAGE + 4 * (size_t)npad_of(n) + 256 + 1024;  // + alignment slack
 }
 inline bool fits(int n, int kp) { return n <= 256 && smem_bytes(n, kp) <= kSmemLimit; }
 
@@ -82,7 +84,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const unsigned wblk = (unsigned)npad * 128u;  // bytes of one 64-wide column block of W
   unsigned char* Ws = usm;
   unsigned char* As = usm + (size_t)nkb * wblk;
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(As + (size_t)STAGES * A_STAGE);
+  float* bias_s = reinterpret_cast<float*>(As + (size_t)STAGES * A_STAGE);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bias_s + npad);
   unsigned long long* empty = full + STAGES;
   unsigned long long* tfull = empty + STAGES;
   unsigned long long* tempty = tfull + 2;
@@ -104,11 +107,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], EPI_WARPS);
     }
     mbar_init(wbar, 1);
     mbar_fence_init();
   }
+  for (int c = threadIdx.x; c < npad; c += THREADS) bias_s[c] = c < N ? bias[c] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -185,8 +189,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         (void)mbar_wait(&empty[j % STAGES], (unsigned)((j / STAGES) & 1), kWaitPolls);
     }
   } else if (warp >= 2) {
-    // ---- epilogue ----
+    // ---- epilogue: two warps per lane quarter, each a contiguous half of
+    // the columns, two 16-column accumulator loads in flight per wait ----
     const int q = warp & 3;               // lane quarter of tensor memory
+    const int half = (warp - 2) >> 2;     // 0: columns [0, hcol), 1: [hcol, npad)
+    const int hcol = (npad / 32) * 16 > 0 ? (npad / 32) * 16 : npad;
+    const int cbeg = half ? hcol : 0, cend = half ? npad : hcol;
     const int r_in_tile = q * 32 + lane;  // accumulator row of this thread
     int t = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
@@ -197,46 +205,59 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row = (long long)tile * BM + r_in_tile;
-      for (int c0 = 0; c0 < npad; c0 += 16) {
-        unsigned vv[16];
+      const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * 256);
+      for (int c0 = cbeg; c0 < cend; c0 += 32) {
+        const bool two = c0 + 16 < cend;
+        unsigned vv[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(vv[0]), "=r"(vv[1]), "=r"(vv[2]), "=r"(vv[3]), "=r"(vv[4]), "=r"(vv[5]), "=r"(vv[6]),
               "=r"(vv[7]), "=r"(vv[8]), "=r"(vv[9]), "=r"(vv[10]), "=r"(vv[11]), "=r"(vv[12]), "=r"(vv[13]),
               "=r"(vv[14]), "=r"(vv[15])
-            : "r"(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * 256 + c0)));
+            : "r"(taddr + (unsigned)c0));
+        if (two)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(vv[16]), "=r"(vv[17]), "=r"(vv[18]), "=r"(vv[19]), "=r"(vv[20]), "=r"(vv[21]), "=r"(vv[22]),
+                "=r"(vv[23]), "=r"(vv[24]), "=r"(vv[25]), "=r"(vv[26]), "=r"(vv[27]), "=r"(vv[28]), "=r"(vv[29]),
+                "=r"(vv[30]), "=r"(vv[31])
+              : "r"(taddr + (unsigned)(c0 + 16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (row < M) {
-          float x[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = c0 + j;
-            x[j] = __uint_as_float(vv[j]) + (col < N ? bias[col] : 0.f);
-            if (RELU) x[j] = fmaxf(x[j], 0.f);
-          }
-          const int ncol = min(16, ldo - c0);  // columns of the output row in this chunk
-          if (OUT_BF16) {
-            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)row * ldo + c0;
-            if (ncol == 16) {
-              unsigned w[8];
+          for (int h2 = 0; h2 < 2; ++h2) {
+            if (h2 == 1 && !two) break;
+            const int cc = c0 + 16 * h2;
+            float x[16];
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
-                w[j] = *reinterpret_cast<const unsigned*>(&h);
-              }
-              reinterpret_cast<uint4*>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-              reinterpret_cast<uint4*>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-            } else {
-              for (int j = 0; j < ncol; ++j) o[j] = __float2bfloat16_rn(x[j]);
+            for (int j = 0; j < 16; ++j) {
+              x[j] = __uint_as_float(vv[16 * h2 + j]) + bias_s[cc + j];
+              if (RELU) x[j] = fmaxf(x[j], 0.f);
             }
-          } else {
-            float* o = reinterpret_cast<float*>(out) + (size_t)row * ldo + c0;
-            if (ncol == 16 && (ldo % 4) == 0) {
+            const int ncol = min(16, ldo - cc);  // columns of the output row in this chunk
+            if (OUT_BF16) {
+              __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)row * ldo + cc;
+              if (ncol == 16) {
+                unsigned w[8];
 #pragma unroll
-              for (int j = 0; j < 4; ++j)
-                reinterpret_cast<float4*>(o)[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+                for (int j = 0; j < 8; ++j) {
+                  const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+                  w[j] = *reinterpret_cast<const unsigned*>(&h);
+                }
+                reinterpret_cast<uint4*>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                reinterpret_cast<uint4*>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+              } else {
+                for (int j = 0; j < ncol; ++j) o[j] = __float2bfloat16_rn(x[j]);
+              }
             } else {
-              for (int j = 0; j < ncol; ++j) o[j] = x[j];
+              float* o = reinterpret_cast<float*>(out) + (size_t)row * ldo + cc;
+              if (ncol == 16 && (ldo % 4) == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  reinterpret_cast<float4*>(o)[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+              } else {
+                for (int j = 0; j < ncol; ++j) o[j] = x[j];
+              }
             }
           }
         }
