@@ -41,6 +41,7 @@ METRIC = "DOF*GMRES-iters/s (plain FP64 JFNK, ROW3 step, 160x160 p=3 vortex)"
 UNIT = "DOF*iter/s"
 WORKLOAD = "vortex-160x160-p3-ROW3-dt0.05-gmres30-tol1e-6"
 FP64_PEAK_TFLOPS = 1.259  # 152 SMs x 4 FP64 flops/clk/SM x 2.07 GHz (nominal 1.25 TF)
+FP32_PEAK_TFLOPS = 80.54  # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (CUDA cores)
 REF_NX = 24               # oracle sample mesh (same p, scheme, CFL, tolerance)
 REF_ARM_NX = 16           # smaller sample for the per-step reference arm
 
@@ -295,9 +296,12 @@ def our_arm(args):
         wl = f"vortex-160x160-p3-{args.scheme.upper()}-dt{dt:g}-gmres30-tol{TOL_LIN:g}"
     elif args.workload == "tgv":
         # Taylor-Green vortex (Sec. 5): 64^3 hexahedra at p = 3, Re 1600, Ma 0.1,
-        # dt = t_c / 25, tol_lin 1e-6; element-Jacobi blocks only where built (p <= 2)
+        # dt = t_c / 25, tol_lin 1e-6; element-Jacobi blocks for p <= 3 (the
+        # 320-row blocks of p = 3 are stored in FP32 unless BF16 is asked for)
         tg = S.TaylorGreen()
         p = args.p or 3
+        if p == 3 and prec == 0:
+            prec, args.block_precision = 1, "fp32"
         n3 = args.nx or 64
         edges3 = S.uniform_mesh3d(n3)
         X, Y, Z = S.point_coords3d(*edges3, p)
@@ -305,9 +309,9 @@ def our_arm(args):
         del X, Y, Z
         dt, wall = (args.dt or tg.t_c / 25.0), False
         opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=args.gmres_m, m_max=args.gmres_m, gmres_max_restarts=20,
-                               block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 2 else 0)
+                               block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 3 else 0)
         wl = (f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}-gmres{args.gmres_m}"
-              + ("" if p <= 2 else "-noprecond"))
+              + ("" if p <= 3 else "-noprecond"))
     else:
         ch = S.Channel()
         cnx, cny = args.nx or 256, args.ny or 128
@@ -447,18 +451,21 @@ def our_arm(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alu_peak, alu_src = FP64_PEAK_TFLOPS, "FP64 FMA pipe: 152 SMs x 4 flops/clk x 2.07 GHz (derived, nominal 1.25 TF)"
+    if top == "invert" and prec:   # reduced-precision blocks are inverted in FP32 on the CUDA cores
+        alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"
     roofline = {
-        "kernel": top, "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+        "kernel": top, "bound": "alu", "achieved": achieved_tf, "peak": alu_peak,
+        "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
         "traffic": None,
-        "peak_source": "FP64 FMA pipe: 152 SMs x 4 flops/clk x 2.07 GHz (derived, nominal 1.25 TF)",
+        "peak_source": alu_src,
         "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
         "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof["launches"],
         "algorithmic_bytes_per_launch": work_bytes, "algorithmic_flops_per_launch": work_flops,
     }
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file):
+    if os.path.exists(traffic_file) and args.workload == "vortex":   # captured on the vortex kernels
         try:
             tr = json.load(open(traffic_file)).get(top)
             if tr:
@@ -644,8 +651,10 @@ def kernel_arm(args):
         X, Y, Z = S.point_coords3d(*edges, p3)
         U = torch.from_numpy(tg.state(X, Y, Z)).cuda()
         del X, Y, Z
+        if p3 == 3 and prec == 0:
+            prec, args.block_precision = 1, "fp32"   # 320-row blocks are stored in FP32 or BF16
         ctx = fr.Context3D(*edges, p3, fr.default_opts(block_precision=prec, mu=tg.mu, prandtl=tg.prandtl,
-                                                        precond=1 if p3 <= 2 else 0, m_max=4, gmres_m=4))
+                                                        precond=1 if p3 <= 3 else 0, m_max=4, gmres_m=4))
     else:
         xe, ye = S.uniform_mesh(NX)
         X, Y = S.point_coords(xe, ye, P)
@@ -668,20 +677,29 @@ def kernel_arm(args):
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
-    fr.fr_profile_begin(ctx, [args.kernel])
+    # the staged blocks of the viscous and 3D contexts are inverted by
+    # separate launches (family "invert"), timed alongside
+    fams = [args.kernel] + (["invert"] if args.kernel == "factor" else [])
+    fr.fr_profile_begin(ctx, fams)
     for _ in range(args.steps):
         run()
     torch.cuda.synchronize()
-    pr = fr.fr_profile_end(ctx)[args.kernel]
-    us = pr["ms"] / max(pr["launches"], 1) * 1e3
-    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "ndof": ctx.ndof,
-                      "block_precision": args.block_precision,
-                      "jv_precision": args.jv_precision,
-                      "launches": pr["launches"], "avg_us": us,
-                      "tflops": pr["flops"] / pr["launches"] / (us * 1e-6) / 1e12,
-                      "gbs": pr["bytes"] / pr["launches"] / (us * 1e-6) / 1e9,
-                      "bytes_per_launch": pr["bytes"] / pr["launches"],
-                      "flops_per_launch": pr["flops"] / pr["launches"]}))
+    prof = fr.fr_profile_end(ctx)
+
+    def summary(pr):
+        us = pr["ms"] / max(pr["launches"], 1) * 1e3
+        return {"launches": pr["launches"], "avg_us": us,
+                "tflops": pr["flops"] / max(pr["launches"], 1) / (us * 1e-6) / 1e12 if us > 0 else None,
+                "gbs": pr["bytes"] / max(pr["launches"], 1) / (us * 1e-6) / 1e9 if us > 0 else None,
+                "bytes_per_launch": pr["bytes"] / max(pr["launches"], 1),
+                "flops_per_launch": pr["flops"] / max(pr["launches"], 1),
+                "ms_per_call": pr["ms"] / args.steps}
+    out = {"kernel": args.kernel, "workload": args.workload, "ndof": ctx.ndof,
+           "block_precision": args.block_precision, "jv_precision": args.jv_precision}
+    out.update(summary(prof[args.kernel]))
+    if args.kernel == "factor" and prof["invert"]["launches"]:
+        out["invert"] = summary(prof["invert"])
+    print(json.dumps(out))
     return 0
 
 

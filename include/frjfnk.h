@@ -464,13 +464,14 @@ int fr_autotune(fr_ctx* ctx, const double* U, double shift, int reps, double* ms
 enum {
   FR_KF_RESIDUAL = 0,  /* R(U) */
   FR_KF_JV = 1,        /* FD operator A z and b - A z */
-  FR_KF_FACTOR = 2,    /* element-block formation + inversion */
+  FR_KF_FACTOR = 2,    /* element-block formation (+ inversion where one kernel does both) */
   FR_KF_APPLY = 3,     /* element-Jacobi apply (incl. basis normalisation) */
   FR_KF_DOTS = 4,      /* Gram-Schmidt multi-dot products */
   FR_KF_UPDATE = 5,    /* Gram-Schmidt multi-AXPY updates */
   FR_KF_SOLUPDATE = 6, /* x += M^-1 V y */
   FR_KF_OTHER = 7,     /* norms, linear combinations, copies, Givens */
-  FR_KF_COUNT = 8
+  FR_KF_INVERT = 8,    /* inversion of staged element blocks (viscous and 3D contexts) */
+  FR_KF_COUNT = 9
 };
 
 /* Test hook (no counterpart in the paper) for the bounded waits of the
@@ -484,6 +485,16 @@ enum {
  * gave up).  Nothing faults.  A context that reported FR_ERR_TIMEOUT keeps
  * reporting it: destroy it. */
 int fr_set_wait_test(fr_ctx* ctx, unsigned polls, int skip_first_copy);
+
+/* Elements whose FD element blocks (Sec. 4.5) are staged in FP64 and
+ * inverted at a time.  3D degree-3 contexts (320-row blocks, 800 KB each in
+ * FP64) stage 4096 elements at a time; every other context stages all
+ * elements at once.  n may lower the chunk (1 <= n <= the chunk the context
+ * allocated; a smaller chunk changes no result, only the number of
+ * launches); FR_ERR_INVALID_ARG otherwise.  With chunks, a new shift of the
+ * pseudo-transient iteration forms the blocks again instead of re-inverting
+ * the staging. */
+int fr_set_block_chunk(fr_ctx* ctx, long long n);
 
 /* Number of kernels this library has launched in this process. */
 long long fr_kernel_launches(void);

@@ -31,7 +31,7 @@ FR_ERR_TIMEOUT = 6
 FR_ERR_UNSUPPORTED = 7
 
 # kernel families of the measurement hooks
-KF_NAMES = ["residual", "jv", "factor", "apply", "dots", "update", "solupdate", "other"]
+KF_NAMES = ["residual", "jv", "factor", "apply", "dots", "update", "solupdate", "other", "invert"]
 FR_KF_COUNT = len(KF_NAMES)
 ERROR_NAMES = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_CUDA", 3: "FR_ERR_NONFINITE",
                4: "FR_ERR_NOT_CONVERGED", 5: "FR_ERR_PTC_STALLED", 6: "FR_ERR_TIMEOUT",
@@ -127,6 +127,7 @@ def _load():
         "step_ssprk3": (I, [P, D, P, ctypes.POINTER(fr_step_stats), V]),
         "fr_kernel_launches": (ctypes.c_longlong, []),
         "fr_set_wait_test": (I, [P, ctypes.c_uint, I]),
+        "fr_set_block_chunk": (I, [P, ctypes.c_longlong]),
         "fr_jv_noalloc": (I, [ctypes.POINTER(fr_mesh_desc), I, ctypes.POINTER(fr_opts), P, P, P, D, P, V]),
         "fr_mlp_create": (I, [I, I, I, I, ctypes.POINTER(ctypes.c_void_p)]),
         "fr_mlp_destroy": (I, [P]),
@@ -407,6 +408,11 @@ def step_ssprk3(ctx: Context, dt: float, U, stream=None):
 def fr_set_wait_test(ctx: Context, polls: int = 0, skip_first_copy: bool = False):
     """Test hook for the element-Jacobi apply's bounded waits (see the C header)."""
     return ctx.check(lib.fr_set_wait_test(ctx.handle, int(polls), int(bool(skip_first_copy))))
+
+
+def fr_set_block_chunk(ctx: Context, n: int):
+    """Elements whose FD element blocks are staged and inverted at a time (see the C header)."""
+    return ctx.check(lib.fr_set_block_chunk(ctx.handle, int(n)))
 
 
 def fr_kernel_launches() -> int:

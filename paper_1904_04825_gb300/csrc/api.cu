@@ -91,6 +91,7 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   c->ny = mesh->ny;
   c->ne = (long long)mesh->nx * mesh->ny;
   c->ndof = c->ne * c->nb;
+  c->blk_chunk = c->ne;
   FRK_CUDA(c, cudaGetDevice(&c->device));
   build_tables(p, &c->tab);
   double* hx = new double[mesh->nx];
@@ -162,8 +163,10 @@ int create(const fr_mesh_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
 }
 
 // 3D context: periodic hexahedra, 5 variables, (p+1)^3 points per element.
-// Element blocks and their staging exist only where they are built (p <= 2
-// with the preconditioner on).
+// Element blocks and their staging exist only with the preconditioner on
+// (p <= 3).  Degree 3 (320-row blocks): the blocks are stored in the block
+// precision (FP32 or BF16) and the FP64 staging holds kStageChunk3
+// elements at a time (3.4 GB).
 int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   c->opts = *o;
   c->dim3 = 1;
@@ -199,8 +202,16 @@ int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 6 * n2 * 20));
   FRK_TRY(dalloc(c, &c->fb, (size_t)c->ne * 3 * n2 * 10));
   if (o->precond) {
-    FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * c->nb * c->nb));
-    FRK_TRY(dalloc(c, &c->mst, (size_t)c->ne * c->nb * c->nb));
+    const size_t nb2 = (size_t)c->nb * c->nb;
+    if (p <= 2) {
+      c->blk_chunk = c->ne;
+      FRK_TRY(dalloc(c, &c->blocks, (size_t)c->ne * nb2));
+    } else {
+      c->blk_chunk = c->ne < kStageChunk3 ? c->ne : kStageChunk3;
+      const size_t sbytes = o->block_precision == 1 ? 4 : 2;
+      FRK_TRY(dalloc(c, &c->blocks, ((size_t)c->ne * nb2 * sbytes + 7) / 8));
+    }
+    FRK_TRY(dalloc(c, &c->mst, (size_t)c->blk_chunk * nb2));
     FRK_TRY(dalloc(c, &c->rloc, n));
   }
   FRK_TRY(dalloc(c, &c->diss, 4));
@@ -417,9 +428,10 @@ extern "C" int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts
       o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
     return FR_ERR_INVALID_ARG;
   // the 3D path: Rusanov flux, FP64 operator, no body force; element blocks
-  // for p <= 2 (5 (p+1)^3 = 40 or 135 rows), no learned guess
+  // for p <= 3 (5 (p+1)^3 = 40, 135 or 320 rows; 320-row blocks in FP32 or
+  // BF16 only), no learned guess
   if (o.riemann != 0 || o.jv_precision != 0 || o.guess == 2 || o.body_force_x != 0.0) return FR_ERR_UNSUPPORTED;
-  if (o.precond && p > 2) return FR_ERR_UNSUPPORTED;
+  if (o.precond && (p > 3 || (p == 3 && o.block_precision == 0))) return FR_ERR_UNSUPPORTED;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;
   for (int i = 0; i < mesh->ny; ++i)
@@ -459,6 +471,15 @@ extern "C" int fr_set_wait_test(fr_ctx* ctx, unsigned polls, int skip_first_copy
     return set_error(ctx, FR_ERR_INVALID_ARG, "fr_set_wait_test: skip_first_copy must be 0 or 1");
   ctx->wait_polls = polls ? polls : kWaitPolls;
   ctx->test_skip_copy = skip_first_copy;
+  return FR_OK;
+}
+
+extern "C" int fr_set_block_chunk(fr_ctx* ctx, long long n) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  const long long cap = ctx->dim3 && ctx->p == 3 ? (ctx->ne < kStageChunk3 ? ctx->ne : kStageChunk3) : ctx->ne;
+  if (!ctx->mst || n < 1 || n > cap)
+    return set_error(ctx, FR_ERR_INVALID_ARG, "fr_set_block_chunk: n must be in [1, %lld]", cap);
+  ctx->blk_chunk = n;
   return FR_OK;
 }
 

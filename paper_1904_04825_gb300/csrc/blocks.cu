@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "gj_cluster.cuh"
 #include "gj_tc.cuh"
 
 namespace frk {
@@ -313,7 +314,7 @@ struct InvertLayout {
 };
 
 template <int NB, typename T, typename S>
-__global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long ne,
+__global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, void* blocks, long long e0,
                                                 double dshift, int* err) {
   using L = InvertLayout<NB, T>;
   constexpr int LD = L::LD;
@@ -321,8 +322,8 @@ __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, 
   T* M = reinterpret_cast<T*>(smem_inv);
   T* col = M + NB * LD;
   int* piv = reinterpret_cast<int*>(col + NB);
-  const long long e = blockIdx.x;
-  const double* src = mst + e * (long long)NB * NB;
+  const long long e = e0 + blockIdx.x;
+  const double* src = mst + (long long)blockIdx.x * NB * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     const int c = idx / NB, r = idx % NB;
     M[r * LD + c] = (T)(r == c ? src[idx] + dshift : src[idx]);
@@ -528,15 +529,23 @@ __global__ void __launch_bounds__(ApplyLayout<NB, S, A>::THREADS)
                        t.red, t.done, t.ea, t.kerr, t.polls, t.skip, bid, nblk);
 }
 
+// Elements per pass and threads of the one-thread-per-row kernels.
+template <int NB> struct RowsShape {
+  static constexpr int EPC = NB >= 256 ? 1 : 256 / NB;
+  static constexpr int THREADS = (EPC * NB + 31) / 32 * 32;
+};
+
 // z_e = M_e^-1 (s r_e) for blocks whose rows are not 16-byte multiples (3D
-// degree 2: nb = 135), without bulk copies: EPC elements per pass, one
-// thread per row, column-major blocks so thread i reads consecutive
-// addresses; optional r_e *= s written back and sum of squares of z.
+// degree 2: nb = 135) or too large to stage in shared memory (3D degree 3:
+// nb = 320), without bulk copies: EPC elements per pass, one thread per row,
+// column-major blocks so thread i reads consecutive addresses; optional
+// r_e *= s written back and sum of squares of z.
 template <int NB, typename S, typename A>
-__global__ void __launch_bounds__(256) k_apply_rows(const S* __restrict__ Minv, double* r, const double* scale,
-                                                    double* z, long long ne, double* sumsq, Reduce red,
-                                                    const int* done, EpsArgs ea) {
-  constexpr int EPC = 256 / NB;
+__global__ void __launch_bounds__(RowsShape<NB>::THREADS) k_apply_rows(const S* __restrict__ Minv, double* r,
+                                                                       const double* scale, double* z, long long ne,
+                                                                       double* sumsq, Reduce red, const int* done,
+                                                                       EpsArgs ea) {
+  constexpr int EPC = RowsShape<NB>::EPC;
   __shared__ A rs[EPC][NB];
   __shared__ double sh[32];
   if (done && *done) return;
@@ -559,6 +568,7 @@ __global__ void __launch_bounds__(256) k_apply_rows(const S* __restrict__ Minv, 
     if (act) {
       const S* Me = Minv + e * (long long)NB * NB;
       A acc = 0;
+#pragma unroll 16
       for (int kk = 0; kk < NB; ++kk) acc = fma(load_acc(Me + kk * NB + i), rs[el][kk], acc);
       const double zi = (double)acc;
       z[e * NB + i] = zi;
@@ -604,11 +614,11 @@ __global__ void k_scale_copy(double* r, const double* scale, double* z, long lon
 
 // x += Minv (sum_{l<k} y_l V_l) per element (precond) -- right-preconditioned update.
 template <int NB, typename S, typename A>
-__global__ void __launch_bounds__(256) k_solupdate(const S* __restrict__ Minv,
-                                                   const double* __restrict__ V, long long ldv,
-                                                   const double* y, const int* kp, double* x,
-                                                   long long ne) {
-  constexpr int EPC = 256 / NB;
+__global__ void __launch_bounds__(RowsShape<NB>::THREADS) k_solupdate(const S* __restrict__ Minv,
+                                                                      const double* __restrict__ V, long long ldv,
+                                                                      const double* y, const int* kp, double* x,
+                                                                      long long ne) {
+  constexpr int EPC = RowsShape<NB>::EPC;
   __shared__ A ts[EPC][NB];
   __shared__ double ys[kMaxVec];
   const int k = *kp;
@@ -628,6 +638,7 @@ __global__ void __launch_bounds__(256) k_solupdate(const S* __restrict__ Minv,
     if (act) {
       const S* Me = Minv + e * (long long)NB * NB;
       A acc = 0;
+#pragma unroll 16
       for (int kk = 0; kk < NB; ++kk) acc = fma(load_acc(Me + kk * NB + i), ts[el][kk], acc);
       x[e * NB + i] += (double)acc;
     }
@@ -678,7 +689,7 @@ int factor_p(fr_ctx* ctx, const FactorArgs& a, cudaStream_t s) {
 
 template <int NB>
 unsigned apply_grid(long long ne) {
-  constexpr int EPC = 256 / NB;
+  constexpr int EPC = RowsShape<NB>::EPC;
   long long g = (ne + EPC - 1) / EPC;
   if (g > kRedBlocks) g = kRedBlocks;
   return (unsigned)(g < 1 ? 1 : g);
@@ -737,7 +748,7 @@ int apply_rows_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, doubl
   const double nd = (double)ctx->ndof;
   const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
-  constexpr int threads = ((256 / NB) * NB + 31) / 32 * 32;  // whole warps (the reduction shuffles)
+  constexpr int threads = RowsShape<NB>::THREADS;  // whole warps (the reduction shuffles)
   { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf);
     k_apply_rows<NB, S, A><<<apply_grid<NB>(ctx->ne), threads, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z,
                                                                        ctx->ne, sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
@@ -767,7 +778,7 @@ int apply_nb(fr_ctx* ctx, double* r, const double* scale, double* z, double* sum
 
 template <int NB, typename S, typename A>
 int solupdate_nbs(fr_ctx* ctx, double* x, cudaStream_t s) {
-  { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate<NB, S, A><<<apply_grid<NB>(ctx->ne), (256 / NB) * NB, 0, s>>>(
+  { ProfScope ps_(ctx, FR_KF_SOLUPDATE, s); k_solupdate<NB, S, A><<<apply_grid<NB>(ctx->ne), RowsShape<NB>::THREADS, 0, s>>>(
       reinterpret_cast<const S*>(ctx->blocks), ctx->V, ctx->ndof, ctx->gd.y, ctx->gd.k, x, ctx->ne); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
@@ -791,43 +802,71 @@ unsigned vec_grid(const fr_ctx* ctx, long long n) {
 }  // namespace
 
 template <int NB, typename T, typename S>
-int invert_nbts(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
+int invert_nbts(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n, cudaStream_t s) {
   constexpr size_t bytes = InvertLayout<NB, T>::BYTES;
   if constexpr (bytes > kSmemMax) {
     return set_error(ctx, FR_ERR_UNSUPPORTED, "element blocks of %d rows in this precision exceed shared memory", NB);
   }
   FRK_CUDA(ctx, cudaFuncSetAttribute(k_invert<NB, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)bytes));
-  { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, 2.0 * NB * NB * (double)NB * (double)ctx->ne);
-    k_invert<NB, T, S><<<(unsigned)ctx->ne, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, ctx->ne, dshift,
-                                                                               ctx->kerr); }
+  { ProfScope ps_(ctx, FR_KF_INVERT, s, 0.0, 2.0 * NB * NB * (double)NB * (double)n);
+    k_invert<NB, T, S><<<(unsigned)n, NB <= 64 ? 128 : 256, bytes, s>>>(mst, ctx->blocks, e0, dshift, ctx->kerr); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+
+// blocks larger than one SM's shared memory: FP32 Gauss-Jordan over a
+// cluster of two CTAs (gj_cluster.cuh), stored in S
+template <int NB, typename S>
+int invert_cluster_nbs(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n, cudaStream_t s) {
+  using Sh = gjcl::Shape<NB>;
+  static_assert(Sh::BYTES <= kSmemMax, "one CTA's half of the block fits shared memory");
+  auto kern = gjcl::k_invert_cluster<NB, S, StoreT<S>>;
+  FRK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::BYTES));
+  { ProfScope ps_(ctx, FR_KF_INVERT, s, 0.0, 2.0 * NB * NB * (double)NB * (double)n);
+    kern<<<(unsigned)(n * gjcl::CL), gjcl::THREADS, Sh::BYTES, s>>>(mst, reinterpret_cast<S*>(ctx->blocks), e0,
+                                                                   dshift); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }
 
 template <int NB>
-int invert_nb(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
+int invert_nb(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n, cudaStream_t s) {
   switch (ctx->opts.block_precision) {
-    case 1: return invert_nbts<NB, float, float>(ctx, mst, dshift, s);
-    case 2: return invert_nbts<NB, float, __nv_bfloat16>(ctx, mst, dshift, s);
-    default: return invert_nbts<NB, double, double>(ctx, mst, dshift, s);
+    case 1: return invert_nbts<NB, float, float>(ctx, mst, dshift, e0, n, s);
+    case 2: return invert_nbts<NB, float, __nv_bfloat16>(ctx, mst, dshift, e0, n, s);
+    default: return invert_nbts<NB, double, double>(ctx, mst, dshift, e0, n, s);
   }
 }
 
-int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
+int launch_block_invert_range(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n,
+                              cudaStream_t s) {
+  if (n <= 0) return FR_OK;
   switch (ctx->nb) {
-    case 36: return invert_nb<36>(ctx, mst, dshift, s);
-    case 40: return invert_nb<40>(ctx, mst, dshift, s);
-    case 135: return invert_nb<135>(ctx, mst, dshift, s);
-    case 64: return invert_nb<64>(ctx, mst, dshift, s);
-    case 100: return invert_nb<100>(ctx, mst, dshift, s);
-    case 144: return invert_nb<144>(ctx, mst, dshift, s);
-    case 196: return invert_nb<196>(ctx, mst, dshift, s);
+    case 36: return invert_nb<36>(ctx, mst, dshift, e0, n, s);
+    case 40: return invert_nb<40>(ctx, mst, dshift, e0, n, s);
+    case 135: return invert_nb<135>(ctx, mst, dshift, e0, n, s);
+    case 64: return invert_nb<64>(ctx, mst, dshift, e0, n, s);
+    case 100: return invert_nb<100>(ctx, mst, dshift, e0, n, s);
+    case 144: return invert_nb<144>(ctx, mst, dshift, e0, n, s);
+    case 196: return invert_nb<196>(ctx, mst, dshift, e0, n, s);
+    case 320:
+      switch (ctx->opts.block_precision) {
+        case 1: return invert_cluster_nbs<320, float>(ctx, mst, dshift, e0, n, s);
+        case 2: return invert_cluster_nbs<320, __nv_bfloat16>(ctx, mst, dshift, e0, n, s);
+        default: return set_error(ctx, FR_ERR_UNSUPPORTED, "320-row element blocks are stored in FP32 or BF16");
+      }
     default: return set_error(ctx, FR_ERR_UNSUPPORTED, "block size %d not compiled", ctx->nb);
   }
 }
 
+int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s) {
+  return launch_block_invert_range(ctx, mst, dshift, 0, ctx->ne, s);
+}
+
 int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s) {
+  if (ctx->blk_chunk < ctx->ne)
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "the staged blocks are kept per chunk only; form them again");
   FRK_TRY(launch_block_invert(ctx, ctx->mst, shift - ctx->staged_shift, s));
   ctx->blocks_valid = 1;
   return FR_OK;
@@ -866,6 +905,7 @@ int launch_block_apply(fr_ctx* ctx, double* r, const double* scale, double* z, d
     case 36: return apply_nb<36>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 40: return apply_nb<40>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 135: return apply_rows_nb<135>(ctx, r, scale, z, sumsq, done, s, with_eps);
+    case 320: return apply_rows_nb<320>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 64: return apply_nb<64>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 100: return apply_nb<100>(ctx, r, scale, z, sumsq, done, s, with_eps);
     case 144: return apply_nb<144>(ctx, r, scale, z, sumsq, done, s, with_eps);
@@ -885,6 +925,7 @@ int launch_solution_update(fr_ctx* ctx, double* x, cudaStream_t s) {
     case 36: return solupdate_nb<36>(ctx, x, s);
     case 40: return solupdate_nb<40>(ctx, x, s);
     case 135: return solupdate_nb<135>(ctx, x, s);
+    case 320: return solupdate_nb<320>(ctx, x, s);
     case 64: return solupdate_nb<64>(ctx, x, s);
     case 100: return solupdate_nb<100>(ctx, x, s);
     case 144: return solupdate_nb<144>(ctx, x, s);

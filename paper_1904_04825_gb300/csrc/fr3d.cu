@@ -21,11 +21,13 @@
 //    six faces' common fluxes (low faces its own, high faces the neighbours'
 //    low faces), then the output of the mode.  Both elements of a face read
 //    the same stored flux, so conservation holds to round-off.
-// Element-Jacobi columns (k3_cell mode 3, degrees 1 and 2): slot = (element,
+// Element-Jacobi columns (k3_cell mode 3, degrees 1 to 3): slot = (element,
 // column c), own state perturbed in DOF c by eps_c = beps (1 + |q_c|), own
 // traces recomputed in the kernel, neighbour traces frozen (trace buffer of
 // the unperturbed state); the slot forms its six faces' common data itself
-// and stages column c of shift I - J_ee for the inversion kernel.
+// and stages column c of shift I - J_ee for the inversion kernel.  Degree 3
+// (320 x 320 blocks, 800 KB each in FP64) stages and inverts the elements in
+// chunks, so the FP64 staging holds one chunk.
 #include "device.cuh"
 
 namespace frk {
@@ -45,6 +47,7 @@ struct F3Args {
   const double* eps2;
   const int* done;
   long long ne;
+  long long e0, nchunk;  // mode 3: the elements e0 .. e0 + nchunk - 1, columns staged from out[0]
   int nx, ny, nz;
   double gam, mu, kappa, shift, beps;
   Tables tab;
@@ -332,9 +335,9 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
   double* dq = d2 + 5 * NP;          // [6][N2][5] q_com - q_face
   double* fn = dq + 30 * N2;         // [6][N2][5] common total normal flux
   const long long slot = (long long)blockIdx.x * E + el;
-  const long long nslots = JAC ? a.ne * NB : a.ne;
+  const long long nslots = JAC ? a.nchunk * NB : a.ne;
   const bool active = el < E && slot < nslots;
-  const long long e = JAC ? slot / NB : slot;
+  const long long e = JAC ? a.e0 + slot / NB : slot;
   const int col = JAC ? (int)(slot % NB) : 0;
   double eps = 0.0, ieps = 0.0;
   if (PERTURB) {
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
     } else if (MODE == 3) {
       // column col of M = shift I - J_ee, staged column-major [col][row]
       const int row = v * NP + t;
-      a.out[(e * NB + col) * NB + row] = (row == col ? a.shift : 0.0) - (R - a.R0[o]) / ceps;
+      a.out[((e - a.e0) * NB + col) * NB + row] = (row == col ? a.shift : 0.0) - (R - a.R0[o]) / ceps;
     } else {
       const double zo = a.z[o];
       const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
@@ -558,6 +561,8 @@ F3Args make_args3(fr_ctx* ctx) {
   a.hy = ctx->hy;
   a.hz = ctx->hz;
   a.ne = ctx->ne;
+  a.e0 = 0;
+  a.nchunk = ctx->ne;
   a.nx = ctx->nx;
   a.ny = ctx->ny;
   a.nz = ctx->nz;
@@ -592,7 +597,7 @@ int f3_launch(fr_ctx* ctx, int mode, const F3Args& a, bool perturb_trace, cudaSt
     FRK_LAUNCHED(ctx);
     count_launch();  // the scope counted the trace kernel
     if (mode == 3) {
-      const long long g3 = (ctx->ne * NB + E - 1) / E;
+      const long long g3 = (a.nchunk * NB + E - 1) / E;
       k3_cell<P, 3><<<(unsigned)g3, E * NP, L::BYTES, s>>>(a);
     } else {
       const long long nf = ctx->ne * 3 * N2;
@@ -669,10 +674,30 @@ int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
   return f3_dispatch(ctx, mode, a, mode != 0, s, wb, wf);
 }
 
+namespace {
+// element-Jacobi columns of the elements a.e0 .. a.e0 + a.nchunk - 1; the
+// trace buffer already holds the unperturbed traces
+template <int P>
+int f3_columns(fr_ctx* ctx, const F3Args& a, cudaStream_t s) {
+  using L = CellLayout<P>;
+  constexpr int NP = L::NP, E = F3Slots<P>::E, NB = 5 * NP;
+  FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+  // one element residual per column: the own six faces' common data, counted
+  // like the residual with every face of the element
+  const double wf = (ns3d_residual_flops_per_element(P) + 3.0 * L::N2 * 245.0) * NB * (double)a.nchunk;
+  { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, wf);
+    k3_cell<P, 3><<<(unsigned)((a.nchunk * NB + E - 1) / E), E * NP, L::BYTES, s>>>(a); }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+}  // namespace
+
 int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
-  if (ctx->p > 2 || !ctx->mst)
-    return set_error(ctx, FR_ERR_UNSUPPORTED, "3D element blocks are built for degrees 1 and 2");
-  // R0 of the element-local residuals = R(U) with the same (unperturbed) traces
+  if (ctx->p > 3 || !ctx->mst || ctx->blk_chunk < 1)
+    return set_error(ctx, FR_ERR_UNSUPPORTED, "3D element blocks are built for degrees 1 to 3");
+  // R0 of the element-local residuals = R(U); it leaves the unperturbed
+  // traces in the trace buffer, which the columns read as the frozen
+  // neighbour traces
   F3Args a = make_args3(ctx);
   a.U = U;
   a.out = ctx->rloc;
@@ -680,8 +705,17 @@ int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
   a.R0 = ctx->rloc;
   a.out = ctx->mst;
   a.shift = shift;
-  FRK_TRY(f3_dispatch(ctx, 3, a, false, s, 0.0, 0.0));
-  return launch_block_invert(ctx, ctx->mst, 0.0, s);
+  for (long long e0 = 0; e0 < ctx->ne; e0 += ctx->blk_chunk) {
+    a.e0 = e0;
+    a.nchunk = ctx->ne - e0 < ctx->blk_chunk ? ctx->ne - e0 : ctx->blk_chunk;
+    switch (ctx->p) {
+      case 1: FRK_TRY(f3_columns<1>(ctx, a, s)); break;
+      case 2: FRK_TRY(f3_columns<2>(ctx, a, s)); break;
+      default: FRK_TRY(f3_columns<3>(ctx, a, s)); break;
+    }
+    FRK_TRY(launch_block_invert_range(ctx, ctx->mst, 0.0, e0, a.nchunk, s));
+  }
+  return FR_OK;
 }
 
 int launch_f3_dissipation(fr_ctx* ctx, const double* U, double* out, cudaStream_t s) {

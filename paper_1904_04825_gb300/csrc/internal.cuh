@@ -16,6 +16,7 @@ constexpr int kThreads = 256;     // default block size of the vector kernels
 constexpr int kMaxVec = 64;       // largest Krylov basis slice handled per call (m_max + 1)
 constexpr int kVecBlocks = 456;   // default grid of the streaming vector kernels (3 x 152 SMs)
 constexpr int kRedBlocks = 4096;  // capacity of the partial-sum buffer (blocks)
+constexpr long long kStageChunk3 = 4096;  // elements per FP64 staging chunk of 3D degree-3 blocks
 
 // 1D tables of Sec. 3 on Gauss-Legendre points, passed to kernels by value.
 //   Dt[i][k] = D_ik - g_L'(xi_i) l_k(-1) - g_R'(xi_i) l_k(+1)
@@ -133,6 +134,7 @@ struct fr_ctx {
   double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
+  long long blk_chunk = 0;   // elements whose staged blocks mst holds at once (ne unless staged in chunks)
   int hist_row = 0;          // ROW order of the last step if its stage solutions are intact
   fr_mlp* guess = nullptr;   // learned initial-guess model (ROW stages), or null
   float* gfeat = nullptr;    // [ne][3 nb] features for the guess
@@ -295,6 +297,9 @@ int launch_vortex_error(fr_ctx* ctx, const double* U, const fr_vortex* vx, doubl
 // blocks.cu: invert staged FP64 blocks (column-major M[c][row], dshift added to
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
+// invert the staged blocks of elements e0 .. e0 + n - 1 (mst holds them from its start)
+int launch_block_invert_range(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n,
+                              cudaStream_t s);
 int launch_block_reshift(fr_ctx* ctx, double shift, cudaStream_t s);
 // guess.cu (B_GUESS_R: stepper buffer free while a stage solve starts)
 constexpr int B_GUESS_R = 3;

@@ -216,7 +216,14 @@ int ptc(fr_ctx* ctx, const double* cst, double omega_dt, double dt, double* q, d
         FRK_TRY(launch_block_factor(ctx, q, shift, s));
         formed_k = k;
       } else if (ctx->opts.precond_refresh != 2 && blocks_shift != shift) {
-        FRK_TRY(launch_block_reshift(ctx, shift, s));
+        if (ctx->blk_chunk < ctx->ne) {
+          // staged blocks are kept for one chunk of elements only: a new
+          // shift forms the blocks again, at the current iterate
+          FRK_TRY(launch_block_factor(ctx, q, shift, s));
+          formed_k = k;
+        } else {
+          FRK_TRY(launch_block_reshift(ctx, shift, s));
+        }
       }
       blocks_shift = shift;  // precond_refresh = 2 keeps the stage's first blocks and shift
     }

@@ -1,6 +1,6 @@
 """3D hexahedral Navier-Stokes path on the GPU against the FP64 oracle
 (oracle/fr3d.py): residual (Euler and BR2, degrees 1-4, ragged element
-tiles), FD operator, element-Jacobi blocks (degrees 1, 2), ROW / ESDIRK /
+tiles), FD operator, element-Jacobi blocks (degrees 1-3), ROW / ESDIRK /
 SSPRK3 steps, the Taylor-Green dissipation rate, and properties of the
 64^3 p = 3 Taylor-Green workload.  Tolerances as in test_gpu_parity.py."""
 import numpy as np
@@ -102,9 +102,11 @@ def test_jv_matches_oracle(fr, p):
     assert _rel(y.cpu().numpy(), yo) < 1e-6
 
 
-@pytest.mark.parametrize("p,prec,tol", [(1, 0, 1e-6), (1, 2, 3e-2), (2, 0, 1e-6), (2, 1, 1e-4)])
+@pytest.mark.parametrize("p,prec,tol", [(1, 0, 1e-6), (1, 2, 3e-2), (2, 0, 1e-6), (2, 1, 1e-4), (3, 1, 1e-4),
+                                        (3, 2, 3e-2)])
 def test_element_jacobi_matches_oracle(fr, p, prec, tol):
-    """Blocks of 40 rows (bulk-copy apply) and 135 rows (row apply)."""
+    """Blocks of 40 rows (bulk-copy apply), 135 rows (row apply) and 320
+    rows (FP32 Gauss-Jordan over a two-CTA cluster, row apply)."""
     edges, U0 = _random_case(p, dims=(2, 4, 2), seed=13)
     gas = Gas3D(mu=0.03, prandtl=0.71)
     prob = Problem3D(Mesh3D(*edges), p, gas)
@@ -116,6 +118,29 @@ def test_element_jacobi_matches_oracle(fr, p, prec, tol):
     fr.ejacobi_apply(ctx, _t(r0), z)
     zo = ElementJacobi(element_blocks(prob, U0, shift))(r0)
     assert _rel(z.cpu().numpy(), zo) < tol
+
+
+def test_degree3_blocks_staged_in_chunks(fr):
+    """320-row blocks staged and inverted a few elements at a time (ragged
+    last chunk) give the same preconditioner, bit for bit, as one chunk."""
+    p = 3
+    edges, U0 = _random_case(p, dims=(2, 4, 2), seed=17)
+    shift = 25.0
+    r0 = _t(S.random_vector(U0.shape, 9))
+    zs = []
+    for chunk in (None, 5, 1):
+        ctx = fr.Context3D(*edges, p, _opts(fr, 0.03, precond=1, block_precision=1))
+        if chunk:
+            fr.fr_set_block_chunk(ctx, chunk)
+        fr.ejacobi_factor(ctx, _t(U0), None, shift)
+        z = ctx.empty()
+        fr.ejacobi_apply(ctx, r0, z)
+        zs.append(z.cpu().numpy())
+        ctx.close()
+    assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2])
+    with pytest.raises(fr.FrError):
+        ctx = fr.Context3D(*edges, p, _opts(fr, 0.03, precond=1, block_precision=1))
+        fr.fr_set_block_chunk(ctx, 17)      # more than the 16 elements
 
 
 def test_ssprk3_steps_match_oracle(fr):
@@ -132,14 +157,16 @@ def test_ssprk3_steps_match_oracle(fr):
     assert _rel(U.cpu().numpy(), Uo) < 1e-12
 
 
-@pytest.mark.parametrize("p,precond", [(1, 1), (2, 1), (3, 0)])
+@pytest.mark.parametrize("p,precond", [(1, 1), (2, 1), (3, 0), (3, 1)])
 def test_row3_step_matches_oracle(fr, p, precond):
-    n = 4 if p < 3 else 3
+    n = 4 if p < 3 else (2 if precond else 3)   # the oracle's blocks need even nx, ny, nz
     edges, U0 = _tgv_case(n, p)
     gas = Gas3D(mu=TG.mu, prandtl=TG.prandtl)
     prob = Problem3D(Mesh3D(*edges), p, gas)
     dt = 0.1
-    ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=precond, tol_lin=1e-12, gmres_max_restarts=200))
+    prec = 1 if p == 3 and precond else 0       # 320-row blocks are stored in FP32
+    ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=precond, block_precision=prec, tol_lin=1e-12,
+                                        gmres_max_restarts=200))
     U = _t(U0)
     st = fr.step_row(ctx, 3, dt, U)
     Uo, so = o_row(prob, ROW[3](), dt, U0, SolverOpts(tol_lin=1e-12, m=30, max_restarts=200,
@@ -155,6 +182,27 @@ def test_esdirk3_step_matches_oracle(fr):
     prob = Problem3D(Mesh3D(*edges), p, gas)
     dt = 0.1
     ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=1, gmres_max_restarts=60))
+    po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
+    U = _t(U0)
+    st = fr.step_esdirk(ctx, 3, dt, U, po)
+    Uo, so = o_esdirk(prob, ESDIRK[3](), dt, U0, PtcOpts(tol_nl=1e-12, tol_lin=1e-3),
+                      SolverOpts(m=30, max_restarts=60))
+    assert st.converged and so.converged
+    assert _rel(U.cpu().numpy(), Uo) < 1e-9
+
+
+def test_esdirk3_degree3_step_with_chunked_blocks_matches_oracle(fr):
+    """ESDIRK3 with 320-row FP32 blocks staged three elements at a time: a
+    new pseudo-time shift forms the blocks again at the current iterate
+    (the oracle re-inverts the stage's first blocks); both converge to the
+    same stage solutions."""
+    p = 3
+    edges, U0 = _tgv_case(2, p)
+    gas = Gas3D(mu=TG.mu, prandtl=TG.prandtl)
+    prob = Problem3D(Mesh3D(*edges), p, gas)
+    dt = 0.1
+    ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=1, block_precision=1, gmres_max_restarts=60))
+    fr.fr_set_block_chunk(ctx, 3)
     po = fr.default_ptc_opts(tol_nl=1e-12, tol_lin=1e-3)
     U = _t(U0)
     st = fr.step_esdirk(ctx, 3, dt, U, po)
@@ -188,6 +236,8 @@ def test_unsupported_3d_options_rejected(fr):
             fr.Context3D(*edges, 3, _opts(fr, 0.01, **kw))
     with pytest.raises(fr.FrError):
         fr.Context3D(*edges, 5, _opts(fr, 0.01))
+    with pytest.raises(fr.FrError):
+        fr.Context3D(*edges, 4, _opts(fr, 0.01, precond=1, block_precision=1))
     ctx2 = fr.Context(*S.uniform_mesh(4), 2)
     with pytest.raises(fr.FrError):
         fr.fr_dissipation_rate(ctx2, ctx2.empty())

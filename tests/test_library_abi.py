@@ -93,7 +93,8 @@ def test_3d_argument_checks_without_gpu(libpath):
         return fr.lib.fr_ctx_create_3d(ctypes.byref(d), p, ctypes.byref(o), ctypes.byref(h))
     assert create(desc, 5, precond=0) == fr.FR_ERR_UNSUPPORTED          # degrees 1-4
     assert create(desc, 0, precond=0) == fr.FR_ERR_UNSUPPORTED
-    assert create(desc, 3) == fr.FR_ERR_UNSUPPORTED                      # 320-row blocks not built
+    assert create(desc, 3) == fr.FR_ERR_UNSUPPORTED                      # 320-row blocks: FP32/BF16 only
+    assert create(desc, 4, block_precision=1) == fr.FR_ERR_UNSUPPORTED   # 625-row blocks not built
     assert create(desc, 2, riemann=1) == fr.FR_ERR_UNSUPPORTED           # Rusanov only
     assert create(desc, 2, jv_precision=1) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, guess=2) == fr.FR_ERR_UNSUPPORTED
@@ -107,6 +108,7 @@ def test_3d_argument_checks_without_gpu(libpath):
     assert fr.lib.fr_ctx_create_3d(None, 2, None, ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
     out = (ctypes.c_double * 3)()
     assert fr.lib.fr_dissipation_rate(None, None, 1.0, out, None) == fr.FR_ERR_INVALID_ARG
+    assert fr.lib.fr_set_block_chunk(None, 1) == fr.FR_ERR_INVALID_ARG
 
 
 def test_wrong_length_tensors_rejected_before_any_library_call(libpath):
