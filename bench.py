@@ -309,9 +309,10 @@ def our_arm(args):
         del X, Y, Z
         dt, wall = (args.dt or tg.t_c / 25.0), False
         opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=args.gmres_m, m_max=args.gmres_m, gmres_max_restarts=20,
-                               block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 3 else 0)
+                               block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 3 else 0,
+                               block_columns=1 if args.block_columns == "fp32" and p <= 3 else 0)
         wl = (f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}-gmres{args.gmres_m}"
-              + ("" if p <= 3 else "-noprecond"))
+              + ("" if p <= 3 else "-noprecond") + ("-fp32columns" if args.block_columns == "fp32" else ""))
     else:
         ch = S.Channel()
         cnx, cny = args.nx or 256, args.ny or 128
@@ -632,6 +633,110 @@ def t_end_arm(args):
     return 0
 
 
+def tgv_t_end_arm(args):
+    """Taylor-Green vortex to t_end (Sec. 5, the time-integrator study): the
+    kinetic-energy dissipation rate eps = eps1 + eps3 (mu_v = 0) after every
+    step of each implicit scheme against an SSPRK3 reference with
+    dt = 2e-4 t_c on the same mesh and degree, and Error(eps) = RMS over the
+    steps of eps_n - eps_ref,n; wall time (host waits included) and GMRES
+    iterations per run.  ROW at tol_rel,linear = 1e-6, ESDIRK/BDF2 at
+    tol_rel,nonlinear = 1e-6 with tol_rel,linear = 1e-1, GMRES(30),
+    element-Jacobi blocks (FP32 storage at p = 3)."""
+    import numpy as np
+    import torch
+    import paper_1904_04825_gb300 as fr
+    import synthetic as S
+
+    torch.cuda.set_device(0)
+    tg = S.TaylorGreen()
+    p, n3 = args.p or 3, args.nx or 16
+    edges = S.uniform_mesh3d(n3)
+    X, Y, Z = S.point_coords3d(*edges, p)
+    U0 = torch.from_numpy(tg.state(X, Y, Z)).cuda()
+    del X, Y, Z
+    t_end = args.t_end * tg.t_c
+    dt_ref = 2e-4 * tg.t_c
+    divs = [int(x) for x in args.tgv_dt_divs.split(",")]
+    dts = [tg.t_c / d for d in divs]
+    n_ref = int(round(t_end / dt_ref))
+    strides = [int(round(dt / dt_ref)) for dt in dts]
+    for dt, st_ in zip(dts, strides):
+        if abs(st_ * dt_ref - dt) > 1e-9 * dt:
+            raise SystemExit(f"dt = {dt} is not a multiple of the reference step {dt_ref}")
+    sample = math.gcd(*strides)
+    gas = dict(mu=tg.mu, prandtl=tg.prandtl)
+
+    def eps_of(ctx, U):
+        e1, e3, _ = fr.fr_dissipation_rate(ctx, U, tg.rho0)
+        return e1 + e3
+
+    # reference: SSPRK3, eps sampled every `sample` steps
+    ctx = fr.Context3D(*edges, p, fr.default_opts(precond=0, **gas))
+    U = U0.clone()
+    ref = {0: eps_of(ctx, U)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(1, n_ref + 1):
+        fr.step_ssprk3(ctx, dt_ref, U)
+        if k % sample == 0:
+            ref[k] = eps_of(ctx, U)
+    torch.cuda.synchronize()
+    ref_wall = time.perf_counter() - t0
+    ctx.close()
+    kmax = max(ref, key=ref.get)
+    out = {"workload": f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-to-{args.t_end:g}tc", "ndof": 5 * (p + 1) ** 3 * n3 ** 3,
+           "block_columns": args.block_columns,
+           "reference": {"scheme": "SSPRK3", "dt": dt_ref, "steps": n_ref, "wall_s": ref_wall,
+                         "eps_max": ref[kmax], "t_of_eps_max": kmax * dt_ref,
+                         "eps_at": {f"{t:g}": ref[int(round(t * tg.t_c / dt_ref))]
+                                    for t in (2.0, 4.0, 6.0, 8.0, 9.0, 10.0) if t <= args.t_end}},
+           "runs": []}
+    prec = 1 if p == 3 else 0
+    schemes = (args.tgv_schemes or args.scheme).split(",")
+    for dt, stride in zip(dts, strides):
+        nsteps = n_ref // stride
+        for sch in schemes:
+            kind, order = sch[:-1], int(sch[-1])
+            ctx = fr.Context3D(*edges, p, fr.default_opts(precond=1, block_precision=prec, tol_lin=1e-6 if kind == "row" else 1e-1,
+                                                           gmres_m=30, m_max=30, gmres_max_restarts=20,
+                                                           block_columns=1 if args.block_columns == "fp32" and prec else 0,
+                                                           **gas))
+            ptc = fr.default_ptc_opts(tol_nl=1e-6, tol_lin=1e-1)
+            U = U0.clone()
+            Uprev = torch.empty_like(U)
+            errs, iters, bad, failed = [], 0, 0, None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(1, nsteps + 1):
+                try:
+                    if kind == "row":
+                        st = fr.step_row(ctx, order, dt, U)
+                    elif kind == "esdirk":
+                        st = fr.step_esdirk(ctx, order, dt, U, ptc)
+                    else:
+                        st = fr.step_bdf2(ctx, dt, U, Uprev, k == 1, ptc)
+                except fr.FrError as e:
+                    failed = {"step": k, "error": str(e)}
+                    break
+                iters += st.gmres_iters
+                bad += 0 if st.converged else 1
+                errs.append(eps_of(ctx, U) - ref[k * stride])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            run = {"scheme": sch.upper(), "dt_over_tc": dt / tg.t_c, "steps": nsteps, "wall_s": wall,
+                   "gmres_iters": iters, "unconverged_steps": bad,
+                   "error_eps": float(np.sqrt(np.mean(np.square(errs)))) if errs else None,
+                   "eps_minus_ref_at": {f"{t:g}": errs[int(round(t * tg.t_c / dt)) - 1]
+                                        for t in (8.0, 10.0) if t <= args.t_end and not failed}}
+            if failed:
+                run["failed"] = failed
+            out["runs"].append(run)
+            ctx.close()
+            print(json.dumps(run), flush=True)
+    print(json.dumps(out))
+    return 0
+
+
 def kernel_arm(args):
     """Time one kernel family alone on the full-size inputs (for per-kernel
     numbers and as a short, clean target for ncu captures)."""
@@ -651,10 +756,12 @@ def kernel_arm(args):
         X, Y, Z = S.point_coords3d(*edges, p3)
         U = torch.from_numpy(tg.state(X, Y, Z)).cuda()
         del X, Y, Z
-        if p3 == 3 and prec == 0:
+        blocks = args.kernel in ("factor", "apply") and p3 <= 3   # allocate the blocks only where timed
+        if blocks and p3 == 3 and prec == 0:
             prec, args.block_precision = 1, "fp32"   # 320-row blocks are stored in FP32 or BF16
         ctx = fr.Context3D(*edges, p3, fr.default_opts(block_precision=prec, mu=tg.mu, prandtl=tg.prandtl,
-                                                        precond=1 if p3 <= 3 else 0, m_max=4, gmres_m=4))
+                                                        precond=1 if blocks else 0, m_max=4, gmres_m=4,
+                                                        block_columns=1 if blocks and args.block_columns == "fp32" else 0))
     else:
         xe, ye = S.uniform_mesh(NX)
         X, Y = S.point_coords(xe, ye, P)
@@ -1095,6 +1202,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--block-precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="element-Jacobi block precision (fp64 = the plain method)")
+    ap.add_argument("--block-columns", choices=["fp64", "fp32"], default="fp64",
+                    help="arithmetic of the FD element-block columns (fp32: 3D with fp32/bf16 blocks)")
     ap.add_argument("--riemann", choices=["rusanov", "roe"], default="rusanov",
                     help="common inviscid flux (roe: the paper's; Euler only)")
     ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
@@ -1111,7 +1220,8 @@ def main():
                     choices=["row2", "row3", "row4", "esdirk2", "esdirk3", "esdirk4", "bdf2", "ssprk3"])
     ap.add_argument("--dt", type=float, default=None)
     ap.add_argument("--t-end", type=float, default=None,
-                    help="vortex only: run to t_end, report time-to-t_end and E(rho)")
+                    help="vortex: run to t_end, report time-to-t_end and E(rho); tgv: run to t_end t_c, "
+                         "report Error(eps) against an SSPRK3 reference")
     ap.add_argument("--cfl", type=float, default=13.6)
     ap.add_argument("--tol", type=float, default=1e-6,
                     help="--t-end: tol_rel,linear for ROW, tol_rel,nonlinear for ESDIRK/BDF2")
@@ -1126,6 +1236,10 @@ def main():
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None, help="--workload channel: cells across the channel")
     ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--tgv-schemes", default=None,
+                    help="--workload tgv --t-end: comma-separated schemes (default --scheme)")
+    ap.add_argument("--tgv-dt-divs", default="25",
+                    help="--workload tgv --t-end: time steps t_c / d for these d (comma-separated)")
     args = ap.parse_args()
     if args.scheme is None and args.workload != "batch":
         args.scheme = "row3"
@@ -1135,6 +1249,8 @@ def main():
         return reference_arm(args)
     if args.kernel:
         return kernel_arm(args)
+    if args.t_end and args.workload == "tgv":
+        return tgv_t_end_arm(args)
     if args.t_end:
         return t_end_arm(args)
     if args.workload == "batch":

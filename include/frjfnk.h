@@ -111,6 +111,15 @@ typedef struct fr_opts {
   int riemann;           /* common inviscid flux at the faces (Sec. 3, Eq. invis_com):
                             0 = Rusanov (default), 1 = Roe without entropy fix (the
                             paper's); Euler residual only */
+  int block_columns;     /* arithmetic of the FD columns of J_ee (Sec. 4.5):
+                            0 = FP64 (default); 1 = FP32, with the step
+                            eps_j = max(block_eps_rel, 2^-12) (1 + |U_j|) (about
+                            the square root of FP32's unit roundoff) divided by
+                            the step the FP32 rounding actually took, and R(U)
+                            of each element formed by the same FP32 arithmetic.
+                            The columns then carry a relative error of ~1e-3,
+                            which changes only the preconditioner.  3D contexts
+                            with block_precision 1 or 2 only */
 } fr_opts;
 
 /* Pseudo-transient continuation options (Sec. 4.4; fill with

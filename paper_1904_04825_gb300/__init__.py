@@ -67,7 +67,8 @@ class fr_opts(ctypes.Structure):
                 ("mu", ctypes.c_double), ("prandtl", ctypes.c_double),
                 ("body_force_x", ctypes.c_double), ("wall_temperature", ctypes.c_double),
                 ("block_precision", ctypes.c_int), ("precond_refresh", ctypes.c_int),
-                ("guess", ctypes.c_int), ("jv_precision", ctypes.c_int), ("riemann", ctypes.c_int)]
+                ("guess", ctypes.c_int), ("jv_precision", ctypes.c_int), ("riemann", ctypes.c_int),
+                ("block_columns", ctypes.c_int)]
 
 
 class fr_ptc_opts(ctypes.Structure):

@@ -39,6 +39,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->lin_fx);
   cudaFree(c->lin_fy);
   cudaFree(c->rloc);
+  cudaFree(c->r0f);
   cudaFree(c->gfeat);
   for (double* p : c->bhist) cudaFree(p);
   cudaFree(c->gout);
@@ -213,6 +214,7 @@ int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
     }
     FRK_TRY(dalloc(c, &c->mst, (size_t)c->blk_chunk * nb2));
     FRK_TRY(dalloc(c, &c->rloc, n));
+    if (o->block_columns == 1) FRK_TRY(dalloc(c, &c->r0f, (size_t)c->blk_chunk * c->nb));
   }
   FRK_TRY(dalloc(c, &c->diss, 4));
   FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));
@@ -362,6 +364,7 @@ extern "C" void fr_default_opts(fr_opts* o) {
   o->guess = 0;
   o->jv_precision = 0;
   o->riemann = 0;
+  o->block_columns = 0;
 }
 
 extern "C" void fr_default_ptc_opts(fr_ptc_opts* o) {
@@ -392,6 +395,8 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, int p, const fr_opts* opt
       o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
     return FR_ERR_INVALID_ARG;
   if (o.riemann == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
+  if (o.block_columns < 0 || o.block_columns > 1) return FR_ERR_INVALID_ARG;
+  if (o.block_columns == 1) return FR_ERR_UNSUPPORTED;  // FP32 columns: 3D contexts only
   if (o.jv_precision == 1 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;  // Euler residual only
   // degrees 5 and 6: Euler residual only; p = 6 FP64 blocks (196 x 196) exceed shared memory
   if (p > 4 && (o.mu > 0.0 || mesh->wall_y)) return FR_ERR_UNSUPPORTED;
@@ -431,6 +436,8 @@ extern "C" int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts
   // for p <= 3 (5 (p+1)^3 = 40, 135 or 320 rows; 320-row blocks in FP32 or
   // BF16 only), no learned guess
   if (o.riemann != 0 || o.jv_precision != 0 || o.guess == 2 || o.body_force_x != 0.0) return FR_ERR_UNSUPPORTED;
+  if (o.block_columns < 0 || o.block_columns > 1) return FR_ERR_INVALID_ARG;
+  if (o.block_columns == 1 && (!o.precond || o.block_precision == 0)) return FR_ERR_UNSUPPORTED;
   if (o.precond && (p > 3 || (p == 3 && o.block_precision == 0))) return FR_ERR_UNSUPPORTED;
   for (int i = 0; i < mesh->nx; ++i)
     if (!(mesh->x_edges[i + 1] > mesh->x_edges[i])) return FR_ERR_INVALID_ARG;

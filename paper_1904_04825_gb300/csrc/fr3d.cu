@@ -48,6 +48,8 @@ struct F3Args {
   const int* done;
   long long ne;
   long long e0, nchunk;  // mode 3: the elements e0 .. e0 + nchunk - 1, columns staged from out[0]
+  float* r0f;            // mode 3 in FP32: element-local R(U) of the chunk, [nchunk][NB]
+  int r0_pass;           // mode 3 in FP32: 1 = write r0f (one unperturbed slot per element)
   int nx, ny, nz;
   double gam, mu, kappa, shift, beps;
   Tables tab;
@@ -60,17 +62,19 @@ template <> struct F3Slots<2> { static constexpr int E = 8; };
 template <> struct F3Slots<3> { static constexpr int E = 4; };
 template <> struct F3Slots<4> { static constexpr int E = 2; };
 
-// doubles of dynamic shared memory per element of k3_cell: state, three
-// derivative / flux arrays, q_com - q_face and f_n on the 6 N^2 face points
-template <int P> struct CellLayout {
+// values (of type T) of dynamic shared memory per element of k3_cell: state,
+// three derivative / flux arrays, q_com - q_face and f_n on the 6 N^2 face points
+template <int P, typename T = double> struct CellLayout {
   static constexpr int N = P + 1, N2 = N * N, NP = N2 * N;
   static constexpr int PER = 20 * NP + 60 * N2;
-  static constexpr size_t BYTES = (size_t)F3Slots<P>::E * PER * sizeof(double);
+  static constexpr size_t BYTES = (size_t)F3Slots<P>::E * PER * sizeof(T);
 };
 
-template <int N>
-__device__ __forceinline__ double tsum3(const double* x, int stride, const double* c) {
-  double s = c[0] * x[0];
+// The pointwise and face functions below take the arithmetic type T: double
+// for R(U) and A z, float for the FP32 element-Jacobi columns.
+template <int N, typename T>
+__device__ __forceinline__ T tsum3(const T* x, int stride, const T* c) {
+  T s = c[0] * x[0];
 #pragma unroll
   for (int l = 1; l < N; ++l) s = fma(c[l], x[l * stride], s);
   return s;
@@ -87,53 +91,54 @@ __device__ __forceinline__ void line_of(int d, int f, int* off, int* stride) {
 
 // inviscid flux along direction d and |v_d| + c (selects instead of indexing
 // by d, so the arrays stay in registers when d is not a constant)
-__device__ __forceinline__ double flux3(const double q[5], int d, double gam, double f[5]) {
-  const double ri = 1.0 / q[0];
-  const double md = d == 0 ? q[1] : (d == 1 ? q[2] : q[3]);
-  const double vd = md * ri;
-  const double p = (gam - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ri);
+template <typename T>
+__device__ __forceinline__ T flux3(const T q[5], int d, T gam, T f[5]) {
+  const T ri = T(1) / q[0];
+  const T md = d == 0 ? q[1] : (d == 1 ? q[2] : q[3]);
+  const T vd = md * ri;
+  const T p = (gam - T(1)) * (q[4] - T(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ri);
   f[0] = md;
-  f[1] = fma(q[1], vd, d == 0 ? p : 0.0);
-  f[2] = fma(q[2], vd, d == 1 ? p : 0.0);
-  f[3] = fma(q[3], vd, d == 2 ? p : 0.0);
+  f[1] = fma(q[1], vd, d == 0 ? p : T(0));
+  f[2] = fma(q[2], vd, d == 1 ? p : T(0));
+  f[3] = fma(q[3], vd, d == 2 ? p : T(0));
   f[4] = vd * (q[4] + p);
   return fabs(vd) + sqrt(gam * p * ri);
 }
 
-__device__ __forceinline__ void rusanov3(const double qm[5], const double qp[5], int d, double gam,
-                                         double fn[5]) {
-  double fm[5], fp[5];
-  const double lm = flux3(qm, d, gam, fm);
-  const double lp = flux3(qp, d, gam, fp);
-  const double lam = fmax(lm, lp);
+template <typename T>
+__device__ __forceinline__ void rusanov3(const T qm[5], const T qp[5], int d, T gam, T fn[5]) {
+  T fm[5], fp[5];
+  const T lm = flux3(qm, d, gam, fm);
+  const T lp = flux3(qp, d, gam, fp);
+  const T lam = fmax(lm, lp);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) fn[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * lam * (qp[v] - qm[v]);
+  for (int v = 0; v < 5; ++v) fn[v] = T(0.5) * (fm[v] + fp[v]) - T(0.5) * lam * (qp[v] - qm[v]);
 }
 
 // viscous fluxes along the directions d with mask bit d set, from q and the
 // gradients g[c][v] (c: direction); R = 1
-__device__ __forceinline__ void visc3(const double q[5], const double g[3][5], double gam, double mu,
-                                      double kappa, int mask, double fv[3][5]) {
-  const double ri = 1.0 / q[0];
-  const double vel[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-  const double e = q[4] * ri;
-  double dv[3][3];  // dv[c][m] = d v_m / d x_c
-  double dT[3];
+template <typename T>
+__device__ __forceinline__ void visc3(const T q[5], const T g[3][5], T gam, T mu, T kappa, int mask, T fv[3][5]) {
+  const T ri = T(1) / q[0];
+  const T vel[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  const T e = q[4] * ri;
+  T dv[3][3];  // dv[c][m] = d v_m / d x_c
+  T dT[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) dv[c][m] = (g[c][1 + m] - vel[m] * g[c][0]) * ri;
-    dT[c] = (gam - 1.0) * ((g[c][4] - e * g[c][0]) * ri - (vel[0] * dv[c][0] + vel[1] * dv[c][1] + vel[2] * dv[c][2]));
+    dT[c] = (gam - T(1)) * ((g[c][4] - e * g[c][0]) * ri - (vel[0] * dv[c][0] + vel[1] * dv[c][1] + vel[2] * dv[c][2]));
   }
-  const double div = dv[0][0] + dv[1][1] + dv[2][2];
+  const T div = dv[0][0] + dv[1][1] + dv[2][2];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (!(mask & (1 << d))) continue;
-    double tau[3];
+    T tau[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) tau[m] = mu * (dv[d][m] + dv[m][d]);
-    tau[d] -= (2.0 / 3.0) * mu * div;
-    fv[d][0] = 0.0;
+    tau[d] -= T(2.0 / 3.0) * mu * div;
+    fv[d][0] = T(0);
     fv[d][1] = tau[0];
     fv[d][2] = tau[1];
     fv[d][3] = tau[2];
@@ -144,26 +149,26 @@ __device__ __forceinline__ void visc3(const double q[5], const double g[3][5], d
 // common solution and total normal flux on a face normal to d from the (-)
 // and (+) traces m, pp ([v][q, q_x, q_y, q_z]); hm, hp: the two elements'
 // sizes along d; cbr2 = (P+1)(P+2)/2
-__device__ __forceinline__ void common3(const double m[5][4], const double pp[5][4], int d, double hm,
-                                        double hp, double cbr2, const F3Args& a, double qc[5],
-                                        double fn[5]) {
-  double qm[5], qp[5], g[3][5];
+template <typename T>
+__device__ __forceinline__ void common3(const T m[5][4], const T pp[5][4], int d, T hm, T hp, T cbr2,
+                                        const F3Args& a, T qc[5], T fn[5]) {
+  T qm[5], qp[5], g[3][5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qm[v] = m[v][0];
     qp[v] = pp[v][0];
-    qc[v] = 0.5 * (qm[v] + qp[v]);
+    qc[v] = T(0.5) * (qm[v] + qp[v]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) g[c][v] = 0.5 * (m[v][1 + c] + pp[v][1 + c]);
-    const double rm = (2.0 / hm) * cbr2 * (qc[v] - qm[v]);   // lifting of the (-) element
-    const double rp = -(2.0 / hp) * cbr2 * (qc[v] - qp[v]);  // lifting of the (+) element
+    for (int c = 0; c < 3; ++c) g[c][v] = T(0.5) * (m[v][1 + c] + pp[v][1 + c]);
+    const T rm = (T(2) / hm) * cbr2 * (qc[v] - qm[v]);   // lifting of the (-) element
+    const T rp = -(T(2) / hp) * cbr2 * (qc[v] - qp[v]);  // lifting of the (+) element
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      if (c == d) g[c][v] = 0.5 * ((m[v][1 + c] + rm) + (pp[v][1 + c] + rp));
+      if (c == d) g[c][v] = T(0.5) * ((m[v][1 + c] + rm) + (pp[v][1 + c] + rp));
   }
-  double fi[5], fv[3][5];
-  rusanov3(qm, qp, d, a.gam, fi);
-  visc3(qc, g, a.gam, a.mu, a.kappa, 1 << d, fv);
+  T fi[5], fv[3][5];
+  rusanov3(qm, qp, d, (T)a.gam, fi);
+  visc3(qc, g, (T)a.gam, (T)a.mu, (T)a.kappa, 1 << d, fv);
 #pragma unroll
   for (int v = 0; v < 5; ++v) fn[v] = fi[v] - (d == 0 ? fv[0][v] : (d == 1 ? fv[1][v] : fv[2][v]));
 }
@@ -189,15 +194,14 @@ __device__ __forceinline__ long long neighbour(int ix, int iy, int iz, int face,
 }
 
 // reference derivatives of the 5 variables at point t of one element
-template <int N>
-__device__ __forceinline__ void ref_derivs(const double* sq, const double (*sD)[N], int t, double* d0,
-                                           double* d1, double* d2) {
+template <int N, typename T>
+__device__ __forceinline__ void ref_derivs(const T* sq, const T (*sD)[N], int t, T* d0, T* d1, T* d2) {
   constexpr int N2 = N * N, NP = N2 * N;
   const int i = t % N, j = (t / N) % N, k = t / N2;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double* x = sq + v * NP;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const T* x = sq + v * NP;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
     for (int l = 0; l < N; ++l) {
       a0 = fma(sD[i][l], x[l + N * j + N2 * k], a0);
@@ -211,14 +215,13 @@ __device__ __forceinline__ void ref_derivs(const double* sq, const double (*sD)[
 }
 
 // full trace (q and physical gradient) of face point (face, f)
-template <int N>
-__device__ __forceinline__ void own_trace(const double* sq, const double* d0, const double* d1,
-                                          const double* d2, int face, int f, const double s[3],
-                                          const double* lm, const double* lp, double o[5][4]) {
+template <int N, typename T>
+__device__ __forceinline__ void own_trace(const T* sq, const T* d0, const T* d1, const T* d2, int face, int f,
+                                          const T s[3], const T* lm, const T* lp, T o[5][4]) {
   constexpr int NP = N * N * N;
   int off, stride;
   line_of<N>(face >> 1, f, &off, &stride);
-  const double* c = (face & 1) ? lp : lm;
+  const T* c = (face & 1) ? lp : lm;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     o[v][0] = tsum3<N>(sq + v * NP + off, stride, c);
@@ -305,62 +308,76 @@ __global__ void __launch_bounds__(256) k3_face(const F3Args a) {
 }
 
 // MODE 0: out = R(U); 1: out = A z; 2: out = b - A z (state U + eps z, face
-// data from the face buffer); 3: element-Jacobi column (see the file header)
-template <int P, int MODE>
+// data from the face buffer); 3: element-Jacobi column (see the file header).
+// T: arithmetic type, double except for FP32 element-Jacobi columns (MODE 3,
+// T = float): then a first pass (a.r0_pass) writes the element-local R(U) of
+// each element of the chunk in FP32 to a.r0f, and the columns pass divides
+// R(U + eps_c e_c) - r0f by the step actually taken in FP32.
+template <int P, int MODE, typename T = double>
 __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
-  using L = CellLayout<P>;
+  using L = CellLayout<P, T>;
   constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E, NB = 5 * NP;
   constexpr bool PERTURB = MODE == 1 || MODE == 2;
   constexpr bool JAC = MODE == 3;
-  constexpr double cbr2 = (P + 1) * (P + 2) / 2.0;
-  extern __shared__ double smem3[];
-  __shared__ double sD[N][N], sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+  constexpr bool J32 = JAC && sizeof(T) == 4;
+  static_assert(sizeof(T) == 8 || JAC, "R(U) and A z run in FP64");
+  constexpr T cbr2 = T((P + 1) * (P + 2) / 2.0);
+  extern __shared__ __align__(16) unsigned char smem3_raw[];
+  T* smem3 = reinterpret_cast<T*>(smem3_raw);
+  __shared__ T sD[N][N], sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
   if (a.done && *a.done) return;
   if (threadIdx.x < N * N) {
-    sD[threadIdx.x / N][threadIdx.x % N] = a.tab.D[threadIdx.x / N][threadIdx.x % N];
-    sDt[threadIdx.x / N][threadIdx.x % N] = a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
+    sD[threadIdx.x / N][threadIdx.x % N] = (T)a.tab.D[threadIdx.x / N][threadIdx.x % N];
+    sDt[threadIdx.x / N][threadIdx.x % N] = (T)a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
   }
   if (threadIdx.x < N) {
-    slm[threadIdx.x] = a.tab.lm[threadIdx.x];
-    slp[threadIdx.x] = a.tab.lp[threadIdx.x];
-    sdgL[threadIdx.x] = a.tab.dgL[threadIdx.x];
-    sdgR[threadIdx.x] = a.tab.dgR[threadIdx.x];
+    slm[threadIdx.x] = (T)a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = (T)a.tab.lp[threadIdx.x];
+    sdgL[threadIdx.x] = (T)a.tab.dgL[threadIdx.x];
+    sdgR[threadIdx.x] = (T)a.tab.dgR[threadIdx.x];
   }
   const int el = threadIdx.x / NP, t = threadIdx.x % NP;
-  double* base = smem3 + (size_t)(el < E ? el : 0) * L::PER;
-  double* sq = base;                 // [5][NP]
-  double* d0 = sq + 5 * NP;          // derivatives, then fluxes, along x / y / z
-  double* d1 = d0 + 5 * NP;
-  double* d2 = d1 + 5 * NP;
-  double* dq = d2 + 5 * NP;          // [6][N2][5] q_com - q_face
-  double* fn = dq + 30 * N2;         // [6][N2][5] common total normal flux
+  T* base = smem3 + (size_t)(el < E ? el : 0) * L::PER;
+  T* sq = base;                 // [5][NP]
+  T* d0 = sq + 5 * NP;          // derivatives, then fluxes, along x / y / z
+  T* d1 = d0 + 5 * NP;
+  T* d2 = d1 + 5 * NP;
+  T* dq = d2 + 5 * NP;          // [6][N2][5] q_com - q_face
+  T* fn = dq + 30 * N2;         // [6][N2][5] common total normal flux
+  const bool r0_pass = J32 && a.r0_pass;
   const long long slot = (long long)blockIdx.x * E + el;
-  const long long nslots = JAC ? a.nchunk * NB : a.ne;
+  const long long nslots = JAC ? (r0_pass ? a.nchunk : a.nchunk * NB) : a.ne;
   const bool active = el < E && slot < nslots;
-  const long long e = JAC ? a.e0 + slot / NB : slot;
-  const int col = JAC ? (int)(slot % NB) : 0;
+  const long long e = JAC ? a.e0 + (r0_pass ? slot : slot / NB) : slot;
+  const int col = JAC && !r0_pass ? (int)(slot % NB) : -1;
   double eps = 0.0, ieps = 0.0;
   if (PERTURB) {
     eps = a.eps2[0];
     ieps = a.eps2[1];
   }
   int ix = 0, iy = 0, iz = 0;
-  double s[3] = {1.0, 1.0, 1.0}, hown[3] = {1.0, 1.0, 1.0};
-  double ceps = 0.0;
+  T s[3] = {T(1), T(1), T(1)}, hown[3] = {T(1), T(1), T(1)};
+  double ceps = 0.0;  // FD step of the column (FP32: the step taken after rounding)
   if (active) {
     coords(e, a, &ix, &iy, &iz);
-    hown[0] = a.hx[ix];
-    hown[1] = a.hy[iy];
-    hown[2] = a.hz[iz];
+    hown[0] = (T)a.hx[ix];
+    hown[1] = (T)a.hy[iy];
+    hown[2] = (T)a.hz[iz];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s[c] = 2.0 / hown[c];
-    if (JAC) ceps = a.beps * (1.0 + fabs(a.U[e * NB + col]));
+    for (int c = 0; c < 3; ++c) s[c] = T(2) / hown[c];
+    if (JAC && col >= 0) {
+      const double uc = a.U[e * NB + col];
+      ceps = a.beps * (1.0 + fabs(uc));
+      if (J32) ceps = (double)((float)(uc + ceps) - (float)uc);
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const long long o = e * NB + v * NP + t;
       double qv = PERTURB ? fma(eps, a.z[o], a.U[o]) : a.U[o];
-      if (JAC && v * NP + t == col) qv += ceps;
-      sq[v * NP + t] = qv;
+      if (JAC && v * NP + t == col) qv += J32 ? 0.0 : ceps;
+      T tq = (T)qv;
+      if (J32 && v * NP + t == col) tq = (T)(qv + a.beps * (1.0 + fabs(qv)));
+      sq[v * NP + t] = tq;
     }
   }
   __syncthreads();
@@ -370,9 +387,9 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
   if (active) {
     for (int fp = t; fp < 6 * N2; fp += NP) {
       const int face = fp / N2, f = fp % N2, d = face >> 1;
-      double qface[5], qc[5], fnum[5];
+      T qface[5], qc[5], fnum[5];
       if (JAC) {
-        double o[5][4], nbt[5][4];
+        T o[5][4], nbt[5][4];
         own_trace<N>(sq, d0, d1, d2, face, f, s, slm, slp, o);
         double hn;
         const long long nbe = neighbour(ix, iy, iz, face, a, &hn);
@@ -381,14 +398,14 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
         for (int v = 0; v < 5; ++v) {
           qface[v] = o[v][0];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) nbt[v][c] = src[v * 4 + c];
+          for (int c = 0; c < 4; ++c) nbt[v][c] = (T)src[v * 4 + c];
         }
-        if (face & 1) common3(o, nbt, d, hown[d], hn, cbr2, a, qc, fnum);
-        else common3(nbt, o, d, hn, hown[d], cbr2, a, qc, fnum);
+        if (face & 1) common3(o, nbt, d, hown[d], (T)hn, cbr2, a, qc, fnum);
+        else common3(nbt, o, d, (T)hn, hown[d], cbr2, a, qc, fnum);
       } else {
         int off, stride;
         line_of<N>(d, f, &off, &stride);
-        const double* c = (face & 1) ? slp : slm;
+        const T* c = (face & 1) ? slp : slm;
 #pragma unroll
         for (int v = 0; v < 5; ++v) qface[v] = tsum3<N>(sq + v * NP + off, stride, c);
         long long fe = e;
@@ -399,8 +416,8 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
         const double* src = a.fb + ((fe * 3 + d) * N2 + f) * 10;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          qc[v] = src[v];
-          fnum[v] = src[5 + v];
+          qc[v] = (T)src[v];
+          fnum[v] = (T)src[5 + v];
         }
       }
 #pragma unroll
@@ -415,30 +432,30 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
   const int f0 = j + N * k, f1 = i + N * k, f2 = i + N * j;  // this point's face points per direction
   // corrected gradient and total fluxes at the own point (overwrite d0..d2)
   if (active) {
-    double q[5], g[3][5];
+    T q[5], g[3][5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       q[v] = sq[v * NP + t];
-      double x = d0[v * NP + t];
+      T x = d0[v * NP + t];
       x = fma(dq[(0 * N2 + f0) * 5 + v], sdgL[i], x);
       x = fma(dq[(1 * N2 + f0) * 5 + v], sdgR[i], x);
-      double y = d1[v * NP + t];
+      T y = d1[v * NP + t];
       y = fma(dq[(2 * N2 + f1) * 5 + v], sdgL[j], y);
       y = fma(dq[(3 * N2 + f1) * 5 + v], sdgR[j], y);
-      double zz = d2[v * NP + t];
+      T zz = d2[v * NP + t];
       zz = fma(dq[(4 * N2 + f2) * 5 + v], sdgL[k], zz);
       zz = fma(dq[(5 * N2 + f2) * 5 + v], sdgR[k], zz);
       g[0][v] = s[0] * x;
       g[1][v] = s[1] * y;
       g[2][v] = s[2] * zz;
     }
-    double fv[3][5];
-    visc3(q, g, a.gam, a.mu, a.kappa, 7, fv);
-    double* dst[3] = {d0, d1, d2};
+    T fv[3][5];
+    visc3(q, g, (T)a.gam, (T)a.mu, (T)a.kappa, 7, fv);
+    T* dst[3] = {d0, d1, d2};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double fi[5];
-      (void)flux3(q, d, a.gam, fi);
+      T fi[5];
+      (void)flux3(q, d, (T)a.gam, fi);
       // each thread reads and overwrites only its own point
 #pragma unroll
       for (int v = 0; v < 5; ++v) dst[d][v * NP + t] = fi[v] - fv[d][v];
@@ -448,14 +465,14 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
   if (!active) return;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double* F = d0 + v * NP;
-    const double* G = d1 + v * NP;
-    const double* H = d2 + v * NP;
-    double dF = sdgL[i] * fn[(0 * N2 + f0) * 5 + v];
+    const T* F = d0 + v * NP;
+    const T* G = d1 + v * NP;
+    const T* H = d2 + v * NP;
+    T dF = sdgL[i] * fn[(0 * N2 + f0) * 5 + v];
     dF = fma(sdgR[i], fn[(1 * N2 + f0) * 5 + v], dF);
-    double dG = sdgL[j] * fn[(2 * N2 + f1) * 5 + v];
+    T dG = sdgL[j] * fn[(2 * N2 + f1) * 5 + v];
     dG = fma(sdgR[j], fn[(3 * N2 + f1) * 5 + v], dG);
-    double dH = sdgL[k] * fn[(4 * N2 + f2) * 5 + v];
+    T dH = sdgL[k] * fn[(4 * N2 + f2) * 5 + v];
     dH = fma(sdgR[k], fn[(5 * N2 + f2) * 5 + v], dH);
 #pragma unroll
     for (int l = 0; l < N; ++l) {
@@ -463,17 +480,25 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
       dG = fma(sDt[j][l], G[i + N * l + N2 * k], dG);
       dH = fma(sDt[k][l], H[i + N * j + N2 * l], dH);
     }
-    const double R = -fma(s[0], dF, fma(s[1], dG, s[2] * dH));
+    const T R = -fma(s[0], dF, fma(s[1], dG, s[2] * dH));
     const long long o = e * NB + v * NP + t;
     if (MODE == 0) {
-      a.out[o] = R;
+      a.out[o] = (double)R;
     } else if (MODE == 3) {
       // column col of M = shift I - J_ee, staged column-major [col][row]
       const int row = v * NP + t;
-      a.out[((e - a.e0) * NB + col) * NB + row] = (row == col ? a.shift : 0.0) - (R - a.R0[o]) / ceps;
+      double* dst = a.out + ((e - a.e0) * NB + col) * NB + row;
+      if (r0_pass) {
+        a.r0f[(e - a.e0) * NB + row] = (float)R;
+      } else if (J32) {  // the difference quotient in FP32 (the step ceps is an FP32 value)
+        const float dq32 = ((float)R - a.r0f[(e - a.e0) * NB + row]) / (float)ceps;
+        *dst = (row == col ? a.shift : 0.0) - (double)dq32;
+      } else {
+        *dst = (row == col ? a.shift : 0.0) - ((double)R - a.R0[o]) / ceps;
+      }
     } else {
       const double zo = a.z[o];
-      const double Az = eps > 0.0 ? fma(-(R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
+      const double Az = eps > 0.0 ? fma(-((double)R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
       a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
     }
   }
@@ -563,6 +588,8 @@ F3Args make_args3(fr_ctx* ctx) {
   a.ne = ctx->ne;
   a.e0 = 0;
   a.nchunk = ctx->ne;
+  a.r0f = nullptr;
+  a.r0_pass = 0;
   a.nx = ctx->nx;
   a.ny = ctx->ny;
   a.nz = ctx->nz;
@@ -675,20 +702,34 @@ int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
 }
 
 namespace {
-// element-Jacobi columns of the elements a.e0 .. a.e0 + a.nchunk - 1; the
-// trace buffer already holds the unperturbed traces
-template <int P>
-int f3_columns(fr_ctx* ctx, const F3Args& a, cudaStream_t s) {
-  using L = CellLayout<P>;
+// element-Jacobi columns of the elements a.e0 .. a.e0 + a.nchunk - 1 in the
+// arithmetic T; the trace buffer already holds the unperturbed traces
+template <int P, typename T>
+int f3_columns(fr_ctx* ctx, F3Args a, cudaStream_t s) {
+  using L = CellLayout<P, T>;
   constexpr int NP = L::NP, E = F3Slots<P>::E, NB = 5 * NP;
-  FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+  FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
   // one element residual per column: the own six faces' common data, counted
   // like the residual with every face of the element
-  const double wf = (ns3d_residual_flops_per_element(P) + 3.0 * L::N2 * 245.0) * NB * (double)a.nchunk;
-  { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, wf);
-    k3_cell<P, 3><<<(unsigned)((a.nchunk * NB + E - 1) / E), E * NP, L::BYTES, s>>>(a); }
+  const double per = ns3d_residual_flops_per_element(P) + 3.0 * L::N2 * 245.0;
+  if (sizeof(T) == 4) {
+    // FP32: the element-local R(U) of each element by the same arithmetic first
+    a.r0f = ctx->r0f;
+    a.r0_pass = 1;
+    { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, per * (double)a.nchunk);
+      k3_cell<P, 3, T><<<(unsigned)((a.nchunk + E - 1) / E), E * NP, L::BYTES, s>>>(a); }
+    FRK_LAUNCHED(ctx);
+    a.r0_pass = 0;
+  }
+  { ProfScope ps_(ctx, FR_KF_FACTOR, s, 0.0, per * NB * (double)a.nchunk);
+    k3_cell<P, 3, T><<<(unsigned)((a.nchunk * NB + E - 1) / E), E * NP, L::BYTES, s>>>(a); }
   FRK_LAUNCHED(ctx);
   return FR_OK;
+}
+
+template <int P>
+int f3_columns_p(fr_ctx* ctx, const F3Args& a, cudaStream_t s) {
+  return ctx->opts.block_columns == 1 ? f3_columns<P, float>(ctx, a, s) : f3_columns<P, double>(ctx, a, s);
 }
 }  // namespace
 
@@ -705,13 +746,17 @@ int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
   a.R0 = ctx->rloc;
   a.out = ctx->mst;
   a.shift = shift;
+  if (ctx->opts.block_columns == 1) {
+    if (!ctx->r0f) return set_error(ctx, FR_ERR_UNSUPPORTED, "FP32 block columns need block_columns = 1 at creation");
+    a.beps = fmax(ctx->opts.block_eps_rel, 1.0 / 4096.0);  // ~ sqrt of FP32's unit roundoff
+  }
   for (long long e0 = 0; e0 < ctx->ne; e0 += ctx->blk_chunk) {
     a.e0 = e0;
     a.nchunk = ctx->ne - e0 < ctx->blk_chunk ? ctx->ne - e0 : ctx->blk_chunk;
     switch (ctx->p) {
-      case 1: FRK_TRY(f3_columns<1>(ctx, a, s)); break;
-      case 2: FRK_TRY(f3_columns<2>(ctx, a, s)); break;
-      default: FRK_TRY(f3_columns<3>(ctx, a, s)); break;
+      case 1: FRK_TRY(f3_columns_p<1>(ctx, a, s)); break;
+      case 2: FRK_TRY(f3_columns_p<2>(ctx, a, s)); break;
+      default: FRK_TRY(f3_columns_p<3>(ctx, a, s)); break;
     }
     FRK_TRY(launch_block_invert_range(ctx, ctx->mst, 0.0, e0, a.nchunk, s));
   }

@@ -120,6 +120,28 @@ def test_element_jacobi_matches_oracle(fr, p, prec, tol):
     assert _rel(z.cpu().numpy(), zo) < tol
 
 
+@pytest.mark.parametrize("p,prec,tol", [(2, 1, 2e-3), (3, 1, 2e-3), (3, 2, 3e-2)])
+def test_fp32_columns_match_oracle(fr, p, prec, tol):
+    """Element-Jacobi columns formed in FP32 (block_columns = 1: step
+    2^-12 (1 + |q|), the element-local R(U) by the same FP32 arithmetic)
+    against the oracle's FP64 blocks: the FD columns carry ~1e-3 relative
+    error (truncation of the larger step plus FP32 rounding of the residual
+    over the step), so the apply agrees to that level."""
+    edges, U0 = _random_case(p, dims=(2, 4, 2), seed=13)
+    gas = Gas3D(mu=0.03, prandtl=0.71)
+    prob = Problem3D(Mesh3D(*edges), p, gas)
+    shift = 40.0
+    ctx = fr.Context3D(*edges, p, _opts(fr, 0.03, precond=1, block_precision=prec, block_columns=1))
+    fr.fr_set_block_chunk(ctx, 5)            # chunks of 5 elements, ragged last chunk
+    fr.ejacobi_factor(ctx, _t(U0), None, shift)
+    r0 = S.random_vector(U0.shape, 8)
+    z = ctx.empty()
+    fr.ejacobi_apply(ctx, _t(r0), z)
+    zo = ElementJacobi(element_blocks(prob, U0, shift))(r0)
+    err = _rel(z.cpu().numpy(), zo)
+    assert err < tol, err
+
+
 def test_degree3_blocks_staged_in_chunks(fr):
     """320-row blocks staged and inverted a few elements at a time (ragged
     last chunk) give the same preconditioner, bit for bit, as one chunk."""
@@ -157,8 +179,10 @@ def test_ssprk3_steps_match_oracle(fr):
     assert _rel(U.cpu().numpy(), Uo) < 1e-12
 
 
-@pytest.mark.parametrize("p,precond", [(1, 1), (2, 1), (3, 0), (3, 1)])
-def test_row3_step_matches_oracle(fr, p, precond):
+@pytest.mark.parametrize("p,precond,cols", [(1, 1, 0), (2, 1, 0), (3, 0, 0), (3, 1, 0), (3, 1, 1)])
+def test_row3_step_matches_oracle(fr, p, precond, cols):
+    """cols = 1: FP32 block columns; the preconditioner changes, the
+    converged step does not."""
     n = 4 if p < 3 else (2 if precond else 3)   # the oracle's blocks need even nx, ny, nz
     edges, U0 = _tgv_case(n, p)
     gas = Gas3D(mu=TG.mu, prandtl=TG.prandtl)
@@ -166,7 +190,7 @@ def test_row3_step_matches_oracle(fr, p, precond):
     dt = 0.1
     prec = 1 if p == 3 and precond else 0       # 320-row blocks are stored in FP32
     ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=precond, block_precision=prec, tol_lin=1e-12,
-                                        gmres_max_restarts=200))
+                                        gmres_max_restarts=200, block_columns=cols))
     U = _t(U0)
     st = fr.step_row(ctx, 3, dt, U)
     Uo, so = o_row(prob, ROW[3](), dt, U0, SolverOpts(tol_lin=1e-12, m=30, max_restarts=200,

@@ -74,6 +74,11 @@ def test_defaults_and_argument_checks_without_gpu(libpath):
     assert fr.lib.fr_ctx_create(ctypes.byref(desc1), 2, None, ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
     bad = fr.default_opts(m_max=64)
     assert fr.lib.fr_ctx_create(ctypes.byref(desc), 2, ctypes.byref(bad), ctypes.byref(h)) == fr.FR_ERR_INVALID_ARG
+    assert o.block_columns == 0
+    for kw, code in ((dict(block_columns=2), fr.FR_ERR_INVALID_ARG),
+                     (dict(block_columns=1, block_precision=1), fr.FR_ERR_UNSUPPORTED)):   # FP32 columns: 3D only
+        bad = fr.default_opts(**kw)
+        assert fr.lib.fr_ctx_create(ctypes.byref(desc), 2, ctypes.byref(bad), ctypes.byref(h)) == code
     assert fr.lib.fr_residual(None, None, None, None) == fr.FR_ERR_INVALID_ARG
     assert fr.lib.fr_last_error(None) is not None
 
@@ -95,6 +100,9 @@ def test_3d_argument_checks_without_gpu(libpath):
     assert create(desc, 0, precond=0) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 3) == fr.FR_ERR_UNSUPPORTED                      # 320-row blocks: FP32/BF16 only
     assert create(desc, 4, block_precision=1) == fr.FR_ERR_UNSUPPORTED   # 625-row blocks not built
+    assert create(desc, 2, block_columns=1) == fr.FR_ERR_UNSUPPORTED     # FP32 columns: reduced-precision blocks
+    assert create(desc, 2, block_columns=1, precond=0, block_precision=1) == fr.FR_ERR_UNSUPPORTED
+    assert create(desc, 2, block_columns=-1) == fr.FR_ERR_INVALID_ARG
     assert create(desc, 2, riemann=1) == fr.FR_ERR_UNSUPPORTED           # Rusanov only
     assert create(desc, 2, jv_precision=1) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, guess=2) == fr.FR_ERR_UNSUPPORTED
