@@ -40,6 +40,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->lin_fy);
   cudaFree(c->rloc);
   cudaFree(c->r0f);
+  cudaFree(c->tbf);
   cudaFree(c->gfeat);
   for (double* p : c->bhist) cudaFree(p);
   cudaFree(c->gout);
@@ -214,7 +215,10 @@ int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
     }
     FRK_TRY(dalloc(c, &c->mst, (size_t)c->blk_chunk * nb2));
     FRK_TRY(dalloc(c, &c->rloc, n));
-    if (o->block_columns == 1) FRK_TRY(dalloc(c, &c->r0f, (size_t)c->blk_chunk * c->nb));
+    if (o->block_columns == 1) {
+      FRK_TRY(dalloc(c, &c->r0f, (size_t)c->blk_chunk * c->nb));
+      FRK_TRY(dalloc(c, &c->tbf, (size_t)c->ne * 6 * n2 * 20));
+    }
   }
   FRK_TRY(dalloc(c, &c->diss, 4));
   FRK_TRY(dalloc(c, &c->V, (size_t)(m + 1) * n));

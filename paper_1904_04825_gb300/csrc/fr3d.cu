@@ -49,6 +49,7 @@ struct F3Args {
   long long ne;
   long long e0, nchunk;  // mode 3: the elements e0 .. e0 + nchunk - 1, columns staged from out[0]
   float* r0f;            // mode 3 in FP32: element-local R(U) of the chunk, [nchunk][NB]
+  const float* tbf;      // mode 3 in FP32: the trace buffer in FP32
   int r0_pass;           // mode 3 in FP32: 1 = write r0f (one unperturbed slot per element)
   int nx, ny, nz;
   double gam, mu, kappa, shift, beps;
@@ -393,12 +394,12 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
         own_trace<N>(sq, d0, d1, d2, face, f, s, slm, slp, o);
         double hn;
         const long long nbe = neighbour(ix, iy, iz, face, a, &hn);
-        const double* src = a.tb + ((nbe * 6 + (face ^ 1)) * N2 + f) * 20;
+        const long long so = ((nbe * 6 + (face ^ 1)) * N2 + f) * 20;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           qface[v] = o[v][0];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) nbt[v][c] = (T)src[v * 4 + c];
+          for (int c = 0; c < 4; ++c) nbt[v][c] = J32 ? (T)a.tbf[so + v * 4 + c] : (T)a.tb[so + v * 4 + c];
         }
         if (face & 1) common3(o, nbt, d, hown[d], (T)hn, cbr2, a, qc, fnum);
         else common3(nbt, o, d, (T)hn, hown[d], cbr2, a, qc, fnum);
@@ -589,6 +590,7 @@ F3Args make_args3(fr_ctx* ctx) {
   a.e0 = 0;
   a.nchunk = ctx->ne;
   a.r0f = nullptr;
+  a.tbf = nullptr;
   a.r0_pass = 0;
   a.nx = ctx->nx;
   a.ny = ctx->ny;
@@ -702,6 +704,11 @@ int launch_f3_residual(fr_ctx* ctx, int mode, const double* U, const double* z, 
 }
 
 namespace {
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 // element-Jacobi columns of the elements a.e0 .. a.e0 + a.nchunk - 1 in the
 // arithmetic T; the trace buffer already holds the unperturbed traces
 template <int P, typename T>
@@ -747,8 +754,15 @@ int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s)
   a.out = ctx->mst;
   a.shift = shift;
   if (ctx->opts.block_columns == 1) {
-    if (!ctx->r0f) return set_error(ctx, FR_ERR_UNSUPPORTED, "FP32 block columns need block_columns = 1 at creation");
+    if (!ctx->r0f || !ctx->tbf)
+      return set_error(ctx, FR_ERR_UNSUPPORTED, "FP32 block columns need block_columns = 1 at creation");
     a.beps = fmax(ctx->opts.block_eps_rel, 1.0 / 4096.0);  // ~ sqrt of FP32's unit roundoff
+    // the frozen neighbour traces, once in FP32
+    const long long nt = ctx->ne * 6 * (long long)(ctx->n1 * ctx->n1) * 20;
+    { ProfScope ps_(ctx, FR_KF_FACTOR, s, 12.0 * (double)nt, 0.0);
+      k_to_f32<<<(unsigned)(nt / 256 < 4096 ? (nt + 255) / 256 : 4096), 256, 0, s>>>(ctx->tb, ctx->tbf, nt); }
+    FRK_LAUNCHED(ctx);
+    a.tbf = ctx->tbf;
   }
   for (long long e0 = 0; e0 < ctx->ne; e0 += ctx->blk_chunk) {
     a.e0 = e0;

@@ -7,7 +7,9 @@
 // panels of BW = 16 columns; the CTA that holds a panel factorises it:
 //  * for each column c of the panel, the pivot row is the unused row of
 //    largest |M[r][c]| (rows stay in place, pr[c] = r is recorded), and the
-//    elimination is applied to the panel's columns (all rows);
+//    elimination is applied to the panel's columns (all rows); during the
+//    panel each thread holds one row of it in registers, so a pivot costs
+//    a warp-shuffle arg-max, two barriers and a broadcast of the pivot row;
 //  * U = (panel columns after the panel) - (unit vectors of the pivot rows),
 //    NB x BW, is written into the shared memory of both CTAs (distributed
 //    shared memory), with the panel's pivot rows;
@@ -38,15 +40,17 @@ struct Shape {
   static constexpr int QN = CW / 32;         // columns per lane in the update
   static constexpr int RPW = NB / (THREADS / 32);  // rows per warp in the update
   static_assert(NB % (THREADS / 32) == 0, "rows split evenly over the warps");
-  // bytes: M, U, col, pr (int), used (byte), rows (int), srow, pivot row
+  // bytes: M, U, pr (int), rows (int), srow (16-byte aligned), per-warp
+  // pivot candidates (value, row), used (byte)
   static constexpr size_t OFF_U = (size_t)NB * LDM * 4;
-  static constexpr size_t OFF_COL = OFF_U + (size_t)NB * BW * 4;
-  static constexpr size_t OFF_PR = OFF_COL + (size_t)NB * 4;
+  static constexpr size_t OFF_PR = OFF_U + (size_t)NB * BW * 4;
   static constexpr size_t OFF_ROWS = OFF_PR + (size_t)NB * 4;
-  static constexpr size_t OFF_SROW = OFF_ROWS + BW * 4;
-  static constexpr size_t OFF_PROW = OFF_SROW + BW * 4;
-  static constexpr size_t OFF_USED = OFF_PROW + 16;
+  static constexpr size_t OFF_SROW = (OFF_ROWS + BW * 4 + 15) / 16 * 16;
+  static constexpr size_t OFF_REDV = OFF_SROW + BW * 4;
+  static constexpr size_t OFF_REDI = OFF_REDV + 32 * 4;
+  static constexpr size_t OFF_USED = OFF_REDI + 32 * 4;
   static constexpr size_t BYTES = (OFF_USED + NB + 15) / 16 * 16;
+  static_assert(NB == THREADS, "the panel factorisation keeps one row per thread");
 };
 
 // Invert element blocks b = 0 .. (gridDim.x / CL) - 1 of the FP64 staging
@@ -63,12 +67,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(THREADS)
   extern __shared__ __align__(16) unsigned char smem_cl[];
   float* M = reinterpret_cast<float*>(smem_cl);
   float* U = reinterpret_cast<float*>(smem_cl + Sh::OFF_U);
-  float* col = reinterpret_cast<float*>(smem_cl + Sh::OFF_COL);
   int* pr = reinterpret_cast<int*>(smem_cl + Sh::OFF_PR);
   int* rows = reinterpret_cast<int*>(smem_cl + Sh::OFF_ROWS);
   float* srow = reinterpret_cast<float*>(smem_cl + Sh::OFF_SROW);
-  int* s_prow = reinterpret_cast<int*>(smem_cl + Sh::OFF_PROW);
+  float* red_v = reinterpret_cast<float*>(smem_cl + Sh::OFF_REDV);
+  int* red_i = reinterpret_cast<int*>(smem_cl + Sh::OFF_REDI);
   unsigned char* used = smem_cl + Sh::OFF_USED;
+  constexpr int NWARP = THREADS / 32;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -90,50 +95,78 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(THREADS)
     const int owner = c0 / CW;
     const int lc0 = c0 - col0;
     if (rank == owner) {
-      // ---- panel factorisation on the local columns lc0 .. lc0 + BW ----
-      for (int k = 0; k < BW; ++k) {
-        const int c = lc0 + k;
-        for (int i = tid; i < NB; i += THREADS) col[i] = M[i * LDM + c];
-        __syncthreads();
-        if (warp == 0) {
-          float best = -1.f;  // |pivot| (NaN ranks above everything)
-          int bi = NB;
-          for (int r = lane; r < NB; r += 32) {
-            if (used[r]) continue;
-            float v = fabsf(col[r]);
-            if (v != v) v = __int_as_float(0x7f800000);
-            if (v > best) { best = v; bi = r; }
-          }
+      // ---- panel factorisation on the local columns lc0 .. lc0 + BW: thread
+      // i keeps row i of the panel in registers ----
+      const int i = tid;
+      float pv[BW];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          bi = __shfl_sync(0xffffffffu, bi, 0);
-          const float ip = 1.f / col[bi];
-          if (lane < BW) srow[lane] = (lane == k ? 1.f : M[bi * LDM + lc0 + lane]) * ip;
-          if (lane == 0) {
-            *s_prow = bi;
-            used[bi] = 1;
-            rows[k] = bi;
-          }
+      for (int t = 0; t < BW; ++t) pv[t] = M[i * LDM + lc0 + t];
+      bool usd = used[i] != 0;
+#pragma unroll
+      for (int k = 0; k < BW; ++k) {
+        // pivot: the unused row of largest |M[r][c]| (NaN ranks above
+        // everything), the lowest row among equals
+        float best = usd ? -1.f : fabsf(pv[k]);
+        if (best != best) best = __int_as_float(0x7f800000);
+        int bi = usd ? NB : i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          red_v[warp] = best;
+          red_i[warp] = bi;
         }
         __syncthreads();
-        const int r = *s_prow;
-        for (int idx = tid; idx < NB * BW; idx += THREADS) {
-          const int i = idx / BW, t = idx - i * BW;
-          float* m = M + i * LDM + lc0 + t;
-          *m = i == r ? srow[t] : (t == k ? 0.f : *m) - col[i] * srow[t];
+        best = red_v[0];
+        bi = red_i[0];
+#pragma unroll
+        for (int w = 1; w < NWARP; ++w) {
+          const float ob = red_v[w];
+          const int oi = red_i[w];
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const float c = pv[k];  // this row's entry in the pivot column
+        if (i == bi) {
+          const float ip = 1.f / c;
+#pragma unroll
+          for (int t = 0; t < BW; ++t) srow[t] = (t == k ? 1.f : pv[t]) * ip;
+          rows[k] = bi;
+          usd = true;
+          used[i] = 1;
         }
         __syncthreads();
+        const float4* s4 = reinterpret_cast<const float4*>(srow);
+        float sr[BW];
+#pragma unroll
+        for (int t4 = 0; t4 < BW / 4; ++t4) {
+          const float4 v = s4[t4];
+          sr[4 * t4] = v.x;
+          sr[4 * t4 + 1] = v.y;
+          sr[4 * t4 + 2] = v.z;
+          sr[4 * t4 + 3] = v.w;
+        }
+#pragma unroll
+        for (int t = 0; t < BW; ++t) pv[t] = i == bi ? sr[t] : (t == k ? 0.f : pv[t]) - c * sr[t];
       }
-      // ---- U = panel - unit vectors of the pivot rows, to both CTAs ----
-      for (int idx = tid; idx < NB * BW; idx += THREADS) {
-        const int i = idx / BW, k = idx - i * BW;
-        const float u = M[i * LDM + lc0 + k] - (i == rows[k] ? 1.f : 0.f);
-        U[idx] = u;
-        peerU[idx] = u;
+      // ---- the panel back into M; U = panel - unit vectors of the pivot
+      // rows, to both CTAs ----
+      float4* u4 = reinterpret_cast<float4*>(U + i * BW);
+      float4* p4 = reinterpret_cast<float4*>(peerU + i * BW);
+#pragma unroll
+      for (int t4 = 0; t4 < BW / 4; ++t4) {
+        float u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int t = 4 * t4 + q;
+          M[i * LDM + lc0 + t] = pv[t];
+          u[q] = pv[t] - (i == rows[t] ? 1.f : 0.f);
+        }
+        const float4 v = make_float4(u[0], u[1], u[2], u[3]);
+        u4[t4] = v;
+        p4[t4] = v;
       }
       if (tid < BW) peerRows[tid] = rows[tid];
     }

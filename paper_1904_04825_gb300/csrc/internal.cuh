@@ -134,6 +134,7 @@ struct fr_ctx {
   double* mst = nullptr;     // viscous: staging of the FD element blocks before inversion
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   float* r0f = nullptr;      // FP32 block columns: element-local R(U) of one staging chunk
+  float* tbf = nullptr;      // FP32 block columns: FP32 copy of the 3D trace buffer
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
   long long blk_chunk = 0;   // elements whose staged blocks mst holds at once (ne unless staged in chunks)
   int hist_row = 0;          // ROW order of the last step if its stage solutions are intact
