@@ -369,8 +369,9 @@ int fr_guess_stats(const fr_ctx* ctx, long long* tried, long long* used);
  *    meshes are rejected with FR_ERR_INVALID_ARG.  p must be 2, 3 or 4.
  *  - Every call looks up the array's device address on the current device
  *    (this allocates nothing).  The first lookup on a device also loads the
- *    library's device code there: make the first call on each device before
- *    any stream capture.
+ *    library's device code there.  The call copies the host edges on
+ *    `stream` and cannot be captured into a graph: on a stream that is being
+ *    captured it returns FR_ERR_UNSUPPORTED.
  *  - Every call uses the same array and leaves its contents behind; calls
  *    that overlap on the GPU (other streams, other host threads) race.
  *    Serialise them on one stream.

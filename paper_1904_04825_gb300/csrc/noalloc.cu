@@ -112,6 +112,13 @@ extern "C" int fr_jv_noalloc(const fr_mesh_desc* mesh, int p, const fr_opts* opt
     set_static_error("fr_jv_noalloc: only the periodic Euler FP64 product (wall_y = 0, mu = 0, jv_precision = 0)");
     return FR_ERR_UNSUPPORTED;
   }
+  // the edges are copied from the caller's (pageable, possibly temporary)
+  // host arrays on the stream, which a graph capture could not replay
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(as_stream(stream), &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    set_static_error("fr_jv_noalloc: the stream is being captured (the call cannot be captured)");
+    return FR_ERR_UNSUPPORTED;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     set_static_error("fr_jv_noalloc: cudaGetDevice failed");

@@ -80,3 +80,23 @@ def test_noalloc_rejects_meshes_beyond_its_fixed_size_and_other_operators():
         with pytest.raises(fr.FrError) as ei:
             fr.fr_jv_noalloc(xe, xe, 2, t[0], t[1], t[2], 0.0, t[3], opts=fr.default_opts(**kw))
         assert ei.value.code == fr.FR_ERR_UNSUPPORTED
+
+
+def test_noalloc_refuses_stream_capture():
+    """The call copies host edge arrays on the stream, which a captured graph
+    could not replay: on a capturing stream it returns FR_ERR_UNSUPPORTED
+    and records nothing."""
+    import torch
+    import paper_1904_04825_gb300 as fr
+    xe = np.linspace(0.0, 1.0, 5)
+    n = 16 * 4 * 9
+    t = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+    g = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.graph(g):
+        try:
+            fr.fr_jv_noalloc(xe, xe, 2, t[0], t[1], t[2], 0.0, t[3])
+        except fr.FrError as e:
+            codes.append(e.code)
+        t[3].add_(1.0)   # one captured kernel, so the graph is not empty
+    assert codes == [fr.FR_ERR_UNSUPPORTED]
