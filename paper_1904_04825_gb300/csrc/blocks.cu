@@ -585,6 +585,66 @@ __global__ void __launch_bounds__(RowsShape<NB>::THREADS) k_apply_rows(const S* 
   }
 }
 
+// The row apply for BF16 blocks of even, large nb (3D degree 3: nb = 320):
+// each thread two adjacent rows, so one 4-byte load brings the bf16 pair of
+// a column and a warp request covers 128 bytes (2-byte loads left the apply
+// at two thirds of HBM bandwidth).  Two elements per CTA, nb threads.  Each
+// row's sum runs over the columns in the same order as in k_apply_rows.
+template <int NB>
+__global__ void __launch_bounds__(NB) k_apply_rows_bf2(const __nv_bfloat16* __restrict__ Minv, double* r,
+                                                       const double* scale, double* z, long long ne,
+                                                       double* sumsq, Reduce red, const int* done, EpsArgs ea) {
+  static_assert(NB % 64 == 0, "two rows per thread, whole warps per element");
+  constexpr int HALF = NB / 2, EPC = 2;
+  __shared__ float rs[EPC][NB];
+  __shared__ double sh[32];
+  if (done && *done) return;
+  const double sc = scale ? *scale : 1.0;
+  const int el = threadIdx.x / HALF, i2 = threadIdx.x % HALF;
+  double ss = 0.0;
+  for (long long e0 = (long long)blockIdx.x * EPC; e0 < ne; e0 += (long long)gridDim.x * EPC) {
+    const long long e = e0 + el;
+    const bool act = e < ne;
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double v = r[e * NB + 2 * i2 + h];
+        if (scale) {
+          v *= sc;
+          r[e * NB + 2 * i2 + h] = v;
+        }
+        rs[el][2 * i2 + h] = (float)v;
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const __nv_bfloat162* Me = reinterpret_cast<const __nv_bfloat162*>(Minv + e * (long long)NB * NB);
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll 16
+      for (int kk = 0; kk < NB; ++kk) {
+        const float2 m = __bfloat1622float2(Me[kk * HALF + i2]);
+        const float x = rs[el][kk];
+        a0 = fmaf(m.x, x, a0);
+        a1 = fmaf(m.y, x, a1);
+      }
+      const double z0 = (double)a0, z1 = (double)a1;
+      z[e * NB + 2 * i2] = z0;
+      z[e * NB + 2 * i2 + 1] = z1;
+      ss = fma(z0, z0, ss);
+      ss = fma(z1, z1, ss);
+    }
+  }
+  if (sumsq) {
+    const double bs = block_sum(ss, sh);
+    if (threadIdx.x == 0) red.partials[(size_t)blockIdx.x * kMaxVec] = bs;
+    if (last_block(red.counter)) {
+      finish_sums(red, 1, sumsq);
+      if (threadIdx.x == 0) write_eps(ea, *sumsq);
+    }
+  }
+}
+
 // z = s * r (no preconditioner), optional r *= s written back, optional sum of squares.
 __global__ void k_scale_copy(double* r, const double* scale, double* z, long long n,
                              double* sumsq, Reduce red, const int* done, EpsArgs ea) {
@@ -749,9 +809,17 @@ int apply_rows_nbs(fr_ctx* ctx, double* r, const double* scale, double* z, doubl
   const double wb = in_cycle ? 0.0 : (double)sizeof(S) * (double)ctx->ne * NB * NB + 16.0 * nd + (scale ? 8.0 * nd : 0.0);
   const double wf = in_cycle ? 0.0 : 2.0 * NB * nd;
   constexpr int threads = RowsShape<NB>::THREADS;  // whole warps (the reduction shuffles)
-  { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf);
+  if constexpr (std::is_same<S, __nv_bfloat16>::value && NB % 64 == 0) {
+    long long g = (ctx->ne + 1) / 2;
+    if (g > kRedBlocks) g = kRedBlocks;
+    { ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf);
+      k_apply_rows_bf2<NB><<<(unsigned)g, NB, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z, ctx->ne,
+                                                      sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
+  } else {
+    ProfScope ps_(ctx, FR_KF_APPLY, s, wb, wf);
     k_apply_rows<NB, S, A><<<apply_grid<NB>(ctx->ne), threads, 0, s>>>(reinterpret_cast<const S*>(ctx->blocks), r, scale, z,
-                                                                       ctx->ne, sumsq, ctx->red, done, eps_args(ctx, with_eps)); }
+                                                                       ctx->ne, sumsq, ctx->red, done, eps_args(ctx, with_eps));
+  }
   FRK_LAUNCHED(ctx);
   return FR_OK;
 }

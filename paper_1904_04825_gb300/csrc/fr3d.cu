@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
   extern __shared__ __align__(16) unsigned char smem3_raw[];
   T* smem3 = reinterpret_cast<T*>(smem3_raw);
   __shared__ T sD[N][N], sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+  __shared__ float sceps[E];  // FP32 columns: the step each slot took
   if (a.done && *a.done) return;
   if (threadIdx.x < N * N) {
     sD[threadIdx.x / N][threadIdx.x % N] = (T)a.tab.D[threadIdx.x / N][threadIdx.x % N];
@@ -366,22 +367,29 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
     hown[2] = (T)a.hz[iz];
 #pragma unroll
     for (int c = 0; c < 3; ++c) s[c] = T(2) / hown[c];
-    if (JAC && col >= 0) {
+    if (JAC && !J32 && col >= 0) {
       const double uc = a.U[e * NB + col];
       ceps = a.beps * (1.0 + fabs(uc));
-      if (J32) ceps = (double)((float)(uc + ceps) - (float)uc);
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const long long o = e * NB + v * NP + t;
       double qv = PERTURB ? fma(eps, a.z[o], a.U[o]) : a.U[o];
-      if (JAC && v * NP + t == col) qv += J32 ? 0.0 : ceps;
+      if (JAC && !J32 && v * NP + t == col) qv += ceps;
       T tq = (T)qv;
-      if (J32 && v * NP + t == col) tq = (T)(qv + a.beps * (1.0 + fabs(qv)));
+      if (J32 && v * NP + t == col) {
+        // the step in FP32 (no FP64 arithmetic in this kernel: on GB300 one
+        // FP64 operation costs as much issue as 64 FP32 ones)
+        const float c32 = (float)a.beps * (1.f + fabsf((float)tq));
+        const float pq = (float)tq + c32;
+        sceps[el] = pq - (float)tq;
+        tq = pq;
+      }
       sq[v * NP + t] = tq;
     }
   }
   __syncthreads();
+  const float ceps32 = J32 && active && col >= 0 ? sceps[el] : 1.f;
   if (active) ref_derivs<N>(sq, sD, t, d0, d1, d2);
   __syncthreads();
   // face data of the six faces
@@ -491,9 +499,9 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
       double* dst = a.out + ((e - a.e0) * NB + col) * NB + row;
       if (r0_pass) {
         a.r0f[(e - a.e0) * NB + row] = (float)R;
-      } else if (J32) {  // the difference quotient in FP32 (the step ceps is an FP32 value)
-        const float dq32 = ((float)R - a.r0f[(e - a.e0) * NB + row]) / (float)ceps;
-        *dst = (row == col ? a.shift : 0.0) - (double)dq32;
+      } else if (J32) {  // the difference quotient and the column in FP32
+        const float dq32 = ((float)R - a.r0f[(e - a.e0) * NB + row]) / ceps32;
+        *dst = (double)((row == col ? (float)a.shift : 0.f) - dq32);
       } else {
         *dst = (row == col ? a.shift : 0.0) - ((double)R - a.R0[o]) / ceps;
       }
