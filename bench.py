@@ -310,7 +310,8 @@ def our_arm(args):
         dt, wall = (args.dt or tg.t_c / 25.0), False
         opts = fr.default_opts(tol_lin=TOL_LIN, gmres_m=args.gmres_m, m_max=args.gmres_m, gmres_max_restarts=20,
                                block_precision=prec, mu=tg.mu, prandtl=tg.prandtl, precond=1 if p <= 3 else 0,
-                               block_columns=1 if args.block_columns == "fp32" and p <= 3 else 0)
+                               block_columns=1 if args.block_columns == "fp32" and p <= 3 else 0,
+                               jv_precision=1 if args.jv_precision == "fp32" else 0)
         wl = (f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-{args.scheme.upper()}-dt{dt:g}-gmres{args.gmres_m}"
               + ("" if p <= 3 else "-noprecond") + ("-fp32columns" if args.block_columns == "fp32" else ""))
     else:
@@ -685,7 +686,7 @@ def tgv_t_end_arm(args):
     ctx.close()
     kmax = max(ref, key=ref.get)
     out = {"workload": f"taylor-green-{n3}^3-p{p}-Re1600-Ma0.1-to-{args.t_end:g}tc", "ndof": 5 * (p + 1) ** 3 * n3 ** 3,
-           "block_columns": args.block_columns,
+           "block_columns": args.block_columns, "jv_precision": args.jv_precision,
            "reference": {"scheme": "SSPRK3", "dt": dt_ref, "steps": n_ref, "wall_s": ref_wall,
                          "eps_max": ref[kmax], "t_of_eps_max": kmax * dt_ref,
                          "eps_at": {f"{t:g}": ref[int(round(t * tg.t_c / dt_ref))]
@@ -700,6 +701,7 @@ def tgv_t_end_arm(args):
             ctx = fr.Context3D(*edges, p, fr.default_opts(precond=1, block_precision=prec, tol_lin=1e-6 if kind == "row" else 1e-1,
                                                            gmres_m=30, m_max=30, gmres_max_restarts=20,
                                                            block_columns=1 if args.block_columns == "fp32" and prec else 0,
+                                                           jv_precision=1 if args.jv_precision == "fp32" else 0,
                                                            **gas))
             ptc = fr.default_ptc_opts(tol_nl=1e-6, tol_lin=1e-1)
             U = U0.clone()
@@ -761,7 +763,8 @@ def kernel_arm(args):
             prec, args.block_precision = 1, "fp32"   # 320-row blocks are stored in FP32 or BF16
         ctx = fr.Context3D(*edges, p3, fr.default_opts(block_precision=prec, mu=tg.mu, prandtl=tg.prandtl,
                                                         precond=1 if blocks else 0, m_max=4, gmres_m=4,
-                                                        block_columns=1 if blocks and args.block_columns == "fp32" else 0))
+                                                        block_columns=1 if blocks and args.block_columns == "fp32" else 0,
+                                                        jv_precision=1 if args.jv_precision == "fp32" else 0))
     else:
         xe, ye = S.uniform_mesh(NX)
         X, Y = S.point_coords(xe, ye, P)
@@ -1207,7 +1210,7 @@ def main():
     ap.add_argument("--riemann", choices=["rusanov", "roe"], default="rusanov",
                     help="common inviscid flux (roe: the paper's; Euler only)")
     ap.add_argument("--jv-precision", choices=["fp64", "fp32"], default="fp64",
-                    help="fp32: linear parts of the FD operator in FP32 (Euler only)")
+                    help="fp32: linear parts of the FD operator in FP32 (2D Euler and 3D)")
     ap.add_argument("--workload", choices=["vortex", "channel", "batch", "tgv", "guess"], default="vortex")
     ap.add_argument("--train-seeds", type=int, default=500, help="--workload guess: training seeds (4 stage solves each)")
     ap.add_argument("--eval-seeds", type=int, default=50, help="--workload guess: held-out seeds")

@@ -99,7 +99,8 @@ typedef struct fr_opts {
                             fr_mlp fed [b, previous-step stage solution, previous
                             stage solution]; falls back to 1 without a model).
                             GMRES stops at tol_lin * ||b|| whatever the guess */
-  int jv_precision;      /* finite-difference operator A z (Euler residual only):
+  int jv_precision;      /* finite-difference operator A z (2D Euler residual and
+                            3D contexts):
                             0 = FP64 throughout (default, the paper's);
                             1 = the linear parts of R(U+eps z) - R(U) -- solution and
                             flux interpolation, derivative and correction -- in
@@ -107,7 +108,14 @@ typedef struct fr_opts {
                             fluxes and their differences from the cached
                             F(U), f^num(U) in FP64.  A z then carries a relative
                             error of ~1e-7, so use it only with tol_lin >= 1e-6
-                            (ROW at loose tolerances, ESDIRK/BDF2 inner solves) */
+                            (ROW at loose tolerances, ESDIRK/BDF2 inner solves).
+                            3D (BR2 Navier-Stokes): reference derivatives,
+                            traces, BR2 liftings, corrected gradient and
+                            corrected divergence act on z in FP32; the
+                            inviscid and viscous fluxes at U + eps z (state,
+                            traces and gradient from caches at U plus eps
+                            times their FP32 parts of z) in FP64, differenced
+                            against the fluxes cached at U */
   int riemann;           /* common inviscid flux at the faces (Sec. 3, Eq. invis_com):
                             0 = Rusanov (default), 1 = Roe without entropy fix (the
                             paper's); Euler residual only */
@@ -178,10 +186,13 @@ typedef struct fr_mesh3d_desc {
  * that takes a context works on a 3D one (fr_residual, fr_jv, ejacobi_*,
  * gmres_solve, the steppers, fr_autotune, profiling) except the batch and
  * learned-guess calls.  Element-Jacobi blocks (5 (p+1)^3 rows) are built
- * for p <= 2; opts->precond with p > 2, opts->riemann = 1,
- * opts->jv_precision = 1, opts->guess = 2 or a body force return
- * FR_ERR_UNSUPPORTED.  The blocks and their staging (2 Ne nb^2 doubles) are
- * allocated only when opts->precond is set. */
+ * for p <= 3 (p = 3: 320-row blocks stored in FP32 or BF16, block_precision
+ * 1 or 2, staged in chunks of 4096 elements); opts->precond with p > 3 or
+ * with p = 3 and FP64 blocks, opts->riemann = 1, opts->guess = 2 or a body
+ * force return FR_ERR_UNSUPPORTED.  The blocks and their staging are
+ * allocated only when opts->precond is set; jv_precision = 1 allocates its
+ * caches (traces and face data at U, 6 values per DOF at the points, and
+ * FP32 buffers). */
 int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* opts, fr_ctx** out);
 /* Kinetic-energy dissipation rate of the Taylor-Green study (Sec. 5) of the
  * 3D state U (device, ndof doubles): out[0] = eps1 = 2 mu / rho0 <S^d : S^d>,

@@ -41,6 +41,12 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->rloc);
   cudaFree(c->r0f);
   cudaFree(c->tbf);
+  cudaFree(c->lin3_tb);
+  cudaFree(c->lin3_fb);
+  cudaFree(c->lin3_g);
+  cudaFree(c->lin3_f);
+  cudaFree(c->lin3_tbz);
+  cudaFree(c->lin3_fbz);
   cudaFree(c->gfeat);
   for (double* p : c->bhist) cudaFree(p);
   cudaFree(c->gout);
@@ -203,6 +209,14 @@ int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
   const size_t n2 = (size_t)c->n1 * c->n1;
   FRK_TRY(dalloc(c, &c->tb, (size_t)c->ne * 6 * n2 * 20));
   FRK_TRY(dalloc(c, &c->fb, (size_t)c->ne * 3 * n2 * 10));
+  if (o->jv_precision == 1) {  // caches of the A z with FP32 linear parts
+    FRK_TRY(dalloc(c, &c->lin3_tb, (size_t)c->ne * 6 * n2 * 20));
+    FRK_TRY(dalloc(c, &c->lin3_fb, (size_t)c->ne * 3 * n2 * 10));
+    FRK_TRY(dalloc(c, &c->lin3_g, (size_t)c->ndof * 3));
+    FRK_TRY(dalloc(c, &c->lin3_f, (size_t)c->ndof * 3));
+    FRK_TRY(dalloc(c, &c->lin3_tbz, (size_t)c->ne * 6 * n2 * 20));
+    FRK_TRY(dalloc(c, &c->lin3_fbz, (size_t)c->ne * 3 * n2 * 10));
+  }
   if (o->precond) {
     const size_t nb2 = (size_t)c->nb * c->nb;
     if (p <= 2) {
@@ -436,10 +450,10 @@ extern "C" int fr_ctx_create_3d(const fr_mesh3d_desc* mesh, int p, const fr_opts
       !(o.mu >= 0.0) || (o.mu > 0.0 && !(o.prandtl > 0.0)) || o.precond_refresh < 0 || o.precond_refresh > 2 ||
       o.guess < 0 || o.guess > 2 || o.jv_precision < 0 || o.jv_precision > 1 || o.riemann < 0 || o.riemann > 1)
     return FR_ERR_INVALID_ARG;
-  // the 3D path: Rusanov flux, FP64 operator, no body force; element blocks
-  // for p <= 3 (5 (p+1)^3 = 40, 135 or 320 rows; 320-row blocks in FP32 or
-  // BF16 only), no learned guess
-  if (o.riemann != 0 || o.jv_precision != 0 || o.guess == 2 || o.body_force_x != 0.0) return FR_ERR_UNSUPPORTED;
+  // the 3D path: Rusanov flux, no body force; the FD operator in FP64 or with
+  // FP32 linear parts; element blocks for p <= 3 (5 (p+1)^3 = 40, 135 or 320
+  // rows; 320-row blocks in FP32 or BF16 only), no learned guess
+  if (o.riemann != 0 || o.guess == 2 || o.body_force_x != 0.0) return FR_ERR_UNSUPPORTED;
   if (o.block_columns < 0 || o.block_columns > 1) return FR_ERR_INVALID_ARG;
   if (o.block_columns == 1 && (!o.precond || o.block_precision == 0)) return FR_ERR_UNSUPPORTED;
   if (o.precond && (p > 3 || (p == 3 && o.block_precision == 0))) return FR_ERR_UNSUPPORTED;

@@ -50,6 +50,14 @@ struct F3Args {
   long long e0, nchunk;  // mode 3: the elements e0 .. e0 + nchunk - 1, columns staged from out[0]
   float* r0f;            // mode 3 in FP32: element-local R(U) of the chunk, [nchunk][NB]
   const float* tbf;      // mode 3 in FP32: the trace buffer in FP32
+  // A z with FP32 linear parts (jv_precision 1): caches at the linearisation
+  // point U and the FP32 buffers of the product
+  double* ltb;           // traces of U [ne][6][N^2][20]
+  double* lfb;           // low-face common data of U [ne][3][N^2][10]
+  double* lg;            // corrected gradient of U at the points [ne][3][5][Np]
+  double* lf;            // total fluxes at U at the points [ne][3][5][Np]
+  float* tbz;            // traces of z and of its gradient [ne][6][N^2][20]
+  float* fbz;            // per unit eps: q_com differences and f_n differences [ne][3][N^2][10]
   int r0_pass;           // mode 3 in FP32: 1 = write r0f (one unperturbed slot per element)
   int nx, ny, nz;
   double gam, mu, kappa, shift, beps;
@@ -309,7 +317,9 @@ __global__ void __launch_bounds__(256) k3_face(const F3Args a) {
 }
 
 // MODE 0: out = R(U); 1: out = A z; 2: out = b - A z (state U + eps z, face
-// data from the face buffer); 3: element-Jacobi column (see the file header).
+// data from the face buffer); 3: element-Jacobi column (see the file header);
+// 4: the caches of the FP32-linear-parts A z at U (corrected gradient and
+// total fluxes at the points to a.lg, a.lf; face data from the face buffer).
 // T: arithmetic type, double except for FP32 element-Jacobi columns (MODE 3,
 // T = float): then a first pass (a.r0_pass) writes the element-local R(U) of
 // each element of the chunk in FP32 to a.r0f, and the columns pass divides
@@ -469,7 +479,18 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) dst[d][v * NP + t] = fi[v] - fv[d][v];
     }
+    if (MODE == 4) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const long long o = ((e * 3 + c) * 5 + v) * NP + t;
+          a.lg[o] = (double)g[c][v];
+          a.lf[o] = (double)dst[c][v * NP + t];
+        }
+    }
   }
+  if (MODE == 4) return;
   __syncthreads();
   if (!active) return;
 #pragma unroll
@@ -510,6 +531,224 @@ __global__ void __launch_bounds__(256) k3_cell(const F3Args a) {
       const double Az = eps > 0.0 ? fma(-((double)R - a.R0[o]), ieps, a.shift * zo) : a.shift * zo;
       a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
     }
+  }
+}
+
+// ---- A z with FP32 linear parts (jv_precision 1) ----
+// R(U + eps z) - R(U) splits into linear maps (reference derivatives, traces,
+// BR2 liftings, the FR correction of the gradient, the corrected divergence)
+// and the nonlinear pointwise and common fluxes.  The linear maps act on z
+// in FP32; the fluxes are evaluated in FP64 at U + eps z from the cached
+// state, traces and corrected gradient at U plus eps times their FP32
+// counterparts of z, and differenced in FP64 against the fluxes cached at U;
+// the differences, divided by eps, go through the corrected divergence in
+// FP32.  Mode 1: out = shift z - (R(U + eps z) - R(U)) / eps; mode 2: b - that.
+
+// traces of z and of its physical gradient at the 6 N^2 face points, FP32
+template <int P>
+__global__ void __launch_bounds__(256) k3z_trace(const F3Args a) {
+  constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E;
+  __shared__ float sq[E][5 * NP], dd[3][E][5 * NP];
+  __shared__ float sD[N][N], slm[N], slp[N];
+  if (threadIdx.x < N * N) sD[threadIdx.x / N][threadIdx.x % N] = (float)a.tab.D[threadIdx.x / N][threadIdx.x % N];
+  if (threadIdx.x < N) {
+    slm[threadIdx.x] = (float)a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = (float)a.tab.lp[threadIdx.x];
+  }
+  if (a.done && *a.done) return;
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  const long long e = (long long)blockIdx.x * E + el;
+  const bool active = el < E && e < a.ne;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sq[el][v * NP + t] = (float)a.z[e * 5 * NP + v * NP + t];
+  }
+  __syncthreads();
+  if (active) ref_derivs<N>(sq[el], sD, t, dd[0][el], dd[1][el], dd[2][el]);
+  __syncthreads();
+  if (!active) return;
+  int ix, iy, iz;
+  coords(e, a, &ix, &iy, &iz);
+  const float s[3] = {(float)(2.0 / a.hx[ix]), (float)(2.0 / a.hy[iy]), (float)(2.0 / a.hz[iz])};
+  for (int fp = t; fp < 6 * N2; fp += NP) {
+    const int face = fp / N2, f = fp % N2;
+    float o[5][4];
+    own_trace<N>(sq[el], dd[0][el], dd[1][el], dd[2][el], face, f, s, slm, slp, o);
+    float* dst = a.tbz + ((e * 6 + face) * N2 + f) * 20;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[v * 4 + c] = o[v][c];
+  }
+}
+
+// per low face point: the common data at U + eps z in FP64 from the cached
+// traces at U and eps times the FP32 traces of z; per unit eps, the change
+// of q_com (linear: the mean of the two traces of z) and of the common total
+// normal flux (FP64 difference against the cache) to a.fbz
+template <int P>
+__global__ void __launch_bounds__(256) k3z_face(const F3Args a) {
+  constexpr int N = P + 1, N2 = N * N;
+  constexpr double cbr2 = (P + 1) * (P + 2) / 2.0;
+  if (a.done && *a.done) return;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.ne * 3 * N2) return;
+  const int f = (int)(tid % N2);
+  const int d = (int)((tid / N2) % 3);
+  const long long e = tid / (3 * N2);
+  const double eps = a.eps2[0];
+  const double ieps = eps > 0.0 ? a.eps2[1] : 0.0;
+  int ix, iy, iz;
+  coords(e, a, &ix, &iy, &iz);
+  double hm;
+  const long long nbe = neighbour(ix, iy, iz, 2 * d, a, &hm);
+  const double hp = d == 0 ? a.hx[ix] : (d == 1 ? a.hy[iy] : a.hz[iz]);
+  const long long om = ((nbe * 6 + 2 * d + 1) * N2 + f) * 20;  // (-) side: the neighbour's high face
+  const long long op = ((e * 6 + 2 * d) * N2 + f) * 20;        // (+) side: this element's low face
+  double m[5][4], pp[5][4], qc[5], fn[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      m[v][c] = fma(eps, (double)a.tbz[om + v * 4 + c], a.ltb[om + v * 4 + c]);
+      pp[v][c] = fma(eps, (double)a.tbz[op + v * 4 + c], a.ltb[op + v * 4 + c]);
+    }
+  common3(m, pp, d, hm, hp, cbr2, a, qc, fn);
+  const double* f0 = a.lfb + ((e * 3 + d) * N2 + f) * 10;
+  float* dst = a.fbz + ((e * 3 + d) * N2 + f) * 10;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    dst[v] = 0.5f * (a.tbz[om + v * 4] + a.tbz[op + v * 4]);
+    dst[5 + v] = (float)((fn[v] - f0[5 + v]) * ieps);
+  }
+}
+
+// per element: FP32 derivatives and corrected gradient of z; at each point
+// the fluxes at U + eps z in FP64 (state U + eps z, gradient = cached
+// corrected gradient + eps times that of z) minus the cached fluxes, per
+// unit eps, then the corrected divergence in FP32
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) k3z_cell(const F3Args a) {
+  using L = CellLayout<P, float>;
+  constexpr int N = P + 1, N2 = N * N, NP = N2 * N, E = F3Slots<P>::E, NB = 5 * NP;
+  static_assert(MODE == 1 || MODE == 2, "A z or b - A z");
+  extern __shared__ __align__(16) unsigned char smemz_raw[];
+  float* smemz = reinterpret_cast<float*>(smemz_raw);
+  __shared__ float sD[N][N], sDt[N][N], slm[N], slp[N], sdgL[N], sdgR[N];
+  if (a.done && *a.done) return;
+  if (threadIdx.x < N * N) {
+    sD[threadIdx.x / N][threadIdx.x % N] = (float)a.tab.D[threadIdx.x / N][threadIdx.x % N];
+    sDt[threadIdx.x / N][threadIdx.x % N] = (float)a.tab.Dt[threadIdx.x / N][threadIdx.x % N];
+  }
+  if (threadIdx.x < N) {
+    slm[threadIdx.x] = (float)a.tab.lm[threadIdx.x];
+    slp[threadIdx.x] = (float)a.tab.lp[threadIdx.x];
+    sdgL[threadIdx.x] = (float)a.tab.dgL[threadIdx.x];
+    sdgR[threadIdx.x] = (float)a.tab.dgR[threadIdx.x];
+  }
+  const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+  float* base = smemz + (size_t)(el < E ? el : 0) * L::PER;
+  float* sz = base;              // [5][NP] z
+  float* d0 = sz + 5 * NP;       // derivatives of z, then flux differences per unit eps
+  float* d1 = d0 + 5 * NP;
+  float* d2 = d1 + 5 * NP;
+  float* dq = d2 + 5 * NP;       // [6][N2][5] q_com(z) - q_face(z)
+  float* fn = dq + 30 * N2;      // [6][N2][5] common flux differences per unit eps
+  const long long e = (long long)blockIdx.x * E + el;
+  const bool active = el < E && e < a.ne;
+  const double eps = a.eps2[0];
+  const double ieps = eps > 0.0 ? a.eps2[1] : 0.0;
+  int ix = 0, iy = 0, iz = 0;
+  float s[3] = {1.f, 1.f, 1.f};
+  if (active) {
+    coords(e, a, &ix, &iy, &iz);
+    s[0] = (float)(2.0 / a.hx[ix]);
+    s[1] = (float)(2.0 / a.hy[iy]);
+    s[2] = (float)(2.0 / a.hz[iz]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sz[v * NP + t] = (float)a.z[e * NB + v * NP + t];
+  }
+  __syncthreads();
+  if (active) ref_derivs<N>(sz, sD, t, d0, d1, d2);
+  __syncthreads();
+  if (active) {
+    for (int fp = t; fp < 6 * N2; fp += NP) {
+      const int face = fp / N2, f = fp % N2, d = face >> 1;
+      int off, stride;
+      line_of<N>(d, f, &off, &stride);
+      const float* c = (face & 1) ? slp : slm;
+      long long fe = e;
+      if (face & 1) {
+        double hn;
+        fe = neighbour(ix, iy, iz, face, a, &hn);
+      }
+      const float* src = a.fbz + ((fe * 3 + d) * N2 + f) * 10;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        dq[(face * N2 + f) * 5 + v] = src[v] - tsum3<N>(sz + v * NP + off, stride, c);
+        fn[(face * N2 + f) * 5 + v] = src[5 + v];
+      }
+    }
+  }
+  __syncthreads();
+  const int i = t % N, j = (t / N) % N, k = t / N2;
+  const int f0 = j + N * k, f1 = i + N * k, f2 = i + N * j;
+  if (active) {
+    double q[5], g[3][5];
+    const long long cb = e * 15 * NP + t;  // caches [e][3][5][NP]
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const long long o = e * NB + v * NP + t;
+      q[v] = fma(eps, a.z[o], a.U[o]);
+      float x = d0[v * NP + t];
+      x = fmaf(dq[(0 * N2 + f0) * 5 + v], sdgL[i], x);
+      x = fmaf(dq[(1 * N2 + f0) * 5 + v], sdgR[i], x);
+      float y = d1[v * NP + t];
+      y = fmaf(dq[(2 * N2 + f1) * 5 + v], sdgL[j], y);
+      y = fmaf(dq[(3 * N2 + f1) * 5 + v], sdgR[j], y);
+      float zz = d2[v * NP + t];
+      zz = fmaf(dq[(4 * N2 + f2) * 5 + v], sdgL[k], zz);
+      zz = fmaf(dq[(5 * N2 + f2) * 5 + v], sdgR[k], zz);
+      g[0][v] = fma(eps, (double)(s[0] * x), a.lg[cb + (0 * 5 + v) * NP]);
+      g[1][v] = fma(eps, (double)(s[1] * y), a.lg[cb + (1 * 5 + v) * NP]);
+      g[2][v] = fma(eps, (double)(s[2] * zz), a.lg[cb + (2 * 5 + v) * NP]);
+    }
+    double fv[3][5];
+    visc3(q, g, a.gam, a.mu, a.kappa, 7, fv);
+    float* dst[3] = {d0, d1, d2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double fi[5];
+      (void)flux3(q, d, a.gam, fi);
+      // each thread reads and overwrites only its own point
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        dst[d][v * NP + t] = (float)(((fi[v] - fv[d][v]) - a.lf[cb + (d * 5 + v) * NP]) * ieps);
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const float* F = d0 + v * NP;
+    const float* G = d1 + v * NP;
+    const float* H = d2 + v * NP;
+    float dF = sdgL[i] * fn[(0 * N2 + f0) * 5 + v];
+    dF = fmaf(sdgR[i], fn[(1 * N2 + f0) * 5 + v], dF);
+    float dG = sdgL[j] * fn[(2 * N2 + f1) * 5 + v];
+    dG = fmaf(sdgR[j], fn[(3 * N2 + f1) * 5 + v], dG);
+    float dH = sdgL[k] * fn[(4 * N2 + f2) * 5 + v];
+    dH = fmaf(sdgR[k], fn[(5 * N2 + f2) * 5 + v], dH);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      dF = fmaf(sDt[i][l], F[l + N * j + N2 * k], dF);
+      dG = fmaf(sDt[j][l], G[i + N * l + N2 * k], dG);
+      dH = fmaf(sDt[k][l], H[i + N * j + N2 * l], dH);
+    }
+    const float dR = -fmaf(s[0], dF, fmaf(s[1], dG, s[2] * dH));  // (R(U + eps z) - R(U)) / eps
+    const long long o = e * NB + v * NP + t;
+    const double Az = fma(a.shift, a.z[o], -(double)dR);
+    a.out[o] = MODE == 2 ? a.b[o] - Az : Az;
   }
 }
 
@@ -600,6 +839,12 @@ F3Args make_args3(fr_ctx* ctx) {
   a.r0f = nullptr;
   a.tbf = nullptr;
   a.r0_pass = 0;
+  a.ltb = ctx->lin3_tb;
+  a.lfb = ctx->lin3_fb;
+  a.lg = ctx->lin3_g;
+  a.lf = ctx->lin3_f;
+  a.tbz = ctx->lin3_tbz;
+  a.fbz = ctx->lin3_fbz;
   a.nx = ctx->nx;
   a.ny = ctx->ny;
   a.nz = ctx->nz;
@@ -627,6 +872,29 @@ int f3_launch(fr_ctx* ctx, int mode, const F3Args& a, bool perturb_trace, cudaSt
   }
   const unsigned gt = (unsigned)((ctx->ne + E - 1) / E);
   const int fam = mode == 3 ? FR_KF_FACTOR : (mode == 0 ? FR_KF_RESIDUAL : FR_KF_JV);
+  if ((mode == 1 || mode == 2) && ctx->opts.jv_precision == 1) {
+    // A z with FP32 linear parts: FP32 traces of z, face differences, cell
+    using LZ = CellLayout<P, float>;
+    static bool attrz = false;
+    if (!attrz) {
+      FRK_CUDA(ctx, cudaFuncSetAttribute(k3z_cell<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LZ::BYTES));
+      FRK_CUDA(ctx, cudaFuncSetAttribute(k3z_cell<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LZ::BYTES));
+      attrz = true;
+    }
+    if (!a.ltb || !a.tbz) return set_error(ctx, FR_ERR_UNSUPPORTED, "jv_precision = 1 needs its caches (set at creation)");
+    ProfScope ps_(ctx, fam, s, wb, wf);  // one timed record for the three kernels
+    k3z_trace<P><<<gt, E * NP, 0, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    count_launch();
+    const long long nf = ctx->ne * 3 * N2;
+    k3z_face<P><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    count_launch();
+    if (mode == 1) k3z_cell<P, 1><<<gt, E * NP, LZ::BYTES, s>>>(a);
+    else k3z_cell<P, 2><<<gt, E * NP, LZ::BYTES, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    return FR_OK;
+  }
   {
     ProfScope ps_(ctx, fam, s, wb, wf);  // one timed record for the three kernels
     if (perturb_trace) k3_trace<P, true><<<gt, E * NP, 0, s>>>(a);
@@ -747,6 +1015,46 @@ int f3_columns_p(fr_ctx* ctx, const F3Args& a, cudaStream_t s) {
   return ctx->opts.block_columns == 1 ? f3_columns<P, float>(ctx, a, s) : f3_columns<P, double>(ctx, a, s);
 }
 }  // namespace
+
+namespace {
+// the caches of the FP32-linear-parts A z at U: traces and face data of U in
+// their own buffers, then the corrected gradient and total fluxes at the points
+template <int P>
+int f3_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
+  using L = CellLayout<P>;
+  constexpr int NP = L::NP, N2 = L::N2, E = F3Slots<P>::E;
+  F3Args a = make_args3(ctx);
+  a.U = U;
+  a.tb = ctx->lin3_tb;
+  a.fb = ctx->lin3_fb;
+  FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+  const unsigned gt = (unsigned)((ctx->ne + E - 1) / E);
+  {
+    ProfScope ps_(ctx, FR_KF_OTHER, s);
+    k3_trace<P, false><<<gt, E * NP, 0, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    count_launch();
+    const long long nf = ctx->ne * 3 * N2;
+    k3_face<P><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(a);
+    FRK_LAUNCHED(ctx);
+    count_launch();
+    k3_cell<P, 4><<<gt, E * NP, L::BYTES, s>>>(a);
+  }
+  FRK_LAUNCHED(ctx);
+  return FR_OK;
+}
+}  // namespace
+
+int launch_f3_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
+  if (ctx->opts.jv_precision != 1) return FR_OK;
+  switch (ctx->p) {
+    case 1: return f3_linearize<1>(ctx, U, s);
+    case 2: return f3_linearize<2>(ctx, U, s);
+    case 3: return f3_linearize<3>(ctx, U, s);
+    case 4: return f3_linearize<4>(ctx, U, s);
+    default: return set_error(ctx, FR_ERR_UNSUPPORTED, "3D degree %d not compiled", ctx->p);
+  }
+}
 
 int launch_f3_factor(fr_ctx* ctx, const double* U, double shift, cudaStream_t s) {
   if (ctx->p > 3 || !ctx->mst || ctx->blk_chunk < 1)

@@ -135,6 +135,13 @@ struct fr_ctx {
   double* rloc = nullptr;    // viscous: R(U) at the linearisation point of the blocks
   float* r0f = nullptr;      // FP32 block columns: element-local R(U) of one staging chunk
   float* tbf = nullptr;      // FP32 block columns: FP32 copy of the 3D trace buffer
+  // 3D A z with FP32 linear parts: caches at the linearisation point and FP32 buffers
+  double* lin3_tb = nullptr;
+  double* lin3_fb = nullptr;
+  double* lin3_g = nullptr;
+  double* lin3_f = nullptr;
+  float* lin3_tbz = nullptr;
+  float* lin3_fbz = nullptr;
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
   long long blk_chunk = 0;   // elements whose staged blocks mst holds at once (ne unless staged in chunks)
   int hist_row = 0;          // ROW order of the last step if its stage solutions are intact
@@ -299,6 +306,8 @@ int launch_vortex_error(fr_ctx* ctx, const double* U, const fr_vortex* vx, doubl
 // blocks.cu: invert staged FP64 blocks (column-major M[c][row], dshift added to
 // the diagonal) into ctx->blocks; re-invert the staged blocks at a new shift
 int launch_block_invert(fr_ctx* ctx, const double* mst, double dshift, cudaStream_t s);
+// caches of the 3D A z with FP32 linear parts at U (no-op unless jv_precision = 1)
+int launch_f3_linearize(fr_ctx* ctx, const double* U, cudaStream_t s);
 // invert the staged blocks of elements e0 .. e0 + n - 1 (mst holds them from its start)
 int launch_block_invert_range(fr_ctx* ctx, const double* mst, double dshift, long long e0, long long n,
                               cudaStream_t s);

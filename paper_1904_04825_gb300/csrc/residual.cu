@@ -572,7 +572,8 @@ int launch_batch_residual(int p, int riemann, const void* tab, const int* start,
 }
 
 int launch_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
-  if (ctx->opts.jv_precision != 1 || ctx->viscous || ctx->dim3) return FR_OK;
+  if (ctx->dim3) return launch_f3_linearize(ctx, U, s);
+  if (ctx->opts.jv_precision != 1 || ctx->viscous) return FR_OK;
   return launch_residual(ctx, 3, U, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, s);
 }
 

@@ -19,6 +19,7 @@ from oracle.tableaus import ESDIRK, ROW
 pytestmark = pytest.mark.gpu
 
 TG = S.TaylorGreen()
+JV32_TOL = 2e-5   # relative error of the FP32-linear-parts A z (see its test)
 
 
 @pytest.fixture(scope="module")
@@ -100,6 +101,46 @@ def test_jv_matches_oracle(fr, p):
     fr.fr_jv(ctx, _t(U0), _t(R0), _t(z0), 12.0, y)
     yo = fd_jv(prob, U0, R0, z0, 12.0)
     assert _rel(y.cpu().numpy(), yo) < 1e-6
+
+
+@pytest.mark.parametrize("p,mu", [(1, 0.03), (2, 0.03), (3, 0.03), (4, 0.03), (3, 0.0)])
+def test_jv_fp32_linear_parts_matches_oracle(fr, p, mu):
+    """A z with FP32 linear parts (jv_precision = 1) against the oracle's FP64
+    FD product: the FP32 rounding of z and of the derivatives, traces,
+    liftings and divergence leaves a relative error of ~1e-6; z = 0 gives
+    shift z = 0 exactly."""
+    edges, U0 = _random_case(p, dims=(4, 3, 3), seed=11)
+    gas = Gas3D(mu=mu, prandtl=0.71)
+    prob = Problem3D(Mesh3D(*edges), p, gas)
+    R0 = prob.R(U0)
+    z0 = S.random_vector(U0.shape, 5)
+    ctx = fr.Context3D(*edges, p, _opts(fr, mu, jv_precision=1))
+    y = ctx.empty()
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(z0), 12.0, y)
+    yo = fd_jv(prob, U0, R0, z0, 12.0)
+    err = _rel(y.cpu().numpy(), yo)
+    assert err < JV32_TOL, err
+    fr.fr_jv(ctx, _t(U0), _t(R0), _t(np.zeros_like(z0)), 12.0, y)
+    assert np.all(y.cpu().numpy() == 0.0)
+
+
+def test_row3_step_with_fp32_linear_parts_matches_oracle(fr):
+    """ROW3 with the FP32-linear-parts A z at tol_lin 1e-8 (the operator's
+    own relative error is ~1e-6, so GMRES converges to the FP64 step to about
+    that level)."""
+    p = 2
+    edges, U0 = _tgv_case(4, p)
+    gas = Gas3D(mu=TG.mu, prandtl=TG.prandtl)
+    prob = Problem3D(Mesh3D(*edges), p, gas)
+    dt = 0.1
+    ctx = fr.Context3D(*edges, p, _opts(fr, TG.mu, precond=1, tol_lin=1e-8, gmres_max_restarts=100,
+                                        jv_precision=1))
+    U = _t(U0)
+    st = fr.step_row(ctx, 3, dt, U)
+    Uo, so = o_row(prob, ROW[3](), dt, U0, SolverOpts(tol_lin=1e-12, m=30, max_restarts=200, precond=True))
+    assert st.converged and so.converged
+    err = _rel(U.cpu().numpy(), Uo)
+    assert err < 1e-7, err
 
 
 @pytest.mark.parametrize("p,prec,tol", [(1, 0, 1e-6), (1, 2, 3e-2), (2, 0, 1e-6), (2, 1, 1e-4), (3, 1, 1e-4),
@@ -255,7 +296,7 @@ def test_dissipation_rate_matches_oracle(fr, p):
 
 def test_unsupported_3d_options_rejected(fr):
     edges = S.uniform_mesh3d(2)
-    for kw in (dict(precond=1), dict(riemann=1), dict(jv_precision=1)):
+    for kw in (dict(precond=1), dict(riemann=1), dict(jv_precision=2)):
         with pytest.raises(fr.FrError):
             fr.Context3D(*edges, 3, _opts(fr, 0.01, **kw))
     with pytest.raises(fr.FrError):

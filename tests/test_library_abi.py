@@ -104,7 +104,6 @@ def test_3d_argument_checks_without_gpu(libpath):
     assert create(desc, 2, block_columns=1, precond=0, block_precision=1) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, block_columns=-1) == fr.FR_ERR_INVALID_ARG
     assert create(desc, 2, riemann=1) == fr.FR_ERR_UNSUPPORTED           # Rusanov only
-    assert create(desc, 2, jv_precision=1) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, guess=2) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, body_force_x=0.1) == fr.FR_ERR_UNSUPPORTED
     assert create(desc, 2, m_max=64) == fr.FR_ERR_INVALID_ARG
