@@ -19,7 +19,7 @@ from oracle.tableaus import ESDIRK, ROW
 pytestmark = pytest.mark.gpu
 
 TG = S.TaylorGreen()
-JV32_TOL = 2e-5   # relative error of the FP32-linear-parts A z (see its test)
+JV32_TOL = 1e-6   # relative error of the FP32-linear-parts A z: measured 6e-8 .. 9e-8 (p = 1-4)
 
 
 @pytest.fixture(scope="module")
@@ -107,8 +107,9 @@ def test_jv_matches_oracle(fr, p):
 def test_jv_fp32_linear_parts_matches_oracle(fr, p, mu):
     """A z with FP32 linear parts (jv_precision = 1) against the oracle's FP64
     FD product: the FP32 rounding of z and of the derivatives, traces,
-    liftings and divergence leaves a relative error of ~1e-6; z = 0 gives
-    shift z = 0 exactly."""
+    liftings and divergence acts on (R(U + eps z) - R(U)) / eps, not on R,
+    so it leaves a relative error of a few FP32 unit roundoffs (6e-8 to 9e-8
+    measured for p = 1-4); z = 0 gives shift z = 0 exactly."""
     edges, U0 = _random_case(p, dims=(4, 3, 3), seed=11)
     gas = Gas3D(mu=mu, prandtl=0.71)
     prob = Problem3D(Mesh3D(*edges), p, gas)
