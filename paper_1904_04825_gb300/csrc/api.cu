@@ -47,6 +47,7 @@ void free_ctx(fr_ctx* c) {
   cudaFree(c->lin3_f);
   cudaFree(c->lin3_tbz);
   cudaFree(c->lin3_fbz);
+  cudaFree(c->lin3_gc);
   cudaFree(c->gfeat);
   for (double* p : c->bhist) cudaFree(p);
   cudaFree(c->gout);
@@ -216,6 +217,7 @@ int create3d(const fr_mesh3d_desc* mesh, int p, const fr_opts* o, fr_ctx* c) {
     FRK_TRY(dalloc(c, &c->lin3_f, (size_t)c->ndof * 3));
     FRK_TRY(dalloc(c, &c->lin3_tbz, (size_t)c->ne * 6 * n2 * 20));
     FRK_TRY(dalloc(c, &c->lin3_fbz, (size_t)c->ne * 3 * n2 * 10));
+    FRK_TRY(dalloc(c, &c->lin3_gc, (size_t)c->ne * 3 * n2 * 15));
   }
   if (o->precond) {
     const size_t nb2 = (size_t)c->nb * c->nb;

@@ -58,6 +58,8 @@ struct F3Args {
   double* lf;            // total fluxes at U at the points [ne][3][5][Np]
   float* tbz;            // traces of z and of its gradient [ne][6][N^2][20]
   float* fbz;            // per unit eps: q_com differences and f_n differences [ne][3][N^2][10]
+  double* lgc;           // BR2 common gradient of U at the low-face points [ne][3][N^2][15]
+  int write_gc;          // cache pass: k3_face writes lgc
   int r0_pass;           // mode 3 in FP32: 1 = write r0f (one unperturbed slot per element)
   int nx, ny, nz;
   double gam, mu, kappa, shift, beps;
@@ -160,7 +162,7 @@ __device__ __forceinline__ void visc3(const T q[5], const T g[3][5], T gam, T mu
 // sizes along d; cbr2 = (P+1)(P+2)/2
 template <typename T>
 __device__ __forceinline__ void common3(const T m[5][4], const T pp[5][4], int d, T hm, T hp, T cbr2,
-                                        const F3Args& a, T qc[5], T fn[5]) {
+                                        const F3Args& a, T qc[5], T fn[5], T (*gout)[5] = nullptr) {
   T qm[5], qp[5], g[3][5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -180,6 +182,12 @@ __device__ __forceinline__ void common3(const T m[5][4], const T pp[5][4], int d
   visc3(qc, g, (T)a.gam, (T)a.mu, (T)a.kappa, 1 << d, fv);
 #pragma unroll
   for (int v = 0; v < 5; ++v) fn[v] = fi[v] - (d == 0 ? fv[0][v] : (d == 1 ? fv[1][v] : fv[2][v]));
+  if (gout) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gout[c][v] = g[c][v];
+  }
 }
 
 __device__ __forceinline__ void coords(long long e, const F3Args& a, int* ix, int* iy, int* iz) {
@@ -307,12 +315,20 @@ __global__ void __launch_bounds__(256) k3_face(const F3Args a) {
       m[v][c] = nb[v * 4 + c];
       pp[v][c] = own[v * 4 + c];
     }
-  common3(m, pp, d, hm, hp, cbr2, a, qc, fn);
+  double gc[3][5];
+  common3(m, pp, d, hm, hp, cbr2, a, qc, fn, a.write_gc ? gc : nullptr);
   double* dst = a.fb + ((e * 3 + d) * N2 + f) * 10;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     dst[v] = qc[v];
     dst[5 + v] = fn[v];
+  }
+  if (a.write_gc) {  // cache pass of the FP32-linear-parts A z: the common gradient at U
+    double* g = a.lgc + ((e * 3 + d) * N2 + f) * 15;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[c * 5 + v] = gc[c][v];
   }
 }
 
@@ -569,7 +585,8 @@ __global__ void __launch_bounds__(256) k3z_trace(const F3Args a) {
   if (!active) return;
   int ix, iy, iz;
   coords(e, a, &ix, &iy, &iz);
-  const float s[3] = {(float)(2.0 / a.hx[ix]), (float)(2.0 / a.hy[iy]), (float)(2.0 / a.hz[iz])};
+  // 2 / h in FP32 (an FP64 division costs this FP32 kernel more than all its FP32 work)
+  const float s[3] = {2.f / (float)a.hx[ix], 2.f / (float)a.hy[iy], 2.f / (float)a.hz[iz]};
   for (int fp = t; fp < 6 * N2; fp += NP) {
     const int face = fp / N2, f = fp % N2;
     float o[5][4];
@@ -605,21 +622,44 @@ __global__ void __launch_bounds__(256) k3z_face(const F3Args a) {
   const double hp = d == 0 ? a.hx[ix] : (d == 1 ? a.hy[iy] : a.hz[iz]);
   const long long om = ((nbe * 6 + 2 * d + 1) * N2 + f) * 20;  // (-) side: the neighbour's high face
   const long long op = ((e * 6 + 2 * d) * N2 + f) * 20;        // (+) side: this element's low face
-  double m[5][4], pp[5][4], qc[5], fn[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      m[v][c] = fma(eps, (double)a.tbz[om + v * 4 + c], a.ltb[om + v * 4 + c]);
-      pp[v][c] = fma(eps, (double)a.tbz[op + v * 4 + c], a.ltb[op + v * 4 + c]);
-    }
-  common3(m, pp, d, hm, hp, cbr2, a, qc, fn);
-  const double* f0 = a.lfb + ((e * 3 + d) * N2 + f) * 10;
-  float* dst = a.fbz + ((e * 3 + d) * N2 + f) * 10;
+  const long long fo = (e * 3 + d) * N2 + f;
+  // the linear part in FP32: q_com and the BR2 common gradient of z (the
+  // same average and liftings as common3)
+  const float cb = (float)cbr2;
+  float qcz[5], gz[3][5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    dst[v] = 0.5f * (a.tbz[om + v * 4] + a.tbz[op + v * 4]);
-    dst[5 + v] = (float)((fn[v] - f0[5 + v]) * ieps);
+    const float zm = a.tbz[om + v * 4], zp = a.tbz[op + v * 4];
+    qcz[v] = 0.5f * (zm + zp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gz[c][v] = 0.5f * (a.tbz[om + v * 4 + 1 + c] + a.tbz[op + v * 4 + 1 + c]);
+    const float rm = (2.f / (float)hm) * cb * (qcz[v] - zm);
+    const float rp = -(2.f / (float)hp) * cb * (qcz[v] - zp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)  // selected, not indexed by d, so gz stays in registers
+      if (c == d) gz[c][v] = 0.5f * ((a.tbz[om + v * 4 + 1 + c] + rm) + (a.tbz[op + v * 4 + 1 + c] + rp));
+  }
+  // the fluxes at U + eps z in FP64: face states for the Rusanov flux, q_com
+  // and the common gradient for the viscous flux, each = cache + eps * FP32 part
+  const double* f0 = a.lfb + fo * 10;
+  const double* g0 = a.lgc + fo * 15;
+  double qm[5], qp[5], qc[5], g[3][5], fi[5], fv[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qm[v] = fma(eps, (double)a.tbz[om + v * 4], a.ltb[om + v * 4]);
+    qp[v] = fma(eps, (double)a.tbz[op + v * 4], a.ltb[op + v * 4]);
+    qc[v] = fma(eps, (double)qcz[v], f0[v]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c][v] = fma(eps, (double)gz[c][v], g0[c * 5 + v]);
+  }
+  rusanov3(qm, qp, d, a.gam, fi);
+  visc3(qc, g, a.gam, a.mu, a.kappa, 1 << d, fv);
+  float* dst = a.fbz + fo * 10;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double fnv = fi[v] - (d == 0 ? fv[0][v] : (d == 1 ? fv[1][v] : fv[2][v]));
+    dst[v] = qcz[v];
+    dst[5 + v] = (float)((fnv - f0[5 + v]) * ieps);
   }
 }
 
@@ -662,9 +702,9 @@ __global__ void __launch_bounds__(256) k3z_cell(const F3Args a) {
   float s[3] = {1.f, 1.f, 1.f};
   if (active) {
     coords(e, a, &ix, &iy, &iz);
-    s[0] = (float)(2.0 / a.hx[ix]);
-    s[1] = (float)(2.0 / a.hy[iy]);
-    s[2] = (float)(2.0 / a.hz[iz]);
+    s[0] = 2.f / (float)a.hx[ix];
+    s[1] = 2.f / (float)a.hy[iy];
+    s[2] = 2.f / (float)a.hz[iz];
 #pragma unroll
     for (int v = 0; v < 5; ++v) sz[v * NP + t] = (float)a.z[e * NB + v * NP + t];
   }
@@ -845,6 +885,8 @@ F3Args make_args3(fr_ctx* ctx) {
   a.lf = ctx->lin3_f;
   a.tbz = ctx->lin3_tbz;
   a.fbz = ctx->lin3_fbz;
+  a.lgc = ctx->lin3_gc;
+  a.write_gc = 0;
   a.nx = ctx->nx;
   a.ny = ctx->ny;
   a.nz = ctx->nz;
@@ -881,7 +923,7 @@ int f3_launch(fr_ctx* ctx, int mode, const F3Args& a, bool perturb_trace, cudaSt
       FRK_CUDA(ctx, cudaFuncSetAttribute(k3z_cell<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LZ::BYTES));
       attrz = true;
     }
-    if (!a.ltb || !a.tbz) return set_error(ctx, FR_ERR_UNSUPPORTED, "jv_precision = 1 needs its caches (set at creation)");
+    if (!a.ltb || !a.tbz || !a.lgc) return set_error(ctx, FR_ERR_UNSUPPORTED, "jv_precision = 1 needs its caches (set at creation)");
     ProfScope ps_(ctx, fam, s, wb, wf);  // one timed record for the three kernels
     k3z_trace<P><<<gt, E * NP, 0, s>>>(a);
     FRK_LAUNCHED(ctx);
@@ -1027,6 +1069,7 @@ int f3_linearize(fr_ctx* ctx, const double* U, cudaStream_t s) {
   a.U = U;
   a.tb = ctx->lin3_tb;
   a.fb = ctx->lin3_fb;
+  a.write_gc = 1;
   FRK_CUDA(ctx, cudaFuncSetAttribute(k3_cell<P, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
   const unsigned gt = (unsigned)((ctx->ne + E - 1) / E);
   {

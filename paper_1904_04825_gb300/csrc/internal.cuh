@@ -142,6 +142,7 @@ struct fr_ctx {
   double* lin3_f = nullptr;
   float* lin3_tbz = nullptr;
   float* lin3_fbz = nullptr;
+  double* lin3_gc = nullptr;
   double staged_shift = 0.0; // shift the staged blocks in mst were formed with
   long long blk_chunk = 0;   // elements whose staged blocks mst holds at once (ne unless staged in chunks)
   int hist_row = 0;          // ROW order of the last step if its stage solutions are intact
