@@ -454,6 +454,9 @@ def our_arm(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alu_peak, alu_src = FP64_PEAK_TFLOPS, "FP64 FMA pipe: 152 SMs x 4 flops/clk x 2.07 GHz (derived, nominal 1.25 TF)"
+    if top == "jv" and args.jv_precision == "fp32":
+        alu_src += ("; the algorithmic count includes the linear parts, which this product runs in FP32, "
+                    "so the fraction of the FP64 peak can exceed 1")
     if top == "invert" and prec:   # reduced-precision blocks are inverted in FP32 on the CUDA cores
         alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"
     roofline = {
