@@ -80,9 +80,11 @@ typedef struct fr_opts {
   double wall_temperature; /* T at isothermal walls */
   int block_precision;   /* element-Jacobi blocks: 0 = FP64 (default); 1 = FP32
                             inversion and storage; 2 = FP32 inversion, BF16
-                            storage.  The FD columns, the FD matvec, Arnoldi and
+                            storage.  The FD columns (unless block_columns = 1),
+                            the FD matvec (unless jv_precision = 1), Arnoldi and
                             all updates stay FP64 (reduced precision changes
-                            only the preconditioner, not the converged answer) */
+                            only the preconditioner, not the converged answer).
+                            3D degree 3 (320-row blocks) takes 1 or 2 only */
   int precond_refresh;   /* pseudo-transient continuation (ESDIRK, BDF2): 0 = form
                             J_ee once per stage at its first pseudo iterate and
                             re-invert shift*I - J_ee when dtau changes (default);
