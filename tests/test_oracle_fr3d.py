@@ -121,6 +121,24 @@ def test_element_blocks_match_brute_force_diagonal_blocks():
         assert np.linalg.norm(B[e] - Je) / np.linalg.norm(Je) < 2e-6
 
 
+def test_degree3_element_block_matches_brute_force_columns():
+    """The 320-row blocks of degree 3: element 0's block against central
+    differences of the full residual in element 0's DOFs only (every other
+    element unperturbed, so the rows of element 0 are dR_0/dq_0)."""
+    prob, U = _tiny(p=3, seed=5)
+    nb = prob.nb
+    u = U.reshape(-1)
+    J00 = np.zeros((nb, nb))
+    for j in range(nb):
+        h = 1e-6 * max(1.0, abs(u[j]))
+        up = u.copy(); up[j] += h
+        um = u.copy(); um[j] -= h
+        d = (prob.R(up.reshape(U.shape)) - prob.R(um.reshape(U.shape))).reshape(-1)
+        J00[:, j] = d[:nb] / (2 * h)
+    B = diagonal_blocks(prob, U)
+    assert np.linalg.norm(B[0] - J00) / np.linalg.norm(J00) < 2e-6
+
+
 def _tgv_closed_forms():
     """<S:S> and <rho |v|^2 / 2> / rho0 of the Taylor-Green initial field
     (rho0 = V0 = L = 1, p0 from Ma = 0.1), integrated exactly."""
