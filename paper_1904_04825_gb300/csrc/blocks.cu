@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) k_invert(const double* __restrict__ mst, 
 // CTA (element block + its r, one bulk copy each, in a ring of stages).
 template <int NB, typename S> struct ApplyShape;
 template <> struct ApplyShape<36, double> { static constexpr int KS = 4, NS = 6; };
-template <> struct ApplyShape<64, double> { static constexpr int KS = 2, NS = 3; };
+template <> struct ApplyShape<64, double> { static constexpr int KS = 1, NS = 1; };  // swept: (KS, NS) = (1, 1) 192 us, (1, 2) 197, (2, 2) 201, (2, 3) 218, (4, 3) 231 at 160^2 p=3
 template <> struct ApplyShape<100, double> { static constexpr int KS = 2, NS = 2; };
 template <> struct ApplyShape<36, float> { static constexpr int KS = 4, NS = 8; };
 template <> struct ApplyShape<64, float> { static constexpr int KS = 2, NS = 4; };
